@@ -1,0 +1,146 @@
+"""CPU oracle for batched Smith-Waterman with affine gaps.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this package; the product path never
+does, and the oracle imports nothing from the product.
+
+The arithmetic lives in ``sw_oracle.c`` (plain int32 Gotoh, forward pass for
+score and end, reverse pass on the reversed prefixes for the start); this
+module only marshals arguments through ctypes.  Conventions (the paper states
+none of them):
+
+* rows are query residues, columns reference residues;
+* a gap of length L costs ``gap_open + gap_extend * L``;
+* the end is the row-major-first cell holding the maximum score;
+* the start is the row-major-first cell holding that score in the local DP of
+  the reversed prefixes q[q_end..0], r[r_end..0];
+* coordinates are 0-based and inclusive; a zero score reports -1 for all four.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
+RECORD_DTYPE = np.dtype([("score", np.int32), ("q_start", np.int32),
+                         ("q_end", np.int32), ("r_start", np.int32),
+                         ("r_end", np.int32)])
+
+_lib = None
+
+
+def load():
+    """Builds (if needed) and loads liboracle.so."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    i8p = ctypes.POINTER(ctypes.c_int8)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_blosum62.argtypes = [i8p]
+    lib.oracle_blosum62.restype = None
+    lib.oracle_align_pair.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, i8p,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    lib.oracle_align_pair.restype = ctypes.c_int
+    lib.oracle_forward_pair.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, i8p,
+                                        ctypes.c_int32, ctypes.c_int32, i32p, i64p, i64p]
+    lib.oracle_forward_pair.restype = ctypes.c_int
+    lib.oracle_align_batch.argtypes = [u8p, i64p, u8p, i64p, i32p, ctypes.c_int64, i8p,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int]
+    lib.oracle_align_batch.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def blosum62():
+    """The oracle's own BLOSUM62 transcription, int8 [24, 24] (row = query)."""
+    out = np.zeros((24, 24), dtype=np.int8)
+    load().oracle_blosum62(_ptr(out, ctypes.c_int8))
+    return out
+
+
+def encode(text):
+    """ASCII protein string -> uint8 codes in ALPHABET order (upper case only)."""
+    return np.array([ALPHABET.index(c) for c in text], dtype=np.uint8)
+
+
+def _codes(x):
+    if isinstance(x, str):
+        return encode(x)
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+
+
+def _matrix(mat):
+    m = np.ascontiguousarray(np.asarray(mat, dtype=np.int8))
+    if m.shape != (24, 24):
+        raise ValueError("matrix must be 24 x 24")
+    return m
+
+
+def align_pair(q, r, mat=None, gap_open=11, gap_extend=1):
+    """One pair -> (score, q_start, q_end, r_start, r_end)."""
+    lib = load()
+    qc, rc = _codes(q), _codes(r)
+    m = _matrix(blosum62() if mat is None else mat)
+    rec = np.zeros(1, dtype=RECORD_DTYPE)
+    st = lib.oracle_align_pair(_ptr(qc, ctypes.c_uint8), len(qc), _ptr(rc, ctypes.c_uint8),
+                               len(rc), _ptr(m, ctypes.c_int8), gap_open, gap_extend,
+                               rec.ctypes.data)
+    if st != 0:
+        raise RuntimeError("oracle_align_pair failed: %d" % st)
+    return tuple(int(v) for v in rec[0])
+
+
+def forward_pair(q, r, mat=None, gap_open=11, gap_extend=1):
+    """Forward pass only -> (score, q_end, r_end)."""
+    lib = load()
+    qc, rc = _codes(q), _codes(r)
+    m = _matrix(blosum62() if mat is None else mat)
+    s = ctypes.c_int32()
+    qe = ctypes.c_int64()
+    re_ = ctypes.c_int64()
+    st = lib.oracle_forward_pair(_ptr(qc, ctypes.c_uint8), len(qc), _ptr(rc, ctypes.c_uint8),
+                                 len(rc), _ptr(m, ctypes.c_int8), gap_open, gap_extend,
+                                 ctypes.byref(s), ctypes.byref(qe), ctypes.byref(re_))
+    if st != 0:
+        raise RuntimeError("oracle_forward_pair failed: %d" % st)
+    return s.value, qe.value, re_.value
+
+
+def align_batch(q_res, q_off, r_res, r_off, pairs, mat=None, gap_open=11, gap_extend=1,
+                n_threads=None):
+    """Aligns pairs[p] = (q index, r index) over concatenated code buffers.
+
+    Returns an int32 array [P, 5] of (score, q_start, q_end, r_start, r_end).
+    """
+    lib = load()
+    q_res = np.ascontiguousarray(q_res, dtype=np.uint8)
+    r_res = np.ascontiguousarray(r_res, dtype=np.uint8)
+    q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+    r_off = np.ascontiguousarray(r_off, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    n = pairs.shape[0]
+    if n and (pairs[:, 0].min() < 0 or pairs[:, 0].max() >= len(q_off) - 1
+              or pairs[:, 1].min() < 0 or pairs[:, 1].max() >= len(r_off) - 1):
+        raise IndexError("pair index out of range")
+    m = _matrix(blosum62() if mat is None else mat)
+    out = np.zeros((n, 5), dtype=np.int32)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    st = lib.oracle_align_batch(_ptr(q_res, ctypes.c_uint8), _ptr(q_off, ctypes.c_int64),
+                                _ptr(r_res, ctypes.c_uint8), _ptr(r_off, ctypes.c_int64),
+                                _ptr(pairs, ctypes.c_int32), n, _ptr(m, ctypes.c_int8),
+                                gap_open, gap_extend, out.ctypes.data, int(n_threads))
+    if st != 0:
+        raise RuntimeError("oracle_align_batch failed: %d" % st)
+    return out

@@ -1,0 +1,30 @@
+"""Compiles the CPU oracle (sw_oracle.c) into oracle/_build/liboracle.so.
+
+Test infrastructure only: the product path never loads this library.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "sw_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "liboracle.so")
+
+
+def command():
+    return ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+            "-Wall", "-Wextra", "-o", LIB, SRC]
+
+
+def build(force=False):
+    """Builds the library if it is missing or older than its source."""
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    subprocess.run(command(), check=True)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))

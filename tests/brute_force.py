@@ -1,0 +1,96 @@
+"""Brute-force enumeration of local alignments, used to pin the CPU oracle.
+
+An alignment is a sequence of columns: M (query residue against reference
+residue), I (query residue against a gap) and D (reference residue against a
+gap).  A maximal run of L columns of the same gap kind costs ``gap_cost(L)``;
+an I run directly followed by a D run (or the reverse) is two gaps.  A local
+alignment that starts or ends with a gap scores strictly less than the same
+alignment without it, so only alignments whose first and last columns are M
+are enumerated.  Every such alignment of every substring pair is visited by a
+depth-first walk; nothing is shared with the oracle's dynamic programme.
+"""
+
+
+def enumerate_local(q, r, score, gap_cost):
+    """Yields (total, q_start, q_end, r_start, r_end) for every local alignment
+    whose first and last columns are matches.
+
+    q, r: sequences of codes; score(a, b): substitution score; gap_cost(L) > 0.
+    """
+    lq, lr = len(q), len(r)
+    out = []
+
+    def walk(i, j, last, run, gaps_closed, subst, qs, rs):
+        # (i, j) is the last consumed cell; `last` is the kind of the last
+        # column; `run` its current length when it is a gap.
+        if last == "M":
+            out.append((subst - gaps_closed, qs, i, rs, j))
+            pending = 0
+        else:
+            pending = gap_cost(run)
+        # M column
+        if i + 1 < lq and j + 1 < lr:
+            walk(i + 1, j + 1, "M", 0, gaps_closed + pending,
+                 subst + score(q[i + 1], r[j + 1]), qs, rs)
+        # I column (consumes a query residue)
+        if i + 1 < lq:
+            if last == "I":
+                walk(i + 1, j, "I", run + 1, gaps_closed, subst, qs, rs)
+            else:
+                walk(i + 1, j, "I", 1, gaps_closed + pending, subst, qs, rs)
+        # D column (consumes a reference residue)
+        if j + 1 < lr:
+            if last == "D":
+                walk(i, j + 1, "D", run + 1, gaps_closed, subst, qs, rs)
+            else:
+                walk(i, j + 1, "D", 1, gaps_closed + pending, subst, qs, rs)
+
+    for qs in range(lq):
+        for rs in range(lr):
+            walk(qs, rs, "M", 0, 0, score(q[qs], r[rs]), qs, rs)
+    return out
+
+
+def brute_record(q, r, score, gap_cost):
+    """The record the oracle's conventions define, found by enumeration.
+
+    score S = max(0, best total).  End: among optimal alignments, the smallest
+    q_end, then the smallest r_end (row-major first).  Start: among optimal
+    alignments ending there, the largest q_start, then the largest r_start.
+    Also returns the set of all optimal (q_start, q_end, r_start, r_end).
+    """
+    alns = enumerate_local(q, r, score, gap_cost)
+    best = max([a[0] for a in alns], default=0)
+    if best <= 0:
+        return (0, -1, -1, -1, -1), set()
+    opt = {a[1:] for a in alns if a[0] == best}
+    q_end, r_end = min((a[1], a[3]) for a in opt)
+    starts = [(a[0], a[2]) for a in opt if a[1] == q_end and a[3] == r_end]
+    q_start, r_start = max(starts)
+    return (best, q_start, q_end, r_start, r_end), opt
+
+
+def global_affine(q, r, score, go, ge):
+    """Best global alignment score of q against r, gap of length L = go + ge*L.
+
+    Plain three-state programme with gaps allowed at both ends; used to
+    re-score a reported span.
+    """
+    NEG = -10 ** 9
+    lq, lr = len(q), len(r)
+    H = [[NEG] * (lr + 1) for _ in range(lq + 1)]
+    E = [[NEG] * (lr + 1) for _ in range(lq + 1)]   # last column consumes r
+    F = [[NEG] * (lr + 1) for _ in range(lq + 1)]   # last column consumes q
+    H[0][0] = 0
+    for j in range(1, lr + 1):
+        E[0][j] = -(go + ge * j)
+        H[0][j] = E[0][j]
+    for i in range(1, lq + 1):
+        F[i][0] = -(go + ge * i)
+        H[i][0] = F[i][0]
+    for i in range(1, lq + 1):
+        for j in range(1, lr + 1):
+            E[i][j] = max(E[i][j - 1] - ge, H[i][j - 1] - go - ge)
+            F[i][j] = max(F[i - 1][j] - ge, H[i - 1][j] - go - ge)
+            H[i][j] = max(H[i - 1][j - 1] + score(q[i - 1], r[j - 1]), E[i][j], F[i][j])
+    return H[lq][lr]
