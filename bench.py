@@ -1,0 +1,377 @@
+"""Throughput of batched Smith-Waterman (affine gaps, BLOSUM62, open 11 /
+extend 1) on one GB300, on the seeded 2,000,000-pair log-normal workload.
+
+One step = one call of the whole hot path (device bucketing, forward DP for
+score and end, reverse DP for start, records in pair order) over all pairs,
+inputs resident in HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun every rank aligns its own copy of the workload (weak scaling,
+no collective on the data path); the step time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS & alignments/s on 1 GB300 (bit-exact); filter recall; p50/p99 latency"
+ADDMAX_OPS_PER_CELL = 2.5     # five packed 16x2 add-max per two cells
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dp_forward_traffic.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_kernels.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_2m")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(name, mat):
+    from paper_2303_01845_gb300 import workload
+    return workload.generate(name, mat)
+
+
+def cpu_oracle_sample(wl, mat, target_s, seed=7):
+    """Times the oracle (as it stands) on a seeded random subset of the pairs
+    sized to take about target_s seconds on all host cores."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(wl.pairs))
+    # calibrate on a small subset
+    n0 = min(len(perm), 2000)
+    sub = wl.subset(np.sort(perm[:n0]))
+    t = time.perf_counter()
+    oracle.align_batch(sub.q_res, sub.q_off, sub.r_res, sub.r_off, sub.pairs, mat, 11, 1,
+                       n_threads=cores)
+    dt = time.perf_counter() - t
+    rate = sub.cells() / max(dt, 1e-6)
+    mean_cells = sub.cells() / n0
+    n = int(min(len(perm), max(n0, target_s * rate / mean_cells)))
+    sub = wl.subset(np.sort(perm[:n]))
+    t = time.perf_counter()
+    oracle.align_batch(sub.q_res, sub.q_off, sub.r_res, sub.r_off, sub.pairs, mat, 11, 1,
+                       n_threads=cores)
+    dt = time.perf_counter() - t
+    return {"gcups": sub.cells() / dt / 1e9, "aln_per_s": n / dt, "cores": cores, "pairs": n,
+            "cells": sub.cells(), "seconds": dt}
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores, same workload and metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    mat = oracle.blosum62()
+    wl = make_workload(args.workload, mat)
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    # size one step's sample from a calibration run
+    cal = cpu_oracle_sample(wl, mat, per_step / 4, seed=99)
+    mean_cells = cal["cells"] / cal["pairs"]
+    n = int(min(len(wl.pairs), per_step * cal["gcups"] * 1e9 / mean_cells))
+    rng = np.random.default_rng(3)
+    times, cells, pairs = [], 0, 0
+    for step in range(args.warmup + args.steps):
+        sub = wl.subset(np.sort(rng.choice(len(wl.pairs), size=n, replace=False)))
+        t = time.perf_counter()
+        oracle.align_batch(sub.q_res, sub.q_off, sub.r_res, sub.r_off, sub.pairs, mat, 11, 1,
+                           n_threads=cores)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+            cells += sub.cells()
+            pairs += n
+    total = sum(times)
+    value = cells / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "pairs_per_step": n,
+                   "sample": "seeded random subset of the workload's pairs per step"},
+        "alignments_per_s": pairs / total,
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d random pairs of %s per step" % (n, args.workload)},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def traffic_for_current_kernel():
+    """DRAM bytes per forward launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        rec = json.load(open(PROFILE_SUMMARY))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha") != sha(KERNEL_SOURCE):
+        return None
+    return rec.get("dram_bytes_per_forward_pass")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2303_01845_gb300 import swgb
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mat = swgb.swgb_blosum62()
+    wl = make_workload(args.workload, mat)
+    al = swgb.Aligner(local)
+    stream = torch.cuda.current_stream(dev)
+    q = al.seqset(torch.from_numpy(wl.q_res).to(dev), torch.from_numpy(wl.q_off).to(dev))
+    r = al.seqset(torch.from_numpy(wl.r_res).to(dev), torch.from_numpy(wl.r_off).to(dev))
+    pairs = torch.from_numpy(wl.pairs).to(dev)
+    out = torch.empty((len(wl.pairs), 5), dtype=torch.int32, device=dev)
+    params = swgb.make_params(mat, 11, 1, timing=True)
+    P = len(wl.pairs)
+
+    def step():
+        swgb.swgb_align(al.ctx, q.handle, r.handle, pairs, params, out, stream)
+
+    for _ in range(args.warmup):
+        step()
+        swgb.swgb_sync(al.ctx, stream)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    step_ms, fwd_ms, rev_ms = [], [], []
+    launches = 0
+    stats = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            swgb.swgb_sync(al.ctx, stream)
+            stats = swgb.swgb_last_stats(al.ctx)
+            fwd_ms.append(stats["forward_ms"])
+            rev_ms.append(stats["reverse_ms"])
+            launches += stats["kernel_launches"]
+        torch.cuda.synchronize()
+        barrier()
+    clock = clocks.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells = stats["forward_cells"]
+    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
+    aln_per_s = world * P * args.steps / (total_ms / 1e3)
+    fwd_mean = statistics.mean(fwd_ms)
+    achieved = cells / (fwd_mean / 1e3) / 1e9
+
+    # roofline of the forward DP: add-max issue rate x SMs x max clock
+    ops_per_clk, sms = swgb.swgb_probe_addmax_rate(al.ctx)
+    peaks = measured_peaks()
+    sm_max_mhz = peaks.get("sm_max_mhz") or clock.get("sm_max_mhz") or 2070.0
+    peak = sms * sm_max_mhz * 1e6 * ops_per_clk / ADDMAX_OPS_PER_CELL / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(al, wl, mat, dev, stream, args)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, np.asarray(mat), args.cpu_seconds)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
+        "config": {"workload": args.workload, "pairs": P, "forward_cells": cells,
+                   "reverse_cells": stats["reverse_cells"],
+                   "int32_pairs": stats["n_int32_pairs"], "gap_open": 11, "gap_extend": 1,
+                   "matrix": "BLOSUM62",
+                   "l2": "inputs (%.2f GB of residues) exceed L2; no flush" %
+                         ((len(wl.q_res) + len(wl.r_res)) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "alignments_per_s": aln_per_s,
+        "gcups_forward_kernel": achieved,
+        "forward_ms": fwd_mean, "reverse_ms": statistics.mean(rev_ms),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+                     "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+                     "peak_basis": "%d SMs x %.0f MHz x %.1f add-max/clk/SM (measured) / %.1f per cell"
+                                   % (sms, sm_max_mhz, ops_per_clk, ADDMAX_OPS_PER_CELL)},
+        "cpu_baseline": None if cpu is None else {
+            "value": cpu["gcups"], "unit": "GCUPS", "cores": cpu["cores"], "kind": "oracle",
+            "sample": "%d random pairs (%.2e cells) of %s, %.1f s" %
+                      (cpu["pairs"], cpu["cells"], args.workload, cpu["seconds"]),
+            "alignments_per_s": cpu["aln_per_s"]},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
+                   "reasons": clock["reasons"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure_e2e(al, wl, mat, dev, stream, args):
+    """Same metric through the public host-buffer API: every step loads both
+    sequence sets from pinned host memory, copies the pairs in and the records
+    out (swgb_seqset_load + swgb_align_host)."""
+    import torch
+
+    from paper_2303_01845_gb300 import swgb
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    q_res, q_off, r_res, r_off = pin(wl.q_res), pin(wl.q_off), pin(wl.r_res), pin(wl.r_off)
+    pairs = pin(wl.pairs)
+    out = torch.empty((len(wl.pairs), 5), dtype=torch.int32).pin_memory()
+    params = swgb.make_params(mat, 11, 1)
+    qs = al.seqset(q_res, q_off, stream=stream)
+    rs = al.seqset(r_res, r_off, stream=stream)
+
+    def step():
+        swgb.swgb_seqset_load(al.ctx, qs.handle, q_res, q_off, stream=stream)
+        swgb.swgb_seqset_load(al.ctx, rs.handle, r_res, r_off, stream=stream)
+        swgb.swgb_align_host(al.ctx, qs.handle, rs.handle, pairs, params, out, stream)
+
+    step()
+    n = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / n
+    st = swgb.swgb_last_stats(al.ctx)
+    h2d = sum(x.numel() * x.element_size() for x in (q_res, q_off, r_res, r_off, pairs))
+    qs.close()
+    rs.close()
+    return {"value": st["forward_cells"] / dt / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": out.numel() * out.element_size(), "ms_per_step": dt * 1e3,
+            "alignments_per_s": len(wl.pairs) / dt}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * swgb.h -- C ABI of libswgb: batched Smith-Waterman local alignment with
+ * affine gaps on one GB300 (sm_103a), for many-against-many protein search.
+ *
+ * The operation is the paper's alignment step (Sec. "Protein similarity
+ * search pipeline", component (ii): batch alignment of the candidate pairs
+ * found by shared k-mers; Sec. "Load balancing": a Smith-Waterman variant that
+ * fills the whole score matrix of each pair; Sec. "How Performance Was
+ * Measured": cell updates per second count the forward scoring pass).  The
+ * problem statement it serves is Sec. "Overview of the Problem": a set of
+ * query sequences aligned against a set of reference sequences (or a set
+ * against itself), over candidate pairs (Sec. "Load balancing techniques":
+ * each nonzero of the overlap matrix is one pairwise alignment).
+ *
+ * Scoring (integer throughout, "Performance Attributes" table):
+ *   rows i walk the query, columns j the reference; a gap of length L costs
+ *   gap_open + gap_extend * L;
+ *     E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o - e)
+ *     F(i,j) = max(F(i-1,j) - e, H(i-1,j) - o - e)
+ *     H(i,j) = max(0, H(i-1,j-1) + s(q_i, r_j), E(i,j), F(i,j))
+ *   score S = max H.  The paper uses open 11 / extend 2 in its production
+ *   run (program-parameters table); both are arguments here.
+ * Record of a pair (0-based, inclusive coordinates):
+ *   (q_end, r_end)     the row-major-first cell (smallest i, then j) with H = S;
+ *   (q_start, r_start) from the local DP of the reversed prefixes
+ *                      q[q_end..0], r[r_end..0]: its row-major-first cell
+ *                      (a, b) with value S gives q_start = q_end - a,
+ *                      r_start = r_end - b;
+ *   S = 0 reports -1 in all four coordinates.
+ * The paper fixes neither tie-breaks nor the start-finding pass; these are the
+ * library's stated conventions, and results are identical (bit for bit) to a
+ * plain int32 implementation of them.
+ *
+ * Residues are codes 0..23 in the order A R N D C Q E G H I L K M F P S T W Y
+ * V B Z X * (NCBI BLOSUM order).  Sequence sets may also be loaded from ASCII
+ * letters (case-insensitive; U and O read as X).
+ *
+ * Threading: a context owns device scratch reused by every call, so calls on
+ * one context must be ordered (one stream, or caller-serialised).  Different
+ * contexts are independent.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (every int-returning call) ---- */
+#define SWGB_OK 0
+#define SWGB_EINVAL (-1)  /* null pointer, negative count, bad flags, penalty out of range */
+#define SWGB_ERANGE (-2)  /* pair index outside its sequence set, or sequence too long */
+#define SWGB_EBADRES (-3) /* a residue letter or code outside the alphabet */
+#define SWGB_ENOMEM (-4)  /* a device or host allocation failed */
+#define SWGB_ECUDA (-5)   /* a CUDA runtime call failed (message in swgb_last_error) */
+#define SWGB_EINTERNAL (-6) /* the device detected an inconsistency in its own results */
+
+#define SWGB_ALPHABET_SIZE 24
+/* Longest sequence accepted (residues). */
+#define SWGB_MAX_LENGTH 65536
+
+/* ---- flags ---- */
+/* swgb_seqset_create / swgb_seqset_load */
+#define SWGB_SEQ_ASCII 0x1u   /* residues are ASCII letters; otherwise codes 0..23 */
+#define SWGB_SEQ_DEVICE 0x2u  /* residues and offsets are device pointers; otherwise host */
+/* swgb_params.flags */
+#define SWGB_FORCE_INT32 0x1u /* every pair on the 32-bit path (no 16x2 packing) */
+#define SWGB_TIMING 0x2u      /* record CUDA events around the forward and reverse kernels */
+
+typedef struct swgb_ctx swgb_ctx;
+typedef struct swgb_seqset swgb_seqset;
+
+/* One alignment result, 20 bytes. */
+typedef struct {
+    int32_t score;
+    int32_t q_start;
+    int32_t q_end;
+    int32_t r_start;
+    int32_t r_end;
+} swgb_record;
+
+/* Scoring parameters.
+ *   matrix:     host pointer to 24 x 24 int8, row = query code, column =
+ *               reference code (need not be symmetric).  Read during the call.
+ *   gap_open:   o >= 0;  gap_extend: e >= 1.  The 8-bit query profile holds
+ *               s + o + e, so max(matrix) + o + e must be <= 127.
+ *   flags:      SWGB_FORCE_INT32 | SWGB_TIMING. */
+typedef struct {
+    const int8_t* matrix;
+    int32_t gap_open;
+    int32_t gap_extend;
+    uint32_t flags;
+} swgb_params;
+
+/* Counters of the last completed call on a context (see swgb_last_stats). */
+typedef struct {
+    int64_t n_pairs;         /* pairs in the call */
+    int64_t n_int16_pairs;   /* forward pass on the packed 16x2 path */
+    int64_t n_int32_pairs;   /* forward pass on the 32-bit path */
+    int64_t n_reverse_pairs; /* pairs with score > 0 (reverse pass run) */
+    int64_t forward_cells;   /* sum of lq * lr over the pairs */
+    int64_t reverse_cells;   /* sum of (q_end + 1) * (r_end + 1) over scored pairs */
+    float forward_ms;        /* forward DP kernels, CUDA events (SWGB_TIMING), else -1 */
+    float reverse_ms;        /* reverse DP kernels, CUDA events (SWGB_TIMING), else -1 */
+    float total_ms;          /* whole call on the stream (SWGB_TIMING), else -1 */
+    int32_t kernel_launches; /* kernels the call launched */
+} swgb_stats;
+
+/* Creates a context on CUDA device `device` (made current on the calling
+ * thread).  *out receives the context; the caller destroys it.
+ * Errors: EINVAL (out NULL), ECUDA (no such device / CUDA failure), ENOMEM. */
+int swgb_create(int device, swgb_ctx** out);
+
+/* Frees the context and all its device scratch.  NULL is ignored. */
+void swgb_destroy(swgb_ctx* ctx);
+
+/* Message of the last failing call on ctx (empty string if none).  The
+ * pointer stays valid until the next call on ctx. */
+const char* swgb_last_error(const swgb_ctx* ctx);
+
+/* Copies the library's BLOSUM62 (24 x 24 int8, row = query) into out[576]. */
+void swgb_blosum62(int8_t* out);
+
+/* Creates a sequence set on ctx's device from n_seqs sequences: sequence k is
+ * residues[offsets[k] .. offsets[k+1]) (offsets has n_seqs + 1 entries,
+ * non-decreasing, offsets[0] = 0 is not required).  flags: SWGB_SEQ_ASCII,
+ * SWGB_SEQ_DEVICE.  The data are copied (and encoded) into library-owned
+ * device memory on `stream` (a cudaStream_t, NULL = legacy default); the call
+ * returns after the copy has completed, so the inputs may be reused.
+ * Errors: EINVAL, ERANGE (a sequence longer than SWGB_MAX_LENGTH, or offsets
+ * decreasing), EBADRES (a letter/code outside the alphabet), ENOMEM, ECUDA. */
+int swgb_seqset_create(swgb_ctx* ctx, const void* residues, const int64_t* offsets,
+                       int64_t n_seqs, uint32_t flags, void* stream, swgb_seqset** out);
+
+/* Replaces the content of an existing set (same rules as create); device
+ * memory is reused when it is large enough. */
+int swgb_seqset_load(swgb_seqset* set, const void* residues, const int64_t* offsets,
+                     int64_t n_seqs, uint32_t flags, void* stream);
+
+/* Number of sequences and longest length of a set. */
+int swgb_seqset_info(const swgb_seqset* set, int64_t* n_seqs, int64_t* max_length);
+
+/* Frees a sequence set.  NULL is ignored. */
+void swgb_seqset_destroy(swgb_seqset* set);
+
+/* Aligns n_pairs candidate pairs.  pairs: device int32 [n_pairs][2] =
+ * (query index into `queries`, reference index into `refs`); out: device
+ * swgb_record [n_pairs], written in pair order.  Both buffers are caller-owned
+ * and must stay valid until the stream reaches the end of the call.  refs may
+ * equal queries (one set against itself).  Asynchronous on `stream`: returns
+ * after enqueueing; argument errors (EINVAL) are returned immediately, errors
+ * found on the device (ERANGE for a pair index out of range, whose record is
+ * written as zero score) are returned by swgb_sync.  Device scratch is grown
+ * on demand by this call (it may allocate).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int swgb_align(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+               const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+               swgb_record* out, void* stream);
+
+/* Same as swgb_align with HOST pairs and HOST out: copies the pairs to the
+ * device, aligns, copies the records back and waits for the stream.  Pinned
+ * host buffers give asynchronous copies.  Returns the device status too. */
+int swgb_align_host(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                    const int32_t* pairs_host, int64_t n_pairs, const swgb_params* params,
+                    swgb_record* out_host, void* stream);
+
+/* Waits for `stream`, then returns (and clears) the device-side status of the
+ * calls issued on ctx: SWGB_OK, ERANGE or EINTERNAL; ECUDA if the stream
+ * failed. */
+int swgb_sync(swgb_ctx* ctx, void* stream);
+
+/* Counters and (with SWGB_TIMING) kernel times of the last call; waits for
+ * that call's stream.  Errors: EINVAL, ECUDA. */
+int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out);
+
+/* Measures the issue rate of the packed 16x2 add-max instruction the forward
+ * kernel is built on: *ops_per_clk_per_sm = instructions retired per SM clock
+ * per SM, from a kernel of independent chains timed with the SM cycle
+ * counter.  Also reports the SM count.  Synchronous.  Errors: EINVAL, ECUDA. */
+int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_H */

@@ -1,0 +1,519 @@
+// swgb_api.cu -- host side of the C ABI declared in include/swgb.h.
+//
+// Owns contexts (device workspace, events, the last call's counters) and
+// sequence sets (encoded residues + offsets in device memory), validates
+// arguments, and enqueues the per-call pipeline on the caller's stream:
+//
+//   keys (forward)  -> scan -> scatter -> DP forward  x (2 classes x 5 shapes)
+//   keys (reverse)  -> scan -> scatter -> DP reverse  x (2 classes x 5 shapes)
+//
+// Every step runs in the kernels of swgb_kernels.cu; the host never touches
+// pair data.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "swgb_internal.cuh"
+
+#define SWGB_EXPORT extern "C" __attribute__((visibility("default")))
+
+using namespace swgb;
+
+// The library's BLOSUM62 (Henikoff & Henikoff, PNAS 89:10915, 1992) in the
+// NCBI letter order A R N D C Q E G H I L K M F P S T W Y V B Z X *, as text
+// rows of the published integer matrix.
+static const char* kBlosum62Rows[kAlpha] = {
+    " 4 -1 -2 -2  0 -1 -1  0 -2 -1 -1 -1 -1 -2 -1  1  0 -3 -2  0 -2 -1  0 -4",
+    "-1  5  0 -2 -3  1  0 -2  0 -3 -2  2 -1 -3 -2 -1 -1 -3 -2 -3 -1  0 -1 -4",
+    "-2  0  6  1 -3  0  0  0  1 -3 -3  0 -2 -3 -2  1  0 -4 -2 -3  3  0 -1 -4",
+    "-2 -2  1  6 -3  0  2 -1 -1 -3 -4 -1 -3 -3 -1  0 -1 -4 -3 -3  4  1 -1 -4",
+    " 0 -3 -3 -3  9 -3 -4 -3 -3 -1 -1 -3 -1 -2 -3 -1 -1 -2 -2 -1 -3 -3 -2 -4",
+    "-1  1  0  0 -3  5  2 -2  0 -3 -2  1  0 -3 -1  0 -1 -2 -1 -2  0  3 -1 -4",
+    "-1  0  0  2 -4  2  5 -2  0 -3 -3  1 -2 -3 -1  0 -1 -3 -2 -2  1  4 -1 -4",
+    " 0 -2  0 -1 -3 -2 -2  6 -2 -4 -4 -2 -3 -3 -2  0 -2 -2 -3 -3 -1 -2 -1 -4",
+    "-2  0  1 -1 -3  0  0 -2  8 -3 -3 -1 -2 -1 -2 -1 -2 -2  2 -3  0  0 -1 -4",
+    "-1 -3 -3 -3 -1 -3 -3 -4 -3  4  2 -3  1  0 -3 -2 -1 -3 -1  3 -3 -3 -1 -4",
+    "-1 -2 -3 -4 -1 -2 -3 -4 -3  2  4 -2  2  0 -3 -2 -1 -2 -1  1 -4 -3 -1 -4",
+    "-1  2  0 -1 -3  1  1 -2 -1 -3 -2  5 -1 -3 -1  0 -1 -3 -2 -2  0  1 -1 -4",
+    "-1 -1 -2 -3 -1  0 -2 -3 -2  1  2 -1  5  0 -2 -1 -1 -1 -1  1 -3 -1 -1 -4",
+    "-2 -3 -3 -3 -2 -3 -3 -3 -1  0  0 -3  0  6 -4 -2 -2  1  3 -1 -3 -3 -1 -4",
+    "-1 -2 -2 -1 -3 -1 -1 -2 -2 -3 -3 -1 -2 -4  7 -1 -1 -4 -3 -2 -2 -1 -2 -4",
+    " 1 -1  1  0 -1  0  0  0 -1 -2 -2  0 -1 -2 -1  4  1 -3 -2 -2  0  0  0 -4",
+    " 0 -1  0 -1 -1 -1 -1 -2 -2 -1 -1 -1 -1 -2 -1  1  5 -2 -2  0 -1 -1  0 -4",
+    "-3 -3 -4 -4 -2 -2 -3 -2 -2 -3 -2 -3 -1  1 -4 -3 -2 11  2 -3 -4 -3 -2 -4",
+    "-2 -2 -2 -3 -2 -1 -2 -3  2 -1 -1 -2 -1  3 -3 -2 -2  2  7 -1 -3 -2 -1 -4",
+    " 0 -3 -3 -3 -1 -2 -2 -3 -3  3  1 -2  1 -1 -2 -2  0 -3 -1  4 -3 -2 -1 -4",
+    "-2 -1  3  4 -3  0  1 -1  0 -3 -4  0 -3 -3 -2  0 -1 -4 -3 -3  4  1 -1 -4",
+    "-1  0  0  1 -3  3  4 -2  0 -3 -3  1 -1 -3 -1  0 -1 -3 -2 -2  1  4 -1 -4",
+    " 0 -1 -1 -1 -2 -1 -1 -1 -1 -1 -1 -1 -1 -1 -2  0  0 -2 -1 -1 -1 -1 -1 -4",
+    "-4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4  1",
+};
+
+struct swgb_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    Workspace ws{};
+    int64_t bin_capacity = 0;        // ws.bin_of
+    int64_t order_capacity = 0;      // ws.order
+    int32_t* d_pairs = nullptr;      // staging for swgb_align_host
+    swgb_record* d_out = nullptr;
+    int64_t d_pairs_capacity = 0;
+    int64_t d_out_capacity = 0;
+    int32_t* d_encode_flag = nullptr;  // residue check of seqset loads
+    int blocks_per_sm[2][kClasses][kNumShapes] = {};
+    cudaEvent_t ev[6] = {};
+    bool timed = false;
+    cudaStream_t last_stream = nullptr;
+    int32_t last_launches = 0;
+    int64_t last_pairs = 0;
+    unsigned long long* d_probe_cycles = nullptr;
+    uint32_t* d_probe_sink = nullptr;
+};
+
+struct swgb_seqset {
+    swgb_ctx* ctx = nullptr;
+    int device = 0;
+    uint8_t* d_res = nullptr;
+    int64_t* d_off = nullptr;
+    int64_t res_capacity = 0;
+    int64_t off_capacity = 0;
+    int64_t n = 0;
+    int64_t total = 0;
+    int64_t max_len = 0;
+};
+
+namespace {
+
+int fail(swgb_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(swgb_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, SWGB_ENOMEM, m);
+    return fail(ctx, SWGB_ECUDA, m);
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t grow(T** p, int64_t* cap, int64_t need) {
+    if (need <= *cap && *p) return cudaSuccess;
+    int64_t n = std::max<int64_t>(need, *cap * 3 / 2);
+    if (n < 1) n = 1;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+SeqView view(const swgb_seqset* s) { return SeqView{s->d_res, s->d_off, s->n}; }
+
+}  // namespace
+
+SWGB_EXPORT void swgb_blosum62(int8_t* out) {
+    if (!out) return;
+    for (int x = 0; x < kAlpha; ++x) {
+        const char* p = kBlosum62Rows[x];
+        for (int y = 0; y < kAlpha; ++y) {
+            char* end = nullptr;
+            long v = std::strtol(p, &end, 10);
+            out[x * kAlpha + y] = (int8_t)v;
+            p = end;
+        }
+    }
+}
+
+SWGB_EXPORT const char* swgb_last_error(const swgb_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
+    if (!out) return SWGB_EINVAL;
+    *out = nullptr;
+    swgb_ctx* ctx = new (std::nothrow) swgb_ctx();
+    if (!ctx) return SWGB_ENOMEM;
+    ctx->device = device;
+    auto bail = [&](cudaError_t e, const char* what) {
+        int rc = cuda_fail(ctx, e, what);
+        fprintf(stderr, "swgb_create: %s\n", ctx->err.c_str());
+        swgb_destroy(ctx);
+        return rc;
+    };
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return bail(e, "cudaSetDevice");
+    e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return bail(e, "cudaDeviceGetAttribute");
+    Workspace& ws = ctx->ws;
+    if ((e = cudaMalloc(&ws.hist, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.scan, sizeof(uint32_t) * (kNumBins + 1))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.status, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ctx->d_encode_flag, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMemset(ws.status, 0, sizeof(int32_t))) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemset(ws.counters, 0, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "memset");
+    for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < kClasses; ++c)
+            for (int s = 0; s < kNumShapes; ++s) {
+                if ((e = dp_configure(c, s, d == 1)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+                ctx->blocks_per_sm[d][c][s] = std::max(1, dp_blocks_per_sm(c, s, d == 1));
+            }
+    for (auto& ev : ctx->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "cudaEventCreate");
+    *out = ctx;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    Workspace& ws = ctx->ws;
+    cudaFree(ws.hist);
+    cudaFree(ws.scan);
+    cudaFree(ws.cursor);
+    cudaFree(ws.bin_of);
+    cudaFree(ws.order);
+    cudaFree(ws.task_ctr);
+    cudaFree(ws.status);
+    cudaFree(ws.counters);
+    cudaFree(ws.boundary);
+    cudaFree(ctx->d_pairs);
+    cudaFree(ctx->d_out);
+    cudaFree(ctx->d_encode_flag);
+    cudaFree(ctx->d_probe_cycles);
+    cudaFree(ctx->d_probe_sink);
+    for (auto& ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// Sequence sets
+// ---------------------------------------------------------------------------
+SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const int64_t* offsets,
+                                 int64_t n_seqs, uint32_t flags, void* stream) {
+    if (!set || !set->ctx) return SWGB_EINVAL;
+    swgb_ctx* ctx = set->ctx;
+    if (n_seqs < 0 || (flags & ~(SWGB_SEQ_ASCII | SWGB_SEQ_DEVICE)))
+        return fail(ctx, SWGB_EINVAL, "seqset: negative count or unknown flags");
+    if (n_seqs > 0 && !offsets) return fail(ctx, SWGB_EINVAL, "seqset: offsets is NULL");
+    if (n_seqs > INT32_MAX) return fail(ctx, SWGB_ERANGE, "seqset: more than 2^31-1 sequences");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool on_dev = flags & SWGB_SEQ_DEVICE;
+
+    std::vector<int64_t> off((size_t)n_seqs + 1, 0);
+    if (n_seqs > 0) {
+        if (on_dev) {
+            CK(cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * (n_seqs + 1),
+                               cudaMemcpyDeviceToHost, st), "offsets D2H");
+            CK(cudaStreamSynchronize(st), "stream sync");
+        } else {
+            std::memcpy(off.data(), offsets, sizeof(int64_t) * (n_seqs + 1));
+        }
+    }
+    const int64_t base = off[0];
+    int64_t max_len = 0;
+    for (int64_t k = 0; k < n_seqs; ++k) {
+        const int64_t len = off[k + 1] - off[k];
+        if (len < 0) return fail(ctx, SWGB_ERANGE, "seqset: offsets decrease");
+        if (len > SWGB_MAX_LENGTH) return fail(ctx, SWGB_ERANGE, "seqset: sequence longer than SWGB_MAX_LENGTH");
+        max_len = std::max(max_len, len);
+    }
+    for (auto& v : off) v -= base;
+    const int64_t total = off[(size_t)n_seqs];
+    if (total > 0 && !residues) return fail(ctx, SWGB_EINVAL, "seqset: residues is NULL");
+
+    CK(grow(&set->d_res, &set->res_capacity, std::max<int64_t>(total, 1)), "seqset alloc");
+    CK(grow(&set->d_off, &set->off_capacity, n_seqs + 1), "seqset alloc");
+    CK(cudaMemcpyAsync(set->d_off, off.data(), sizeof(int64_t) * (n_seqs + 1),
+                       cudaMemcpyHostToDevice, st), "offsets H2D");
+    const uint8_t* src = static_cast<const uint8_t*>(residues);
+    if (total > 0) {
+        if (on_dev) {
+            src += base;
+        } else {
+            CK(cudaMemcpyAsync(set->d_res, src + base, (size_t)total, cudaMemcpyHostToDevice, st),
+               "residues H2D");
+            src = set->d_res;   // encode in place
+        }
+    }
+    CK(cudaMemsetAsync(ctx->d_encode_flag, 0, sizeof(int32_t), st), "memset");
+    CK(launch_encode(src, set->d_res, total, flags & SWGB_SEQ_ASCII, ctx->d_encode_flag, st), "encode kernel");
+    int32_t bad = 0;
+    CK(cudaMemcpyAsync(&bad, ctx->d_encode_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "flag D2H");
+    CK(cudaStreamSynchronize(st), "stream sync");
+    set->n = n_seqs;
+    set->total = total;
+    set->max_len = max_len;
+    if (bad) return fail(ctx, SWGB_EBADRES, "seqset: residue outside the alphabet");
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_seqset_create(swgb_ctx* ctx, const void* residues, const int64_t* offsets,
+                                   int64_t n_seqs, uint32_t flags, void* stream, swgb_seqset** out) {
+    if (!ctx || !out) return SWGB_EINVAL;
+    *out = nullptr;
+    swgb_seqset* s = new (std::nothrow) swgb_seqset();
+    if (!s) return fail(ctx, SWGB_ENOMEM, "seqset: host allocation");
+    s->ctx = ctx;
+    s->device = ctx->device;
+    int rc = swgb_seqset_load(s, residues, offsets, n_seqs, flags, stream);
+    if (rc != SWGB_OK) {
+        swgb_seqset_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_seqset_info(const swgb_seqset* set, int64_t* n_seqs, int64_t* max_length) {
+    if (!set) return SWGB_EINVAL;
+    if (n_seqs) *n_seqs = set->n;
+    if (max_length) *max_length = set->max_len;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT void swgb_seqset_destroy(swgb_seqset* set) {
+    if (!set) return;
+    cudaSetDevice(set->device);
+    cudaFree(set->d_res);
+    cudaFree(set->d_off);
+    delete set;
+}
+
+// ---------------------------------------------------------------------------
+// Alignment
+// ---------------------------------------------------------------------------
+namespace {
+
+int make_score_args(swgb_ctx* ctx, const swgb_params* params, ScoreArgs* sc, int* max_score) {
+    if (!params || !params->matrix) return fail(ctx, SWGB_EINVAL, "params or matrix is NULL");
+    if (params->gap_open < 0 || params->gap_extend < 1)
+        return fail(ctx, SWGB_EINVAL, "gap_open must be >= 0 and gap_extend >= 1");
+    if (params->flags & ~(SWGB_FORCE_INT32 | SWGB_TIMING))
+        return fail(ctx, SWGB_EINVAL, "unknown params flags");
+    const int oe = params->gap_open + params->gap_extend;
+    int mx = 0;
+    for (int k = 0; k < kAlpha * kAlpha; ++k) mx = std::max<int>(mx, params->matrix[k]);
+    if (oe > 127 || mx + oe > 127)
+        return fail(ctx, SWGB_EINVAL, "max(matrix) + gap_open + gap_extend must be <= 127");
+    for (int x = 0; x < kProfileRows; ++x)
+        for (int y = 0; y < kMatStride; ++y) {
+            int v = kPadProfile;
+            if (x < kAlpha && y < kAlpha) v = params->matrix[x * kAlpha + y] + oe;
+            sc->prof[x][y] = (int8_t)v;
+        }
+    sc->go = params->gap_open;
+    sc->ge = params->gap_extend;
+    *max_score = mx;
+    return SWGB_OK;
+}
+
+// Pairs handled by one persistent block of a (class, shape) kernel.
+int64_t pairs_per_block(int cls, int shape) {
+    return (int64_t)(kDPThreads / 32) * (32 / kShapeG[shape]) * (cls == 0 ? 2 : 1);
+}
+
+int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int32_t* pairs,
+            int64_t n_pairs, const swgb_params* params, swgb_record* out, cudaStream_t st) {
+    ScoreArgs sc;
+    int max_score = 0;
+    int rc = make_score_args(ctx, params, &sc, &max_score);
+    if (rc) return rc;
+    Workspace& ws = ctx->ws;
+    const bool force32 = params->flags & SWGB_FORCE_INT32;
+    const bool timed = params->flags & SWGB_TIMING;
+    CK(grow(&ws.bin_of, &ctx->bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
+    CK(grow(&ws.order, &ctx->order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
+    // chunk-boundary rows for the chunked shape: one row per resident warp
+    {
+        const int64_t stride = ((q->max_len + 31) / 32) * 32;
+        int64_t slots = 0;
+        for (int d = 0; d < 2; ++d)
+            for (int c = 0; c < kClasses; ++c)
+                slots = std::max<int64_t>(slots, (int64_t)ctx->sm_count *
+                                                     ctx->blocks_per_sm[d][c][kNumShapes - 1] *
+                                                     (kDPThreads / 32));
+        if (stride > ws.boundary_stride || slots > ws.boundary_slots || !ws.boundary) {
+            cudaFree(ws.boundary);
+            ws.boundary = nullptr;
+            ws.boundary_stride = ws.boundary_slots = 0;
+            CK(cudaMalloc(&ws.boundary, sizeof(uint2) * (size_t)std::max<int64_t>(stride, 32) * slots),
+               "boundary alloc");
+            ws.boundary_stride = std::max<int64_t>(stride, 32);
+            ws.boundary_slots = slots;
+        }
+    }
+
+    int launches = 0;
+    CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
+    CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * 2 * kNumKernels, st), "memset");
+    if (timed) CK(cudaEventRecord(ctx->ev[0], st), "event");
+
+    const SeqView qv = view(q), rv = view(r);
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool rev = dir == 1;
+        CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st), "memset");
+        CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, force32, max_score, ws, st), "keys kernel");
+        CK(launch_scan(ws, st), "scan kernel");
+        CK(launch_scatter(n_pairs, ws, st), "scatter kernel");
+        launches += 3;
+        if (timed) CK(cudaEventRecord(ctx->ev[rev ? 3 : 1], st), "event");
+        for (int c = 0; c < kClasses; ++c) {
+            for (int s = 0; s < kNumShapes; ++s) {
+                DPArgs a;
+                a.q = qv;
+                a.r = rv;
+                a.pairs = pairs;
+                a.order = ws.order;
+                a.scan = ws.scan;
+                a.task_ctr = ws.task_ctr + dir * kNumKernels + c * kNumShapes + s;
+                a.out = out;
+                a.status = ws.status;
+                a.boundary = ws.boundary;
+                a.boundary_stride = ws.boundary_stride;
+                a.boundary_slots = ws.boundary_slots;
+                a.first_bucket = shape_first_bucket(c, s);
+                a.end_bucket = shape_end_bucket(c, s);
+                a.sc = sc;
+                int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[dir][c][s];
+                const int64_t need = (n_pairs + pairs_per_block(c, s) - 1) / pairs_per_block(c, s);
+                grid = std::max<int64_t>(1, std::min(grid, need));
+                CK(launch_dp(c, s, rev, a, (int)grid, st), "dp kernel");
+                ++launches;
+            }
+        }
+        if (timed) CK(cudaEventRecord(ctx->ev[rev ? 4 : 2], st), "event");
+    }
+    if (timed) CK(cudaEventRecord(ctx->ev[5], st), "event");
+    ctx->timed = timed;
+    ctx->last_stream = st;
+    ctx->last_launches = launches;
+    ctx->last_pairs = n_pairs;
+    return SWGB_OK;
+}
+
+int check_sets(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r) {
+    if (!q || !r) return fail(ctx, SWGB_EINVAL, "sequence set is NULL");
+    if (q->ctx != ctx || r->ctx != ctx) return fail(ctx, SWGB_EINVAL, "sequence set of another context");
+    return SWGB_OK;
+}
+
+}  // namespace
+
+SWGB_EXPORT int swgb_align(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                           const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                           swgb_record* out, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    ctx->err.clear();
+    if (n_pairs < 0) return fail(ctx, SWGB_EINVAL, "n_pairs < 0");
+    if (n_pairs > INT32_MAX) return fail(ctx, SWGB_EINVAL, "n_pairs > 2^31-1");
+    if (n_pairs > 0 && (!pairs || !out)) return fail(ctx, SWGB_EINVAL, "pairs or out is NULL");
+    int rc = check_sets(ctx, queries, refs);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (n_pairs == 0) {
+        ctx->last_pairs = 0;
+        ctx->last_launches = 0;
+        ctx->timed = false;
+        ctx->last_stream = (cudaStream_t)stream;
+        CK(cudaMemsetAsync(ctx->ws.counters, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream), "memset");
+        return SWGB_OK;
+    }
+    return enqueue(ctx, queries, refs, pairs, n_pairs, params, out, (cudaStream_t)stream);
+}
+
+SWGB_EXPORT int swgb_sync(swgb_ctx* ctx, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st), "stream sync");
+    int32_t status = 0;
+    CK(cudaMemcpy(&status, ctx->ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost), "status D2H");
+    CK(cudaMemset(ctx->ws.status, 0, sizeof(int32_t)), "memset");
+    if (status == SWGB_ERANGE) return fail(ctx, SWGB_ERANGE, "a pair index is outside its sequence set");
+    if (status != 0) return fail(ctx, status, "device reported an internal inconsistency");
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_align_host(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                                const int32_t* pairs_host, int64_t n_pairs, const swgb_params* params,
+                                swgb_record* out_host, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    ctx->err.clear();
+    if (n_pairs < 0) return fail(ctx, SWGB_EINVAL, "n_pairs < 0");
+    if (n_pairs > 0 && (!pairs_host || !out_host)) return fail(ctx, SWGB_EINVAL, "pairs or out is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(grow(&ctx->d_pairs, &ctx->d_pairs_capacity, std::max<int64_t>(2 * n_pairs, 2)), "staging alloc");
+    CK(grow(&ctx->d_out, &ctx->d_out_capacity, std::max<int64_t>(n_pairs, 1)), "staging alloc");
+    if (n_pairs > 0)
+        CK(cudaMemcpyAsync(ctx->d_pairs, pairs_host, sizeof(int32_t) * 2 * n_pairs,
+                           cudaMemcpyHostToDevice, st), "pairs H2D");
+    int rc = swgb_align(ctx, queries, refs, ctx->d_pairs, n_pairs, params, ctx->d_out, stream);
+    if (rc) return rc;
+    if (n_pairs > 0)
+        CK(cudaMemcpyAsync(out_host, ctx->d_out, sizeof(swgb_record) * n_pairs,
+                           cudaMemcpyDeviceToHost, st), "records D2H");
+    return swgb_sync(ctx, stream);
+}
+
+SWGB_EXPORT int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out) {
+    if (!ctx || !out) return SWGB_EINVAL;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(ctx->last_stream), "stream sync");
+    unsigned long long c[8];
+    CK(cudaMemcpy(c, ctx->ws.counters, sizeof(c), cudaMemcpyDeviceToHost), "counters D2H");
+    std::memset(out, 0, sizeof(*out));
+    out->n_pairs = ctx->last_pairs;
+    out->forward_cells = (int64_t)c[kCtrFwdCells];
+    out->reverse_cells = (int64_t)c[kCtrRevCells];
+    out->n_int16_pairs = (int64_t)c[kCtrInt16];
+    out->n_int32_pairs = (int64_t)c[kCtrInt32];
+    out->n_reverse_pairs = (int64_t)c[kCtrRevPairs];
+    out->forward_ms = out->reverse_ms = out->total_ms = -1.0f;
+    if (ctx->timed) {
+        CK(cudaEventElapsedTime(&out->forward_ms, ctx->ev[1], ctx->ev[2]), "event time");
+        CK(cudaEventElapsedTime(&out->reverse_ms, ctx->ev[3], ctx->ev[4]), "event time");
+        CK(cudaEventElapsedTime(&out->total_ms, ctx->ev[0], ctx->ev[5]), "event time");
+    }
+    out->kernel_launches = ctx->last_launches;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_count) {
+    if (!ctx || !ops_per_clk_per_sm) return SWGB_EINVAL;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int per_sm = 4;   // 4 x 256 threads resident per SM
+    const int blocks = ctx->sm_count * per_sm;
+    const int iters = 1 << 16;
+    if (!ctx->d_probe_cycles) {
+        CK(cudaMalloc(&ctx->d_probe_cycles, sizeof(unsigned long long) * blocks), "probe alloc");
+        CK(cudaMalloc(&ctx->d_probe_sink, sizeof(uint32_t) * blocks * kProbeThreads), "probe alloc");
+    }
+    CK(launch_probe_addmax(ctx->d_probe_cycles, ctx->d_probe_sink, blocks, iters / 16, 0), "probe");
+    CK(launch_probe_addmax(ctx->d_probe_cycles, ctx->d_probe_sink, blocks, iters, 0), "probe");
+    CK(cudaDeviceSynchronize(), "probe sync");
+    std::vector<unsigned long long> cyc(blocks);
+    CK(cudaMemcpy(cyc.data(), ctx->d_probe_cycles, sizeof(unsigned long long) * blocks,
+                  cudaMemcpyDeviceToHost), "probe D2H");
+    unsigned long long mx = 1;
+    for (auto v : cyc) mx = std::max(mx, v);
+    const double ops_per_sm = (double)per_sm * kProbeThreads * kProbeChains * (double)iters;
+    *ops_per_clk_per_sm = ops_per_sm / (double)mx;
+    if (sm_count) *sm_count = ctx->sm_count;
+    return SWGB_OK;
+}

@@ -1,0 +1,652 @@
+// swgb_kernels.cu -- sm_103a kernels of libswgb.
+//
+// The hot kernel is dp_kernel: the affine-gap local-alignment recurrence of
+// include/swgb.h evaluated over whole score matrices (the paper's alignment
+// step; cell updates of the forward pass are its CUPS metric, Sec. "How
+// Performance Was Measured").  Layout of one pair group:
+//
+//   * the reference ("held" sequence) is cut into chunks of G*R rows; lane k
+//     of a group of G lanes holds rows [k*R, k*R+R) of the chunk in registers;
+//   * the query is streamed: at step t lane k updates query position
+//     i = t - k, so the lanes form an anti-diagonal wavefront and each lane
+//     receives the values of the row above its first row from lane k-1 by a
+//     warp shuffle (the previous step's output of that lane);
+//   * on the packed path every register holds two independent pairs (low and
+//     high 16 bits) and every cell update is five __viaddmax_s16x2 (dual
+//     add-then-max) instructions;  pairs whose score could pass 32767 run the
+//     same code on 32-bit registers;
+//   * substitution scores come from a per-pair profile in shared memory,
+//     prof[query code][held row] = s + o + e (8-bit), read as R bytes per
+//     lane per step and widened by one byte-permute per register.
+//
+// Work distribution: pairs are bucketed on the device by held length (tile
+// shape) and sorted by query length (longest first); one persistent launch per
+// (precision class, tile shape) pulls pair groups from an atomic counter.
+#include <climits>
+#include <cstdint>
+
+#include "swgb_internal.cuh"
+
+namespace swgb {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Residue encoding (ASCII letters or codes -> codes 0..23)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint8_t ascii_code(int c) {
+    if (c >= 'a' && c <= 'z') c -= 'a' - 'A';
+    switch (c) {
+        case 'A': return 0;  case 'R': return 1;  case 'N': return 2;  case 'D': return 3;
+        case 'C': return 4;  case 'Q': return 5;  case 'E': return 6;  case 'G': return 7;
+        case 'H': return 8;  case 'I': return 9;  case 'L': return 10; case 'K': return 11;
+        case 'M': return 12; case 'F': return 13; case 'P': return 14; case 'S': return 15;
+        case 'T': return 16; case 'W': return 17; case 'Y': return 18; case 'V': return 19;
+        case 'B': return 20; case 'Z': return 21; case 'X': return 22; case '*': return 23;
+        case 'U': case 'O': return 22;
+        default: return 255;
+    }
+}
+
+__global__ void encode_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                              int64_t n, int ascii, int32_t* bad) {
+    __shared__ uint8_t tab[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x)
+        tab[k] = ascii ? ascii_code(k) : (k < kAlpha ? (uint8_t)k : (uint8_t)255);
+    __syncthreads();
+    int any_bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        uint8_t c = tab[in[k]];
+        if (c == 255) {
+            any_bad = 1;
+            c = 0;
+        }
+        out[k] = c;
+    }
+    if (__syncthreads_or(any_bad) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
+                          int32_t* bad_flag, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, n, ascii ? 1 : 0, bad_flag);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Bucketing: keys + histogram, scan, scatter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void zero_record(swgb_record* r) {
+    *r = swgb_record{0, -1, -1, -1, -1};
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+__global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pairs,
+                            int64_t n_pairs, swgb_record* out, int reverse, int force32,
+                            int max_score, Workspace ws) {
+    unsigned long long cells = 0, n16 = 0, n32 = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += stride) {
+        int bin = -1;
+        int64_t lq = 0, lr = 0;
+        if (!reverse) {
+            const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
+            if (qi < 0 || qi >= q.n || ri < 0 || ri >= r.n) {
+                set_status(ws.status, SWGB_ERANGE);
+                zero_record(&out[p]);
+            } else {
+                lq = q.off[qi + 1] - q.off[qi];
+                lr = r.off[ri + 1] - r.off[ri];
+                if (lq == 0 || lr == 0) {
+                    zero_record(&out[p]);
+                    lq = lr = 0;
+                }
+            }
+        } else {
+            const swgb_record rec = out[p];
+            if (rec.score > 0) {
+                lq = (int64_t)rec.q_end + 1;
+                lr = (int64_t)rec.r_end + 1;
+            }
+        }
+        if (lq > 0) {
+            const int64_t mn = lq < lr ? lq : lr;
+            const int cls = (!force32 && (int64_t)max_score * mn <= 32767) ? 0 : 1;
+            int64_t qb = lq >> kQBinShift;
+            if (qb > kQBins - 1) qb = kQBins - 1;
+            bin = bucket_of(cls, lr) * kQBins + (kQBins - 1 - (int)qb);
+            atomicAdd(&ws.hist[bin], 1u);
+            cells += (unsigned long long)(lq * lr);
+            if (cls == 0) ++n16; else ++n32;
+        }
+        ws.bin_of[p] = bin;
+    }
+    // block reduction of the counters
+    for (int off = 16; off > 0; off >>= 1) {
+        cells += __shfl_xor_sync(kFull, cells, off);
+        n16 += __shfl_xor_sync(kFull, n16, off);
+        n32 += __shfl_xor_sync(kFull, n32, off);
+    }
+    if ((threadIdx.x & 31) == 0 && (cells | n16 | n32)) {
+        if (!reverse) {
+            atomicAdd(&ws.counters[kCtrFwdCells], cells);
+            atomicAdd(&ws.counters[kCtrInt16], n16);
+            atomicAdd(&ws.counters[kCtrInt32], n32);
+        } else {
+            atomicAdd(&ws.counters[kCtrRevCells], cells);
+            atomicAdd(&ws.counters[kCtrRevPairs], n16 + n32);
+        }
+    }
+}
+
+cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
+                        swgb_record* out, bool reverse, bool force32, int max_score,
+                        const Workspace& ws, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    int64_t blocks = (n_pairs + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, reverse ? 1 : 0,
+                                                  force32 ? 1 : 0, max_score, ws);
+    return cudaGetLastError();
+}
+
+// Exclusive scan of hist[kNumBins] by one block; also resets the cursors.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = (kNumBins + kScanThreads - 1) / kScanThreads;
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(Workspace ws) {
+    __shared__ uint32_t part[kScanThreads];
+    const int t = threadIdx.x;
+    const int base = t * kScanPer;
+    uint32_t local = 0;
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < kNumBins) local += ws.hist[base + k];
+    part[t] = local;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        uint32_t v = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - local;  // exclusive prefix of this thread's span
+    for (int k = 0; k < kScanPer; ++k) {
+        const int b = base + k;
+        if (b < kNumBins) {
+            ws.scan[b] = run;
+            ws.cursor[b] = run;
+            run += ws.hist[b];
+        }
+    }
+    if (t == kScanThreads - 1) ws.scan[kNumBins] = part[t];
+}
+
+cudaError_t launch_scan(const Workspace& ws, cudaStream_t st) {
+    scan_kernel<<<1, kScanThreads, 0, st>>>(ws);
+    return cudaGetLastError();
+}
+
+__global__ void scatter_kernel(int64_t n_pairs, Workspace ws) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += stride) {
+        const int bin = ws.bin_of[p];
+        if (bin >= 0) {
+            const uint32_t pos = atomicAdd(&ws.cursor[bin], 1u);
+            ws.order[pos] = (int32_t)p;
+        }
+    }
+}
+
+cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    int64_t blocks = (n_pairs + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_pairs, ws);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Lane arithmetic: packed 16x2 (two pairs per register) or 32-bit
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+template <bool P16>
+struct Lane;
+
+template <>
+struct Lane<true> {
+    static constexpr int kPack = 2;
+    __device__ __forceinline__ static uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
+        return __viaddmax_s16x2(a, b, c);
+    }
+    __device__ __forceinline__ static uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
+        return __vimax3_s16x2(a, b, c);
+    }
+    __device__ __forceinline__ static uint32_t splat(int v) {
+        return ((uint32_t)v & 0xffffu) * 0x10001u;
+    }
+    __device__ __forceinline__ static int get(uint32_t w, int h) {
+        return h ? (int)(int16_t)(w >> 16) : (int)(int16_t)(w & 0xffffu);
+    }
+    // score of row b (0..3) of the word pair: low half from a (pair 0),
+    // high half from c (pair 1), each byte sign-extended to 16 bits
+    __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t c, int b) {
+        const uint32_t sel = (uint32_t)b | ((uint32_t)(b | 8) << 4) | ((uint32_t)(4 + b) << 8) |
+                             ((uint32_t)((4 + b) | 8) << 12);
+        return prmt(a, c, sel);
+    }
+};
+
+template <>
+struct Lane<false> {
+    static constexpr int kPack = 1;
+    __device__ __forceinline__ static uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
+        return (uint32_t)__viaddmax_s32((int)a, (int)b, (int)c);
+    }
+    __device__ __forceinline__ static uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
+        return (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
+    }
+    __device__ __forceinline__ static uint32_t splat(int v) { return (uint32_t)v; }
+    __device__ __forceinline__ static int get(uint32_t w, int) { return (int)w; }
+    __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t, int b) {
+        const uint32_t s = (uint32_t)(b | 8);
+        const uint32_t sel = (uint32_t)b | (s << 4) | (s << 8) | (s << 12);
+        return prmt(a, 0u, sel);
+    }
+};
+
+// R profile bytes as R/4 words
+template <int R>
+struct ProfWords {
+    uint32_t w[R / 4];
+};
+
+template <int R>
+__device__ __forceinline__ ProfWords<R> load_prof(const int8_t* p) {
+    ProfWords<R> out;
+    if constexpr (R == 8) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        out.w[0] = v.x;
+        out.w[1] = v.y;
+    } else {
+        static_assert(R == 16, "rows per lane must be 8 or 16");
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        out.w[0] = v.x;
+        out.w[1] = v.y;
+        out.w[2] = v.z;
+        out.w[3] = v.w;
+    }
+    return out;
+}
+
+template <int R>
+__device__ __forceinline__ void store_prof(int8_t* p, const uint32_t (&w)[R / 4]) {
+    if constexpr (R == 8) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    } else {
+        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// (value, i, j) ordering of candidate end cells: larger value first, then the
+// row-major-first cell (smaller streamed index i, then smaller held index j).
+__device__ __forceinline__ bool better(int v, int i, int j, int bv, int bi, int bj) {
+    return v > bv || (v == bv && (i < bi || (i == bi && j < bj)));
+}
+
+// ---------------------------------------------------------------------------
+// The DP kernel
+// ---------------------------------------------------------------------------
+constexpr int kSmatBytes = kProfileRows * kMatStride;   // 800
+constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
+
+template <int G, int R, bool P16>
+__host__ __device__ constexpr int dp_prof_bytes_per_warp() {
+    return (32 / G) * (P16 ? 2 : 1) * kProfileRows * G * R;
+}
+
+// REV = false: forward pass over q x r -> score and end cell.
+// REV = true : local DP over the reversed prefixes q[q_end..0] x r[r_end..0]
+//              of each scored pair -> start cell.
+template <int G, int R, bool P16, bool REV>
+__global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
+    using L = Lane<P16>;
+    constexpr int PACK = L::kPack;
+    constexpr int GROUPS = 32 / G;
+    constexpr int ROWS = G * R;
+    constexpr int PROF = kProfileRows * ROWS;  // bytes per pair
+    constexpr int NW = R / 4;
+
+    extern __shared__ __align__(16) uint8_t smem[];
+    int8_t* smat = reinterpret_cast<int8_t*>(smem);
+    for (int k = threadIdx.x; k < kSmatBytes; k += blockDim.x)
+        smat[k] = a.sc.prof[k / kMatStride][k % kMatStride];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G;    // pair group within the warp
+    const int gl = lane % G;   // lane within the group
+    int8_t* prof = reinterpret_cast<int8_t*>(smem + kSmatRegion) +
+                   (size_t)warp * dp_prof_bytes_per_warp<G, R, P16>() + (size_t)g * PACK * PROF;
+
+    const int64_t begin = a.scan[(int64_t)a.first_bucket * kQBins];
+    const int64_t end = a.scan[(int64_t)a.end_bucket * kQBins];
+    const int64_t slot = (int64_t)blockIdx.x * (kDPThreads / 32) + warp;
+    uint2* bnd = a.boundary ? a.boundary + slot * a.boundary_stride : nullptr;
+
+    const int oe = a.sc.go + a.sc.ge;
+    const uint32_t NOE = L::splat(-oe);
+    const uint32_t NE = L::splat(-a.sc.ge);
+
+    for (;;) {
+        uint32_t task = 0;
+        if (lane == 0) task = atomicAdd(a.task_ctr, 1u);
+        task = __shfl_sync(kFull, task, 0);
+        const int64_t first = begin + (int64_t)task * (GROUPS * PACK);
+        if (first >= end) break;
+
+        // ---- the (up to) PACK pairs of this group
+        int pid[PACK];
+        const uint8_t* qp[PACK];
+        const uint8_t* rp[PACK];
+        int lq[PACK], lr[PACK], target[PACK];
+        int ls = 0, lh = 0;
+#pragma unroll
+        for (int h = 0; h < PACK; ++h) {
+            const int64_t pos = first + g * PACK + h;
+            pid[h] = -1;
+            lq[h] = lr[h] = 0;
+            target[h] = 0;
+            qp[h] = rp[h] = nullptr;
+            if (pos < end) {
+                const int p = a.order[pos];
+                pid[h] = p;
+                const int32_t qi = a.pairs[2 * (int64_t)p], ri = a.pairs[2 * (int64_t)p + 1];
+                qp[h] = a.q.res + a.q.off[qi];
+                rp[h] = a.r.res + a.r.off[ri];
+                if (REV) {
+                    const swgb_record rec = a.out[p];
+                    lq[h] = rec.q_end + 1;
+                    lr[h] = rec.r_end + 1;
+                    target[h] = rec.score;
+                } else {
+                    lq[h] = (int)(a.q.off[qi + 1] - a.q.off[qi]);
+                    lr[h] = (int)(a.r.off[ri + 1] - a.r.off[ri]);
+                }
+            }
+            ls = max(ls, lq[h]);
+            lh = max(lh, lr[h]);
+        }
+        // warp-uniform extents (groups of one warp run in lock step)
+        int ls_w = ls, nch = (lh + ROWS - 1) / ROWS;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ls_w = max(ls_w, __shfl_xor_sync(kFull, ls_w, off));
+            nch = max(nch, __shfl_xor_sync(kFull, nch, off));
+        }
+
+        int bv[PACK], bi[PACK], bj[PACK];
+#pragma unroll
+        for (int h = 0; h < PACK; ++h) {
+            bv[h] = -oe;
+            bi[h] = INT_MAX;
+            bj[h] = INT_MAX;
+        }
+
+        for (int c = 0; c < nch; ++c) {
+            const int jc = c * ROWS;          // first held row of the chunk
+            const int jl = jc + gl * R;       // first held row of this lane
+            // ---- profile of the chunk: prof[h][x][row] = s(x, held row) + o + e
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) {
+                uint8_t y[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const int j = jl + k;
+                    y[k] = (j < lr[h]) ? (REV ? rp[h][lr[h] - 1 - j] : rp[h][j]) : (uint8_t)kPadCode;
+                }
+                int8_t* dst = prof + h * PROF + gl * R;
+                for (int x = 0; x < kProfileRows; ++x) {
+                    const int8_t* row = smat + x * kMatStride;
+                    uint32_t w[NW];
+#pragma unroll
+                    for (int k4 = 0; k4 < NW; ++k4) {
+                        w[k4] = (uint32_t)(uint8_t)row[y[4 * k4]] |
+                                ((uint32_t)(uint8_t)row[y[4 * k4 + 1]] << 8) |
+                                ((uint32_t)(uint8_t)row[y[4 * k4 + 2]] << 16) |
+                                ((uint32_t)(uint8_t)row[y[4 * k4 + 3]] << 24);
+                    }
+                    store_prof<R>(dst + x * ROWS, w);
+                }
+            }
+            __syncwarp();
+
+            // ---- wavefront over the streamed query
+            uint32_t Hop[R], F[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Hop[r] = NOE;   // H - (o + e) of the previous query position
+                F[r] = NOE;
+            }
+            uint32_t hin_prev = NOE, eout = NOE, hout = NOE;
+            uint32_t lb = NOE;   // best H - (o + e) seen by this lane in this chunk
+            int ci[PACK], cj[PACK];
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) ci[h] = cj[h] = -1;
+
+            const bool read_bnd = (c > 0) && (gl == 0);
+            const bool write_bnd = (c + 1 < nch) && (gl == G - 1);
+            const int steps = ls_w + G - 1;
+            for (int t = 0; t < steps; ++t) {
+                const int i = t - gl;
+                uint32_t ein = __shfl_up_sync(kFull, eout, 1, G);
+                uint32_t hin = __shfl_up_sync(kFull, hout, 1, G);
+                if (i < 0 || i >= ls) continue;
+                if (gl == 0) {
+                    if (read_bnd) {
+                        const uint2 v = bnd[i];
+                        ein = v.x;
+                        hin = v.y;
+                    } else {
+                        ein = NOE;
+                        hin = NOE;
+                    }
+                }
+                // profile words of the query letter at i, per pair
+                ProfWords<R> pw[PACK];
+#pragma unroll
+                for (int h = 0; h < PACK; ++h) {
+                    const int x = (i < lq[h]) ? (REV ? qp[h][lq[h] - 1 - i] : qp[h][i]) : kPadCode;
+                    pw[h] = load_prof<R>(prof + h * PROF + x * ROWS + gl * R);
+                }
+                uint32_t hd = hin_prev;   // H(i-1, j-1) - (o + e) for the first row
+                uint32_t e = ein;         // E(i, first row)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
+                    const uint32_t u = L::addmax(hd, s, F[r]);       // max(Hdiag + s, F)
+                    const uint32_t U = L::addmax(u, NOE, NOE);      // max(u, 0) - (o + e)
+                    const uint32_t hn = L::addmax(e, NOE, U);       // H - (o + e)
+                    e = L::addmax(e, NE, U);                        // E of the next row
+                    F[r] = L::addmax(F[r], NE, hn);                 // F of the next query position
+                    hd = Hop[r];
+                    Hop[r] = hn;
+                }
+                eout = e;
+                hout = Hop[R - 1];
+                hin_prev = hin;
+                if (write_bnd) bnd[i] = make_uint2(eout, hout);
+
+                // ---- running maximum of this lane (first cell reaching it)
+                uint32_t m = lb;
+#pragma unroll
+                for (int r = 0; r < R; r += 2) m = L::max3(m, Hop[r], Hop[r + 1]);
+                if (m != lb) {
+#pragma unroll
+                    for (int h = 0; h < PACK; ++h) {
+                        const int mh = L::get(m, h);
+                        if (mh > L::get(lb, h)) {
+                            int rr = R - 1;
+#pragma unroll
+                            for (int r = R - 1; r >= 0; --r)
+                                if (L::get(Hop[r], h) == mh) rr = r;
+                            ci[h] = i;
+                            cj[h] = jl + rr;
+                        }
+                    }
+                    lb = m;
+                }
+            }
+            // ---- merge the chunk's best into the lane's best
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) {
+                if (ci[h] >= 0) {
+                    const int v = L::get(lb, h);
+                    if (better(v, ci[h], cj[h], bv[h], bi[h], bj[h])) {
+                        bv[h] = v;
+                        bi[h] = ci[h];
+                        bj[h] = cj[h];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- reduce over the lanes of the group and write the records
+#pragma unroll
+        for (int h = 0; h < PACK; ++h) {
+            int v = bv[h], ii = bi[h], jj = bj[h];
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const int ov = __shfl_xor_sync(kFull, v, off, G);
+                const int oi = __shfl_xor_sync(kFull, ii, off, G);
+                const int oj = __shfl_xor_sync(kFull, jj, off, G);
+                if (better(ov, oi, oj, v, ii, jj)) {
+                    v = ov;
+                    ii = oi;
+                    jj = oj;
+                }
+            }
+            if (gl == 0 && pid[h] >= 0) {
+                const int S = v + oe;
+                swgb_record* rec = &a.out[pid[h]];
+                if (!REV) {
+                    if (S > 0 && ii != INT_MAX) {
+                        *rec = swgb_record{S, -1, ii, -1, jj};
+                    } else {
+                        *rec = swgb_record{0, -1, -1, -1, -1};
+                    }
+                } else {
+                    if (S != target[h] || ii == INT_MAX) {
+                        set_status(a.status, SWGB_EINTERNAL);
+                    } else {
+                        rec->q_start = lq[h] - 1 - ii;
+                        rec->r_start = lr[h] - 1 - jj;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch over (class, shape, direction)
+// ---------------------------------------------------------------------------
+using DPFn = void (*)(const DPArgs);
+
+template <int S, bool P16, bool REV>
+constexpr DPFn dp_fn() {
+    constexpr int G = S == 0 ? 4 : S == 1 ? 8 : S == 2 ? 16 : 32;
+    constexpr int R = S == 4 ? 16 : 8;
+    return &dp_kernel<G, R, P16, REV>;
+}
+
+template <bool P16, bool REV>
+DPFn dp_pick(int shape) {
+    switch (shape) {
+        case 0: return dp_fn<0, P16, REV>();
+        case 1: return dp_fn<1, P16, REV>();
+        case 2: return dp_fn<2, P16, REV>();
+        case 3: return dp_fn<3, P16, REV>();
+        default: return dp_fn<4, P16, REV>();
+    }
+}
+
+static DPFn dp_lookup(int cls, int shape, bool reverse) {
+    if (cls == 0) return reverse ? dp_pick<true, true>(shape) : dp_pick<true, false>(shape);
+    return reverse ? dp_pick<false, true>(shape) : dp_pick<false, false>(shape);
+}
+
+size_t dp_smem_bytes(int cls, int shape) {
+    const int G = kShapeG[shape], R = kShapeR[shape];
+    const int pack = cls == 0 ? 2 : 1;
+    const size_t per_warp = (size_t)(32 / G) * pack * kProfileRows * G * R;
+    return kSmatRegion + per_warp * (kDPThreads / 32);
+}
+
+cudaError_t dp_configure(int cls, int shape, bool reverse) {
+    return cudaFuncSetAttribute(dp_lookup(cls, shape, reverse),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dp_smem_bytes(cls, shape));
+}
+
+int dp_blocks_per_sm(int cls, int shape, bool reverse) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dp_lookup(cls, shape, reverse), kDPThreads,
+                                                      dp_smem_bytes(cls, shape)) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
+                      cudaStream_t st) {
+    DPFn fn = dp_lookup(cls, shape, reverse);
+    fn<<<grid_blocks, kDPThreads, dp_smem_bytes(cls, shape), st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Issue-rate probe of __viaddmax_s16x2
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kProbeThreads) probe_addmax_kernel(unsigned long long* cycles,
+                                                                      uint32_t* sink, int iters) {
+    uint32_t v[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) v[k] = threadIdx.x * 0x00010001u + k;
+    const uint32_t inc = 0x00010001u;
+    const uint32_t floor_v = (blockIdx.x & 7) * 0x00010001u;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) v[k] = __viaddmax_s16x2(v[k], inc, floor_v);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) acc ^= v[k];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(t1 - t0);
+}
+
+cudaError_t launch_probe_addmax(unsigned long long* cycles, uint32_t* sink, int blocks, int iters,
+                                cudaStream_t st) {
+    probe_addmax_kernel<<<blocks, kProbeThreads, 0, st>>>(cycles, sink, iters);
+    return cudaGetLastError();
+}
+
+}  // namespace swgb

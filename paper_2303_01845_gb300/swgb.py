@@ -1,0 +1,320 @@
+"""ctypes binding of libswgb (include/swgb.h): argument marshalling only.
+
+Every step of the alignment runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers and raises ``SwgbError`` on a
+non-zero status.  There is no fallback: importing it without a built
+``libswgb.so`` raises.
+
+Names follow the C ABI (``swgb_create``, ``swgb_align``, ...).  PyTorch is used
+for device memory and streams only.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SWGB_OK = 0
+SWGB_EINVAL = -1
+SWGB_ERANGE = -2
+SWGB_EBADRES = -3
+SWGB_ENOMEM = -4
+SWGB_ECUDA = -5
+SWGB_EINTERNAL = -6
+
+SWGB_ALPHABET_SIZE = 24
+SWGB_MAX_LENGTH = 65536
+SWGB_SEQ_ASCII = 0x1
+SWGB_SEQ_DEVICE = 0x2
+SWGB_FORCE_INT32 = 0x1
+SWGB_TIMING = 0x2
+
+ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
+
+_NAMES = {SWGB_EINVAL: "EINVAL", SWGB_ERANGE: "ERANGE", SWGB_EBADRES: "EBADRES",
+          SWGB_ENOMEM: "ENOMEM", SWGB_ECUDA: "ECUDA", SWGB_EINTERNAL: "EINTERNAL"}
+
+
+class SwgbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class swgb_record(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("q_start", ctypes.c_int32),
+                ("q_end", ctypes.c_int32), ("r_start", ctypes.c_int32),
+                ("r_end", ctypes.c_int32)]
+
+
+class swgb_params(ctypes.Structure):
+    _fields_ = [("matrix", ctypes.POINTER(ctypes.c_int8)), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class swgb_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_int16_pairs", ctypes.c_int64),
+                ("n_int32_pairs", ctypes.c_int64), ("n_reverse_pairs", ctypes.c_int64),
+                ("forward_cells", ctypes.c_int64), ("reverse_cells", ctypes.c_int64),
+                ("forward_ms", ctypes.c_float), ("reverse_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32)]
+
+
+# (name, restype, argtypes) of every exported function
+_VP = ctypes.c_void_p
+_SIGS = [
+    ("swgb_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("swgb_destroy", None, [_VP]),
+    ("swgb_last_error", ctypes.c_char_p, [_VP]),
+    ("swgb_blosum62", None, [_VP]),
+    ("swgb_seqset_create", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP,
+                                          ctypes.POINTER(_VP)]),
+    ("swgb_seqset_load", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_uint32, _VP]),
+    ("swgb_seqset_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    ("swgb_seqset_destroy", None, [_VP]),
+    ("swgb_align", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64,
+                                  ctypes.POINTER(swgb_params), _VP, _VP]),
+    ("swgb_align_host", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64,
+                                       ctypes.POINTER(swgb_params), _VP, _VP]),
+    ("swgb_sync", ctypes.c_int, [_VP, _VP]),
+    ("swgb_last_stats", ctypes.c_int, [_VP, ctypes.POINTER(swgb_stats)]),
+    ("swgb_probe_addmax_rate", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int)]),
+]
+
+_lib = None
+
+
+def library_path():
+    return _build.SWGB_LIB
+
+
+def load(build_if_missing=True):
+    """Loads libswgb.so (building it in-tree if missing).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.SWGB_LIB
+    if build_if_missing:
+        path = _build.build_swgb()
+    if not os.path.exists(path):
+        raise ImportError("libswgb.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc):
+    if rc != SWGB_OK:
+        msg = load().swgb_last_error(ctx)
+        raise SwgbError(rc, msg.decode(errors="replace") if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def swgb_blosum62():
+    """The library's BLOSUM62, int8 [24, 24] (row = query letter)."""
+    out = np.zeros((24, 24), dtype=np.int8)
+    load().swgb_blosum62(out.ctypes.data)
+    return out
+
+
+def swgb_create(device=0):
+    h = _VP()
+    rc = load().swgb_create(int(device), ctypes.byref(h))
+    if rc != SWGB_OK:
+        raise SwgbError(rc, "swgb_create(device=%d) failed" % device)
+    return h
+
+
+def swgb_destroy(ctx):
+    load().swgb_destroy(ctx)
+
+
+def _seq_args(residues, offsets, flags):
+    on_dev = hasattr(residues, "is_cuda") and residues.is_cuda
+    if on_dev:
+        flags |= SWGB_SEQ_DEVICE
+        if not (hasattr(offsets, "is_cuda") and offsets.is_cuda):
+            raise ValueError("residues and offsets must live on the same side")
+    if hasattr(offsets, "dtype") and str(offsets.dtype) not in ("int64", "torch.int64"):
+        raise TypeError("offsets must be int64")
+    n = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+    return flags, max(n, 0)
+
+
+def swgb_seqset_create(ctx, residues, offsets, ascii=False, stream=None):
+    """residues: uint8 codes (or ASCII with ascii=True); offsets: int64 [n+1].
+    Host (numpy / CPU tensor) or device (CUDA tensor) buffers."""
+    flags, n = _seq_args(residues, offsets, SWGB_SEQ_ASCII if ascii else 0)
+    h = _VP()
+    rc = load().swgb_seqset_create(ctx, _ptr(residues), _ptr(offsets), n, flags,
+                                   _stream_handle(stream), ctypes.byref(h))
+    _check(ctx, rc)
+    return h
+
+
+def swgb_seqset_load(ctx, seqset, residues, offsets, ascii=False, stream=None):
+    flags, n = _seq_args(residues, offsets, SWGB_SEQ_ASCII if ascii else 0)
+    rc = load().swgb_seqset_load(seqset, _ptr(residues), _ptr(offsets), n, flags,
+                                 _stream_handle(stream))
+    _check(ctx, rc)
+
+
+def swgb_seqset_info(seqset):
+    n = ctypes.c_int64()
+    m = ctypes.c_int64()
+    rc = load().swgb_seqset_info(seqset, ctypes.byref(n), ctypes.byref(m))
+    if rc != SWGB_OK:
+        raise SwgbError(rc, "swgb_seqset_info")
+    return n.value, m.value
+
+
+def swgb_seqset_destroy(seqset):
+    load().swgb_seqset_destroy(seqset)
+
+
+def make_params(matrix=None, gap_open=11, gap_extend=1, force_int32=False, timing=False):
+    """swgb_params (keeps a reference to the matrix buffer)."""
+    m = swgb_blosum62() if matrix is None else np.ascontiguousarray(matrix, dtype=np.int8)
+    if m.shape != (24, 24):
+        raise ValueError("matrix must be 24 x 24")
+    p = swgb_params(m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap_open),
+                    int(gap_extend),
+                    (SWGB_FORCE_INT32 if force_int32 else 0) | (SWGB_TIMING if timing else 0))
+    p._matrix_ref = m
+    return p
+
+
+def swgb_align(ctx, queries, refs, pairs, params, out=None, stream=None):
+    """pairs: CUDA int32 tensor [P, 2]; returns (and fills) CUDA int32 [P, 5].
+    Asynchronous on `stream` (default: torch's current stream)."""
+    import torch
+    if not pairs.is_cuda or pairs.dtype != torch.int32:
+        raise TypeError("pairs must be a CUDA int32 tensor")
+    n = pairs.shape[0]
+    if out is None:
+        out = torch.empty((n, 5), dtype=torch.int32, device=pairs.device)
+    if not out.is_cuda or out.dtype != torch.int32 or out.numel() < 5 * n:
+        raise TypeError("out must be a CUDA int32 tensor with P x 5 elements")
+    rc = load().swgb_align(ctx, queries, refs, _ptr(pairs), n, ctypes.byref(params), _ptr(out),
+                           _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
+def swgb_align_host(ctx, queries, refs, pairs, params, out=None, stream=None):
+    """Host pairs int32 [P, 2] (numpy or CPU tensor, pinned for async copies)
+    -> host records int32 [P, 5]; synchronous."""
+    n = pairs.shape[0]
+    if out is None:
+        out = np.empty((n, 5), dtype=np.int32)
+    rc = load().swgb_align_host(ctx, queries, refs, _ptr(pairs), n, ctypes.byref(params),
+                                _ptr(out), _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
+def swgb_sync(ctx, stream=None):
+    _check(ctx, load().swgb_sync(ctx, _stream_handle(stream)))
+
+
+def swgb_last_stats(ctx):
+    s = swgb_stats()
+    _check(ctx, load().swgb_last_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in swgb_stats._fields_}
+
+
+def swgb_probe_addmax_rate(ctx):
+    """(lane-level add-max instructions per SM clock per SM, SM count)."""
+    r = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(ctx, load().swgb_probe_addmax_rate(ctx, ctypes.byref(r), ctypes.byref(n)))
+    return r.value, n.value
+
+
+class Aligner:
+    """Owns a context; convenience wrapper over the functions above."""
+
+    def __init__(self, device=0):
+        self.ctx = swgb_create(device)
+        self.device = device
+
+    def close(self):
+        if self.ctx:
+            swgb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seqset(self, residues, offsets, ascii=False, stream=None):
+        return SeqSet(self, swgb_seqset_create(self.ctx, residues, offsets, ascii, stream))
+
+    def align(self, queries, refs, pairs, params=None, out=None, stream=None, sync=True):
+        params = params or make_params()
+        out = swgb_align(self.ctx, queries.handle, refs.handle, pairs, params, out, stream)
+        if sync:
+            swgb_sync(self.ctx, stream)
+        return out
+
+    def align_host(self, queries, refs, pairs, params=None, out=None, stream=None):
+        params = params or make_params()
+        return swgb_align_host(self.ctx, queries.handle, refs.handle, pairs, params, out, stream)
+
+    def stats(self):
+        return swgb_last_stats(self.ctx)
+
+
+class SeqSet:
+    def __init__(self, aligner, handle):
+        self.aligner = aligner
+        self.handle = handle
+
+    def info(self):
+        return swgb_seqset_info(self.handle)
+
+    def load(self, residues, offsets, ascii=False, stream=None):
+        swgb_seqset_load(self.aligner.ctx, self.handle, residues, offsets, ascii, stream)
+
+    def close(self):
+        if self.handle:
+            swgb_seqset_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

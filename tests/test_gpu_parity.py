@@ -1,0 +1,280 @@
+"""GPU parity: every record from the CUDA library (called through the C ABI)
+equals the CPU oracle's, bit for bit.
+
+Sizes: the whole 10,000-pair uniform-length workload; ragged length grids that
+cross every tile shape, the 512-row chunk boundary and the 16-bit/32-bit
+switch; edge cases (empty sequences, single residues, no positive score,
+out-of-range pairs); and, in the benchmark's launch configuration, the
+2,000,000-pair log-normal workload checked on a seeded sample plus every
+pair on the 32-bit path.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_same, device_sets, gpu_records, oracle_records
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def aligner(torch_cuda):
+    from paper_2303_01845_gb300 import swgb
+    a = swgb.Aligner(0)
+    yield a
+    a.close()
+
+
+@pytest.fixture(scope="module")
+def blosum(oracle_mod):
+    return oracle_mod.blosum62()
+
+
+@pytest.fixture(scope="module")
+def plain10k(blosum):
+    from paper_2303_01845_gb300 import workload
+    return workload.generate("plain_10k", blosum)
+
+
+def params(mat, go=11, ge=1, **kw):
+    from paper_2303_01845_gb300 import swgb
+    return swgb.make_params(mat, go, ge, **kw)
+
+
+def test_plain_10k_bit_exact(aligner, oracle_mod, blosum, plain10k):
+    got = gpu_records(aligner, plain10k, params(blosum))
+    want = oracle_records(oracle_mod, plain10k, blosum, 11, 1)
+    assert_same(got, want, plain10k)
+    st = aligner.stats()
+    assert st["forward_cells"] == plain10k.cells()
+    assert st["n_int16_pairs"] == len(plain10k.pairs)
+    assert st["n_reverse_pairs"] == int((want[:, 0] > 0).sum())
+
+
+def test_plain_10k_forced_int32_path(aligner, oracle_mod, blosum, plain10k):
+    sub = plain10k.subset(np.arange(0, 10000, 7))
+    got = gpu_records(aligner, sub, params(blosum, force_int32=True))
+    want = oracle_records(oracle_mod, sub, blosum, 11, 1)
+    assert_same(got, want, sub)
+    assert aligner.stats()["n_int32_pairs"] == len(sub.pairs)
+
+
+def test_gap_settings_and_asymmetric_matrix(aligner, oracle_mod, blosum, plain10k):
+    sub = plain10k.subset(np.arange(3, 10000, 13))
+    for go, ge in [(11, 2), (0, 1), (5, 3), (20, 4)]:
+        assert_same(gpu_records(aligner, sub, params(blosum, go, ge)),
+                    oracle_records(oracle_mod, sub, blosum, go, ge), sub)
+    rng = np.random.default_rng(5)
+    asym = rng.integers(-6, 7, size=(24, 24)).astype(np.int8)
+    assert_same(gpu_records(aligner, sub, params(asym, 7, 2)),
+                oracle_records(oracle_mod, sub, asym, 7, 2), sub)
+
+
+HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257,
+                511, 512, 513, 1023, 1024, 1025, 1537, 2999]
+STREAM_LENGTHS = [1, 2, 3, 30, 31, 32, 33, 100, 257, 512, 513, 1200]
+
+
+def ragged_workload(seed, mat, held=HELD_LENGTHS, stream=STREAM_LENGTHS):
+    """Queries of every streamed length against references of every held
+    length; half of the references derived from a query (mutated), half
+    unrelated."""
+    from paper_2303_01845_gb300 import workload
+    rng = np.random.default_rng(seed)
+    p = workload.background()
+    queries = [rng.choice(20, size=n, p=p).astype(np.uint8) for n in stream]
+    refs, pairs = [], []
+    for qi, q in enumerate(queries):
+        for L in held:
+            # homologous: a window of the query (repeated to length L), mutated
+            base = np.resize(q, L).copy()
+            mask = rng.random(L) < 0.3
+            base[mask] = rng.choice(20, size=int(mask.sum()), p=p)
+            refs.append(base)
+            pairs.append((qi, len(refs) - 1))
+            refs.append(rng.choice(20, size=L, p=p).astype(np.uint8))
+            pairs.append((qi, len(refs) - 1))
+    return workload.from_sequences(queries, refs, pairs)
+
+
+def test_ragged_lengths_all_shapes(aligner, oracle_mod, blosum):
+    wl = ragged_workload(11, blosum)
+    assert_same(gpu_records(aligner, wl, params(blosum)),
+                oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+
+
+def test_ragged_lengths_int32(aligner, oracle_mod, blosum):
+    wl = ragged_workload(12, blosum, held=[1, 33, 257, 513, 1537], stream=[1, 40, 600])
+    assert_same(gpu_records(aligner, wl, params(blosum, force_int32=True)),
+                oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+
+
+def test_self_alignment_closed_form_across_the_int16_limit(aligner, blosum):
+    """Self-alignments have S = sum of the diagonal over the full length; past
+    2978 residues 11 * n exceeds 32767 and the pair takes the 32-bit path."""
+    from paper_2303_01845_gb300 import workload
+    rng = np.random.default_rng(13)
+    lens = [1, 5, 64, 300, 2978, 2979, 3500, 5000, 9000]
+    seqs = [rng.integers(0, 20, size=n).astype(np.uint8) for n in lens]
+    wl = workload.from_sequences(seqs, seqs, [(k, k) for k in range(len(seqs))])
+    got = gpu_records(aligner, wl, params(blosum))
+    m = blosum.astype(np.int64)
+    for k, s in enumerate(seqs):
+        n = len(s)
+        assert tuple(got[k]) == (int(m[s, s].sum()), 0, n - 1, 0, n - 1)
+    st = aligner.stats()
+    assert st["n_int32_pairs"] == sum(1 for n in lens if 11 * n > 32767)
+
+
+def test_tryptophan_runs_at_the_int16_limit(aligner, oracle_mod, blosum):
+    """W-W scores 11: W runs long enough to pass 32767 must not wrap."""
+    from paper_2303_01845_gb300 import workload
+    w = workload.ALPHABET.index("W")
+    rng = np.random.default_rng(14)
+    seqs = []
+    for n in [2970, 2978, 2979, 2990, 3100]:
+        s = np.full(n, w, np.uint8)
+        s[rng.integers(0, n, size=5)] = rng.integers(0, 20, size=5)
+        seqs.append(s)
+    pairs = [(a, b) for a in range(len(seqs)) for b in range(len(seqs))]
+    wl = workload.from_sequences(seqs, seqs, pairs)
+    assert_same(gpu_records(aligner, wl, params(blosum)),
+                oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+
+
+def test_edge_cases(aligner, oracle_mod, blosum):
+    from paper_2303_01845_gb300 import workload
+    A = workload.ALPHABET
+    enc = lambda s: np.array([A.index(c) for c in s], np.uint8)
+    seqs = [enc(s) for s in ["", "A", "W", "WWWWW", "PPPPPPP", "AAAA", "AAAAAAA",
+                             "HEAGAWGHEE", "PAWHEAE", "*", "BZX*", "C" * 40]]
+    n = len(seqs)
+    pairs = [(a, b) for a in range(n) for b in range(n)]
+    wl = workload.from_sequences(seqs, seqs, pairs)
+    got = gpu_records(aligner, wl, params(blosum))
+    assert_same(got, oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+    # empty sequences report a zero record
+    for p, (a, b) in enumerate(pairs):
+        if len(seqs[a]) == 0 or len(seqs[b]) == 0:
+            assert tuple(got[p]) == (0, -1, -1, -1, -1)
+
+
+def test_one_set_against_itself_and_repeated_pairs(aligner, oracle_mod, blosum, plain10k, torch_cuda):
+    torch = torch_cuda
+    q, _ = device_sets(aligner, plain10k)
+    rng = np.random.default_rng(15)
+    pairs = rng.integers(0, 300, size=(2000, 2)).astype(np.int32)
+    pairs[:50] = pairs[50:100]
+    out = aligner.align(q, q, torch.from_numpy(pairs).cuda(), params(blosum)).cpu().numpy()
+    want = oracle_mod.align_batch(plain10k.q_res, plain10k.q_off, plain10k.q_res, plain10k.q_off,
+                                  pairs, blosum, 11, 1)
+    assert_same(out, want)
+
+
+def test_record_is_independent_of_the_batch(aligner, blosum, plain10k, torch_cuda):
+    """A pair's record is the same alone, in a small batch and in the full one
+    (different buckets, partners in the packed register, launch grids)."""
+    torch = torch_cuda
+    q, r = device_sets(aligner, plain10k)
+    full = gpu_records(aligner, plain10k, params(blosum), sets=(q, r))
+    rng = np.random.default_rng(16)
+    pick = rng.choice(10000, size=40, replace=False)
+    for k in pick[:10]:
+        one = aligner.align(q, r, torch.from_numpy(plain10k.pairs[k:k + 1].copy()).cuda(),
+                            params(blosum)).cpu().numpy()
+        assert (one[0] == full[k]).all()
+    few = aligner.align(q, r, torch.from_numpy(plain10k.pairs[pick].copy()).cuda(),
+                        params(blosum)).cpu().numpy()
+    assert (few == full[pick]).all()
+
+
+def test_ascii_and_host_paths(aligner, oracle_mod, blosum, plain10k, torch_cuda):
+    from paper_2303_01845_gb300 import workload
+    sub = plain10k.subset(np.arange(0, 600))
+    alpha = np.frombuffer(workload.ALPHABET.encode(), np.uint8)
+    q_ascii = alpha[sub.q_res]
+    # mixed case is accepted
+    q_ascii = np.where(np.arange(len(q_ascii)) % 2 == 0, q_ascii, q_ascii + 32 * (q_ascii >= 65))
+    qs = aligner.seqset(q_ascii.astype(np.uint8), sub.q_off, ascii=True)
+    rs = aligner.seqset(sub.r_res, sub.r_off)
+    got = aligner.align_host(qs, rs, np.ascontiguousarray(sub.pairs), params(blosum))
+    assert_same(got, oracle_records(oracle_mod, sub, blosum, 11, 1), sub)
+
+
+def test_errors_are_reported(aligner, blosum, plain10k, torch_cuda):
+    torch = torch_cuda
+    from paper_2303_01845_gb300 import swgb
+    q, r = device_sets(aligner, plain10k)
+    pairs = torch.tensor([[0, 0], [5, 10**6], [-1, 3], [7, 7]], dtype=torch.int32).cuda()
+    with pytest.raises(swgb.SwgbError) as ei:
+        aligner.align(q, r, pairs, params(blosum))
+    assert ei.value.code == swgb.SWGB_ERANGE
+    out = swgb.swgb_align(aligner.ctx, q.handle, r.handle, pairs, params(blosum))
+    with pytest.raises(swgb.SwgbError):
+        swgb.swgb_sync(aligner.ctx)
+    got = out.cpu().numpy()
+    assert tuple(got[1]) == (0, -1, -1, -1, -1) and tuple(got[2]) == (0, -1, -1, -1, -1)
+    assert got[0, 0] > 0 and got[3, 0] > 0
+    # the context stays usable
+    ok = aligner.align(q, r, pairs[[0, 3]].contiguous(), params(blosum)).cpu().numpy()
+    assert (ok == got[[0, 3]]).all()
+    # bad residues
+    with pytest.raises(swgb.SwgbError) as ei:
+        aligner.seqset(np.array([0, 1, 30], np.uint8), np.array([0, 3], np.int64))
+    assert ei.value.code == swgb.SWGB_EBADRES
+    with pytest.raises(swgb.SwgbError) as ei:
+        aligner.seqset(np.frombuffer(b"AC1D", np.uint8).copy(), np.array([0, 4], np.int64), ascii=True)
+    assert ei.value.code == swgb.SWGB_EBADRES
+    # too long
+    with pytest.raises(swgb.SwgbError) as ei:
+        aligner.seqset(np.zeros(swgb.SWGB_MAX_LENGTH + 1, np.uint8),
+                       np.array([0, swgb.SWGB_MAX_LENGTH + 1], np.int64))
+    assert ei.value.code == swgb.SWGB_ERANGE
+    # bad penalties
+    for go, ge in [(-1, 1), (11, 0), (120, 1)]:
+        with pytest.raises(swgb.SwgbError) as ei:
+            aligner.align(q, r, pairs[[0]].contiguous(), params(blosum, go, ge))
+        assert ei.value.code == swgb.SWGB_EINVAL
+    # empty batch
+    empty = torch.zeros((0, 2), dtype=torch.int32).cuda()
+    assert aligner.align(q, r, empty, params(blosum)).shape == (0, 5)
+
+
+@pytest.fixture(scope="module")
+def batched2m(blosum):
+    from paper_2303_01845_gb300 import workload
+    return workload.generate("batched_2m", blosum)
+
+
+def test_batched_2m_sampled_parity(aligner, oracle_mod, blosum, batched2m, torch_cuda):
+    """The full 2,000,000-pair workload in one call (the benchmark's launch
+    configuration); a seeded sample of 20,000 pairs plus every 32-bit pair is
+    compared with the oracle, and every record is checked for the properties
+    that hold at any size."""
+    torch = torch_cuda
+    wl = batched2m
+    q, r = device_sets(aligner, wl)
+    pairs = torch.from_numpy(wl.pairs).cuda()
+    out = aligner.align(q, r, pairs, params(blosum)).cpu().numpy()
+    st = aligner.stats()
+    assert st["forward_cells"] == wl.cells()
+    ql = wl.q_len[wl.pairs[:, 0]]
+    rl = wl.r_len[wl.pairs[:, 1]]
+    s, qs, qe, rs, re_ = out.T
+    assert (s >= 0).all() and (s <= 11 * np.minimum(ql, rl)).all()
+    pos = s > 0
+    assert (out[~pos] == [0, -1, -1, -1, -1]).all()
+    assert ((0 <= qs) & (qs <= qe) & (qe < ql))[pos].all()
+    assert ((0 <= rs) & (rs <= re_) & (re_ < rl))[pos].all()
+    int32_pairs = np.nonzero(11 * np.minimum(ql, rl) > 32767)[0]
+    assert st["n_int32_pairs"] == len(int32_pairs)
+    rng = np.random.default_rng(17)
+    sample = np.union1d(rng.choice(len(wl.pairs), size=20000, replace=False), int32_pairs)
+    sub = wl.subset(sample)
+    assert_same(out[sample], oracle_records(oracle_mod, sub, blosum, 11, 1), sub)
