@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_2m")
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="use only the first N pairs of the workload (profiling cases)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -119,9 +121,18 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def make_workload(name, mat):
+def make_workload(name, mat, pairs=0):
+    import numpy as np
+
     from paper_2303_01845_gb300 import workload
-    return workload.generate(name, mat)
+    wl = workload.generate(name, mat)
+    if pairs and pairs < len(wl.pairs):
+        wl = wl.subset(np.arange(pairs))
+    return wl
+
+
+def workload_name(args):
+    return args.workload + ("[:%d]" % args.pairs if args.pairs else "")
 
 
 def cpu_oracle_sample(wl, mat, target_s, seed=7):
@@ -161,7 +172,7 @@ def run_reference(args):
 
     import oracle
     mat = oracle.blosum62()
-    wl = make_workload(args.workload, mat)
+    wl = make_workload(args.workload, mat, args.pairs)
     cores = os.cpu_count() or 1
     per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     # size one step's sample from a calibration run
@@ -187,11 +198,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "pairs_per_step": n,
+        "config": {"workload": workload_name(args), "pairs_per_step": n,
                    "sample": "seeded random subset of the workload's pairs per step"},
         "alignments_per_s": pairs / total,
         "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
-                         "sample": "%d random pairs of %s per step" % (n, args.workload)},
+                         "sample": "%d random pairs of %s per step" % (n, workload_name(args))},
         "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -223,7 +234,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     mat = swgb.swgb_blosum62()
-    wl = make_workload(args.workload, mat)
+    wl = make_workload(args.workload, mat, args.pairs)
     al = swgb.Aligner(local)
     stream = torch.cuda.current_stream(dev)
     q = al.seqset(torch.from_numpy(wl.q_res).to(dev), torch.from_numpy(wl.q_off).to(dev))
@@ -299,7 +310,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
-        "config": {"workload": args.workload, "pairs": P, "forward_cells": cells,
+        "config": {"workload": workload_name(args), "pairs": P, "forward_cells": cells,
                    "reverse_cells": stats["reverse_cells"],
                    "int32_pairs": stats["n_int32_pairs"], "gap_open": 11, "gap_extend": 1,
                    "matrix": "BLOSUM62",
@@ -316,7 +327,7 @@ def run_ours(args):
         "cpu_baseline": None if cpu is None else {
             "value": cpu["gcups"], "unit": "GCUPS", "cores": cpu["cores"], "kind": "oracle",
             "sample": "%d random pairs (%.2e cells) of %s, %.1f s" %
-                      (cpu["pairs"], cpu["cells"], args.workload, cpu["seconds"]),
+                      (cpu["pairs"], cpu["cells"], workload_name(args), cpu["seconds"]),
             "alignments_per_s": cpu["aln_per_s"]},
         "e2e": e2e,
         "gpu_launches": launches,

@@ -57,6 +57,7 @@ extern "C" {
 #define SWGB_ENOMEM (-4)  /* a device or host allocation failed */
 #define SWGB_ECUDA (-5)   /* a CUDA runtime call failed (message in swgb_last_error) */
 #define SWGB_EINTERNAL (-6) /* the device detected an inconsistency in its own results */
+#define SWGB_ETOOBIG (-7) /* a size exceeds the fixed limits of swgb_align_noalloc */
 
 #define SWGB_ALPHABET_SIZE 24
 /* Longest sequence accepted (residues). */
@@ -181,6 +182,43 @@ int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out);
  * per SM, from a kernel of independent chains timed with the SM cycle
  * counter.  Also reports the SM count.  Synchronous.  Errors: EINVAL, ECUDA. */
 int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_count);
+
+/* ---- allocation-free variant ----
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory while they align -- code running inside a
+ * memory pool or arena that already owns the device's memory, a framework
+ * whose allocator must not be bypassed, or a service that must keep a fixed
+ * footprint after start-up.  It runs the same kernels as swgb_align, but all
+ * device scratch (bucketing arrays, work counters, status word, chunk-boundary
+ * rows) lives in one fixed array compiled into the library, of
+ * SWGB_NOALLOC_SCRATCH_BYTES; every GPU that loads the library holds that
+ * array until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine, and needs no context. */
+#define SWGB_NOALLOC_SCRATCH_BYTES (32 << 20)
+#define SWGB_NOALLOC_MAX_PAIRS (1 << 19)          /* pairs per call */
+#define SWGB_NOALLOC_MAX_QUERY_LENGTH 4096        /* residues per query sequence */
+
+/* Aligns n_pairs pairs like swgb_align, on the calling thread's current
+ * device.  Every pointer is a caller-owned DEVICE pointer: q_codes/q_offsets
+ * (n_q sequences, codes 0..23, offsets n_q + 1 entries), r_codes/r_offsets
+ * (n_r sequences), pairs int32 [n_pairs][2], out swgb_record [n_pairs].
+ * params->matrix is a host pointer, as for swgb_align.
+ * The first call on a device resolves the array's device address and
+ * configures the kernels; make that first call before any stream capture.
+ * Every call shares the one array and it keeps the previous call's contents
+ * (the call clears what must start at zero); calls that overlap on the GPU --
+ * from several threads or streams at once -- race on it and must be
+ * serialised by the caller.  Synchronous: returns after the stream has
+ * finished the call.
+ * Errors: EINVAL (bad argument or penalty), ETOOBIG (n_pairs above
+ * SWGB_NOALLOC_MAX_PAIRS, a query longer than SWGB_NOALLOC_MAX_QUERY_LENGTH
+ * or a reference longer than SWGB_MAX_LENGTH; nothing is launched), EBADRES
+ * (a code >= 24), ERANGE (decreasing offsets, or a pair index out of range:
+ * that pair's record is zero), EINTERNAL, ECUDA. */
+int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offsets, int64_t n_q,
+                       const uint8_t* r_codes, const int64_t* r_offsets, int64_t n_r,
+                       const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                       swgb_record* out, void* stream);
 
 #ifdef __cplusplus
 }

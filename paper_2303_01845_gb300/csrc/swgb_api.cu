@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -516,4 +517,233 @@ SWGB_EXPORT int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm
     *ops_per_clk_per_sm = ops_per_sm / (double)mx;
     if (sm_count) *sm_count = ctx->sm_count;
     return SWGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// swgb_align_noalloc: the same pipeline with every piece of device scratch
+// taken from one fixed array compiled into the library.
+//
+// Some callers cannot allocate device memory while they align: code running
+// inside a memory pool or arena that owns all of the device's memory, a host
+// framework whose allocator must not be bypassed, or a process that has to
+// keep its footprint constant after start-up.  This path never calls
+// cudaMalloc, cudaFree or any other allocating routine (device or host); the
+// caller passes its inputs and outputs as device pointers and the scratch is
+// g_noalloc_scratch below.  Every GPU that loads this library holds the
+// array (SWGB_NOALLOC_SCRATCH_BYTES) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocBytes = SWGB_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocChunkBlocks = 152;   // grid cap of the 512-row-chunk kernels
+constexpr int64_t kNoallocSlots = (int64_t)kNoallocChunkBlocks * (kDPThreads / 32);
+constexpr int kNoallocMaxDevices = 64;
+
+constexpr int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
+
+// byte offsets of the pieces inside the array
+constexpr int64_t kNaHist = 0;
+constexpr int64_t kNaScan = kNaHist + align256(4 * (int64_t)kNumBins);
+constexpr int64_t kNaCursor = kNaScan + align256(4 * ((int64_t)kNumBins + 1));
+constexpr int64_t kNaTask = kNaCursor + align256(4 * (int64_t)kNumBins);
+constexpr int64_t kNaStatus = kNaTask + align256(4 * 2 * (int64_t)kNumKernels);
+constexpr int64_t kNaFlags = kNaStatus + 256;
+constexpr int64_t kNaCounters = kNaFlags + 256;
+constexpr int64_t kNaBinOf = kNaCounters + 256;
+constexpr int64_t kNaOrder = kNaBinOf + align256(4 * (int64_t)SWGB_NOALLOC_MAX_PAIRS);
+constexpr int64_t kNaBoundary = kNaOrder + align256(4 * (int64_t)SWGB_NOALLOC_MAX_PAIRS);
+constexpr int64_t kNaEnd = kNaBoundary + 8 * kNoallocSlots * (int64_t)SWGB_NOALLOC_MAX_QUERY_LENGTH;
+static_assert(kNaEnd <= kNoallocBytes, "no-alloc scratch layout exceeds the array");
+
+// flag bits written by noalloc_check_kernel
+constexpr int32_t kFlagBadCode = 1;
+constexpr int32_t kFlagTooLong = 2;
+constexpr int32_t kFlagBadOffsets = 4;
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch
+    int sm_count = 0;
+    int blocks_per_sm[2][kClasses][kNumShapes] = {};
+};
+
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SWGB_NOALLOC_SCRATCH_BYTES];
+
+// One warp per sequence: codes must be < 24, lengths in [0, max_len].
+__global__ void noalloc_check_kernel(const uint8_t* __restrict__ res, const int64_t* __restrict__ off,
+                                     int64_t n, int64_t max_len, int32_t* flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    int32_t f = 0;
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < n; k += warps) {
+        const int64_t b = off[k], e = off[k + 1];
+        if (e < b) {
+            f |= kFlagBadOffsets;
+            continue;
+        }
+        if (e - b > max_len) f |= kFlagTooLong;
+        for (int64_t i = b + lane; i < e; i += 32)
+            if (res[i] >= kAlpha) f |= kFlagBadCode;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+namespace {
+
+// Same acceptance rule as swgb_align, without building any error string.
+int noalloc_score_args(const swgb_params* params, ScoreArgs* sc, int* max_score) {
+    if (!params || !params->matrix) return SWGB_EINVAL;
+    if (params->gap_open < 0 || params->gap_extend < 1) return SWGB_EINVAL;
+    if (params->flags & ~(SWGB_FORCE_INT32 | SWGB_TIMING)) return SWGB_EINVAL;
+    const int oe = params->gap_open + params->gap_extend;
+    int mx = 0;
+    for (int k = 0; k < kAlpha * kAlpha; ++k) mx = std::max<int>(mx, params->matrix[k]);
+    if (oe > 127 || mx + oe > 127) return SWGB_EINVAL;
+    for (int x = 0; x < kProfileRows; ++x)
+        for (int y = 0; y < kMatStride; ++y) {
+            int v = kPadProfile;
+            if (x < kAlpha && y < kAlpha) v = params->matrix[x * kAlpha + y] + oe;
+            sc->prof[x][y] = (int8_t)v;
+        }
+    sc->go = params->gap_open;
+    sc->ge = params->gap_extend;
+    *max_score = mx;
+    return SWGB_OK;
+}
+
+int noalloc_cuda(cudaError_t e) {
+    return e == cudaSuccess ? SWGB_OK : SWGB_ECUDA;
+}
+
+#define NA_CK(call)                                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return noalloc_cuda(e_); \
+    } while (0)
+
+// First call on a device (with that device current): resolve the array's
+// device address and configure the kernels.
+int noalloc_setup(int dev, NoallocDevice** out) {
+    if (dev < 0 || dev >= kNoallocMaxDevices) return SWGB_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        NA_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        NA_CK(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        for (int dir = 0; dir < 2; ++dir)
+            for (int c = 0; c < kClasses; ++c)
+                for (int s = 0; s < kNumShapes; ++s) {
+                    NA_CK(dp_configure(c, s, dir == 1));
+                    d.blocks_per_sm[dir][c][s] = std::max(1, dp_blocks_per_sm(c, s, dir == 1));
+                }
+        d.base = static_cast<unsigned char*>(ptr);
+        d.ready = true;
+    }
+    *out = &d;
+    return SWGB_OK;
+}
+
+}  // namespace
+
+SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offsets, int64_t n_q,
+                                   const uint8_t* r_codes, const int64_t* r_offsets, int64_t n_r,
+                                   const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                                   swgb_record* out, void* stream) {
+    if (n_q < 0 || n_r < 0 || n_pairs < 0) return SWGB_EINVAL;
+    if ((n_q > 0 && !q_offsets) || (n_r > 0 && !r_offsets)) return SWGB_EINVAL;
+    if (n_pairs > 0 && (!pairs || !out)) return SWGB_EINVAL;
+    if (n_q > INT32_MAX || n_r > INT32_MAX) return SWGB_ETOOBIG;
+    if (n_pairs > SWGB_NOALLOC_MAX_PAIRS) return SWGB_ETOOBIG;
+    ScoreArgs sc;
+    int max_score = 0;
+    int rc = noalloc_score_args(params, &sc, &max_score);
+    if (rc) return rc;
+    if (n_pairs == 0) return SWGB_OK;
+
+    int dev = 0;
+    NA_CK(cudaGetDevice(&dev));
+    NoallocDevice* d = nullptr;
+    rc = noalloc_setup(dev, &d);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = d->base;
+
+    Workspace ws{};
+    ws.hist = reinterpret_cast<uint32_t*>(base + kNaHist);
+    ws.scan = reinterpret_cast<uint32_t*>(base + kNaScan);
+    ws.cursor = reinterpret_cast<uint32_t*>(base + kNaCursor);
+    ws.task_ctr = reinterpret_cast<uint32_t*>(base + kNaTask);
+    ws.status = reinterpret_cast<int32_t*>(base + kNaStatus);
+    ws.counters = reinterpret_cast<unsigned long long*>(base + kNaCounters);
+    ws.bin_of = reinterpret_cast<int32_t*>(base + kNaBinOf);
+    ws.order = reinterpret_cast<int32_t*>(base + kNaOrder);
+    ws.boundary = reinterpret_cast<uint2*>(base + kNaBoundary);
+    ws.boundary_stride = SWGB_NOALLOC_MAX_QUERY_LENGTH;
+    ws.boundary_slots = kNoallocSlots;
+    int32_t* flags = reinterpret_cast<int32_t*>(base + kNaFlags);
+
+    // the array keeps the previous call's contents: clear what starts at zero
+    NA_CK(cudaMemsetAsync(base + kNaStatus, 0, kNaBinOf - kNaStatus, st));
+    NA_CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * 2 * kNumKernels, st));
+
+    // sizes and residue codes, checked on the device before any DP launch
+    const int64_t check_blocks = std::max<int64_t>(1, std::min<int64_t>(((std::max(n_q, n_r) + 7) / 8),
+                                                                       (int64_t)d->sm_count * 8));
+    if (n_q > 0)
+        noalloc_check_kernel<<<(unsigned)check_blocks, 256, 0, st>>>(q_codes, q_offsets, n_q,
+                                                                     SWGB_NOALLOC_MAX_QUERY_LENGTH, flags);
+    if (n_r > 0)
+        noalloc_check_kernel<<<(unsigned)check_blocks, 256, 0, st>>>(r_codes, r_offsets, n_r,
+                                                                     SWGB_MAX_LENGTH, flags);
+    NA_CK(cudaGetLastError());
+    int32_t host_flags = 0;
+    NA_CK(cudaMemcpyAsync(&host_flags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    if (host_flags & kFlagBadOffsets) return SWGB_ERANGE;
+    if (host_flags & kFlagTooLong) return SWGB_ETOOBIG;
+    if (host_flags & kFlagBadCode) return SWGB_EBADRES;
+
+    const SeqView qv{q_codes, q_offsets, n_q}, rv{r_codes, r_offsets, n_r};
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool rev = dir == 1;
+        NA_CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st));
+        NA_CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, params->flags & SWGB_FORCE_INT32, max_score,
+                          ws, st));
+        NA_CK(launch_scan(ws, st));
+        NA_CK(launch_scatter(n_pairs, ws, st));
+        for (int c = 0; c < kClasses; ++c) {
+            for (int s = 0; s < kNumShapes; ++s) {
+                DPArgs a;
+                a.q = qv;
+                a.r = rv;
+                a.pairs = pairs;
+                a.order = ws.order;
+                a.scan = ws.scan;
+                a.task_ctr = ws.task_ctr + dir * kNumKernels + c * kNumShapes + s;
+                a.out = out;
+                a.status = ws.status;
+                a.boundary = ws.boundary;
+                a.boundary_stride = ws.boundary_stride;
+                a.boundary_slots = ws.boundary_slots;
+                a.first_bucket = shape_first_bucket(c, s);
+                a.end_bucket = shape_end_bucket(c, s);
+                a.sc = sc;
+                int64_t grid = (int64_t)d->sm_count * d->blocks_per_sm[dir][c][s];
+                const int64_t per_block = (int64_t)(kDPThreads / 32) * (32 / kShapeG[s]) * (c == 0 ? 2 : 1);
+                grid = std::min(grid, (n_pairs + per_block - 1) / per_block);
+                if (s == kNumShapes - 1) grid = std::min<int64_t>(grid, kNoallocChunkBlocks);
+                NA_CK(launch_dp(c, s, rev, a, (int)std::max<int64_t>(grid, 1), st));
+            }
+        }
+    }
+    int32_t status = 0;
+    NA_CK(cudaMemcpyAsync(&status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    return status;
 }

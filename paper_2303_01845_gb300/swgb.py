@@ -22,6 +22,7 @@ SWGB_EBADRES = -3
 SWGB_ENOMEM = -4
 SWGB_ECUDA = -5
 SWGB_EINTERNAL = -6
+SWGB_ETOOBIG = -7
 
 SWGB_ALPHABET_SIZE = 24
 SWGB_MAX_LENGTH = 65536
@@ -29,11 +30,15 @@ SWGB_SEQ_ASCII = 0x1
 SWGB_SEQ_DEVICE = 0x2
 SWGB_FORCE_INT32 = 0x1
 SWGB_TIMING = 0x2
+SWGB_NOALLOC_SCRATCH_BYTES = 32 << 20
+SWGB_NOALLOC_MAX_PAIRS = 1 << 19
+SWGB_NOALLOC_MAX_QUERY_LENGTH = 4096
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 
 _NAMES = {SWGB_EINVAL: "EINVAL", SWGB_ERANGE: "ERANGE", SWGB_EBADRES: "EBADRES",
-          SWGB_ENOMEM: "ENOMEM", SWGB_ECUDA: "ECUDA", SWGB_EINTERNAL: "EINTERNAL"}
+          SWGB_ENOMEM: "ENOMEM", SWGB_ECUDA: "ECUDA", SWGB_EINTERNAL: "EINTERNAL",
+          SWGB_ETOOBIG: "ETOOBIG"}
 
 
 class SwgbError(RuntimeError):
@@ -82,6 +87,9 @@ _SIGS = [
     ("swgb_last_stats", ctypes.c_int, [_VP, ctypes.POINTER(swgb_stats)]),
     ("swgb_probe_addmax_rate", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int)]),
+    ("swgb_align_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
+                                          _VP, ctypes.c_int64, ctypes.POINTER(swgb_params), _VP,
+                                          _VP]),
 ]
 
 _lib = None
@@ -259,6 +267,33 @@ def swgb_probe_addmax_rate(ctx):
     n = ctypes.c_int()
     _check(ctx, load().swgb_probe_addmax_rate(ctx, ctypes.byref(r), ctypes.byref(n)))
     return r.value, n.value
+
+
+def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, out, stream=None):
+    """Allocation-free alignment for callers that cannot allocate device memory
+    while they align (a pool or arena owns the device, or the footprint must
+    stay fixed): every argument is a caller-owned CUDA tensor (codes uint8,
+    offsets int64, pairs int32 [P, 2], out int32 [P, 5]) and the library's
+    scratch is a fixed array compiled into it.  Synchronous.  Limits:
+    SWGB_NOALLOC_MAX_PAIRS pairs per call, queries up to
+    SWGB_NOALLOC_MAX_QUERY_LENGTH residues; larger inputs raise ETOOBIG."""
+    for t in (q_codes, q_offsets, r_codes, r_offsets, pairs, out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise TypeError("swgb_align_noalloc takes contiguous CUDA tensors")
+    n = pairs.shape[0]
+    if out.numel() < 5 * n:
+        raise ValueError("out must hold P x 5 int32")
+    rc = load().swgb_align_noalloc(_ptr(q_codes), _ptr(q_offsets), q_offsets.shape[0] - 1,
+                                   _ptr(r_codes), _ptr(r_offsets), r_offsets.shape[0] - 1,
+                                   _ptr(pairs), n, ctypes.byref(params), _ptr(out),
+                                   _stream_handle(stream))
+    if rc != SWGB_OK:
+        extra = ""
+        if rc == SWGB_ETOOBIG:
+            extra = ("a size exceeds the fixed limits: at most %d pairs per call and %d residues "
+                     "per query" % (SWGB_NOALLOC_MAX_PAIRS, SWGB_NOALLOC_MAX_QUERY_LENGTH))
+        raise SwgbError(rc, "swgb_align_noalloc failed" + (": " + extra if extra else ""))
+    return out
 
 
 class Aligner:
