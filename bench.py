@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_2m")
     ap.add_argument("--pairs", type=int, default=0,
-                    help="use only the first N pairs of the workload (profiling cases)")
+                    help="use an evenly strided subset of N pairs (profiling cases)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -127,12 +127,13 @@ def make_workload(name, mat, pairs=0):
     from paper_2303_01845_gb300 import workload
     wl = workload.generate(name, mat)
     if pairs and pairs < len(wl.pairs):
-        wl = wl.subset(np.arange(pairs))
+        # an evenly strided subset keeps the mix of lengths and relatedness
+        wl = wl.subset(np.linspace(0, len(wl.pairs) - 1, pairs).astype(np.int64))
     return wl
 
 
 def workload_name(args):
-    return args.workload + ("[:%d]" % args.pairs if args.pairs else "")
+    return args.workload + ("[%d strided]" % args.pairs if args.pairs else "")
 
 
 def cpu_oracle_sample(wl, mat, target_s, seed=7):

@@ -66,6 +66,12 @@ struct swgb_ctx {
     int32_t* d_encode_flag = nullptr;  // residue check of seqset loads
     int blocks_per_sm[2][kClasses][kNumShapes] = {};
     cudaEvent_t ev[6] = {};
+    // the DP kernels of one direction run on the caller's stream and these
+    // side streams (forked and joined with events), so that their tails overlap
+    static constexpr int kSide = 3;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kSide] = {};
     bool timed = false;
     cudaStream_t last_stream = nullptr;
     int32_t last_launches = 0;
@@ -120,6 +126,23 @@ cudaError_t grow(T** p, int64_t* cap, int64_t need) {
 
 SeqView view(const swgb_seqset* s) { return SeqView{s->d_res, s->d_off, s->n}; }
 
+// Row / column maxima of a validated 24 x 24 matrix for the 16-bit test.
+ClassArgs make_class_args(const int8_t* m, int max_score, bool force32) {
+    ClassArgs ca{};
+    ca.max_score = max_score;
+    for (int x = 0; x < kAlpha; ++x) {
+        int rmax = 0, cmax = 0;
+        for (int y = 0; y < kAlpha; ++y) {
+            rmax = std::max<int>(rmax, m[x * kAlpha + y]);
+            cmax = std::max<int>(cmax, m[y * kAlpha + x]);
+        }
+        ca.rowmax[x] = (int8_t)rmax;
+        ca.colmax[x] = (int8_t)cmax;
+    }
+    ca.force32 = force32 ? 1 : 0;
+    return ca;
+}
+
 }  // namespace
 
 SWGB_EXPORT void swgb_blosum62(int8_t* out) {
@@ -173,6 +196,14 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
             }
     for (auto& ev : ctx->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "cudaEventCreate");
+    if ((e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(e, "cudaEventCreate");
+    for (int k = 0; k < swgb_ctx::kSide; ++k) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "cudaEventCreate");
+    }
     *out = ctx;
     return SWGB_OK;
 }
@@ -197,6 +228,11 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
     cudaFree(ctx->d_probe_sink);
     for (auto& ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    for (int k = 0; k < swgb_ctx::kSide; ++k) {
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+        if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+    }
     delete ctx;
 }
 
@@ -325,7 +361,7 @@ int make_score_args(swgb_ctx* ctx, const swgb_params* params, ScoreArgs* sc, int
 
 // Pairs handled by one persistent block of a (class, shape) kernel.
 int64_t pairs_per_block(int cls, int shape) {
-    return (int64_t)(kDPThreads / 32) * (32 / kShapeG[shape]) * (cls == 0 ? 2 : 1);
+    return (int64_t)(kDPThreads / 32) * (32 / shape_G(shape)) * (cls == 0 ? 2 : 1);
 }
 
 int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int32_t* pairs,
@@ -337,24 +373,32 @@ int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int
     Workspace& ws = ctx->ws;
     const bool force32 = params->flags & SWGB_FORCE_INT32;
     const bool timed = params->flags & SWGB_TIMING;
+    const ClassArgs ca = make_class_args(params->matrix, max_score, force32);
     CK(grow(&ws.bin_of, &ctx->bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     CK(grow(&ws.order, &ctx->order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
-    // chunk-boundary rows for the chunked shape: one row per resident warp
+    // chunk-boundary rows: one row per resident warp of every kernel that can
+    // tile long references; kernels run concurrently, so each has its own region
+    int64_t region_off[kClasses][kNumShapes] = {};
+    int64_t region_slots[kClasses][kNumShapes] = {};
     {
-        const int64_t stride = ((q->max_len + 31) / 32) * 32;
+        const int64_t stride = std::max<int64_t>(((q->max_len + 31) / 32) * 32, 32);
         int64_t slots = 0;
-        for (int d = 0; d < 2; ++d)
-            for (int c = 0; c < kClasses; ++c)
-                slots = std::max<int64_t>(slots, (int64_t)ctx->sm_count *
-                                                     ctx->blocks_per_sm[d][c][kNumShapes - 1] *
-                                                     (kDPThreads / 32));
+        for (int c = 0; c < kClasses; ++c)
+            for (int s = kFirstChunkable; s < kNumShapes; ++s) {
+                int64_t n = 0;
+                for (int d = 0; d < 2; ++d)
+                    n = std::max<int64_t>(n, (int64_t)ctx->sm_count * ctx->blocks_per_sm[d][c][s] *
+                                                 (kDPThreads / 32));
+                region_off[c][s] = slots;
+                region_slots[c][s] = n;
+                slots += n;
+            }
         if (stride > ws.boundary_stride || slots > ws.boundary_slots || !ws.boundary) {
             cudaFree(ws.boundary);
             ws.boundary = nullptr;
             ws.boundary_stride = ws.boundary_slots = 0;
-            CK(cudaMalloc(&ws.boundary, sizeof(uint2) * (size_t)std::max<int64_t>(stride, 32) * slots),
-               "boundary alloc");
-            ws.boundary_stride = std::max<int64_t>(stride, 32);
+            CK(cudaMalloc(&ws.boundary, sizeof(uint2) * (size_t)stride * slots), "boundary alloc");
+            ws.boundary_stride = stride;
             ws.boundary_slots = slots;
         }
     }
@@ -368,13 +412,20 @@ int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int
     for (int dir = 0; dir < 2; ++dir) {
         const bool rev = dir == 1;
         CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st), "memset");
-        CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, force32, max_score, ws, st), "keys kernel");
+        CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, ca, ws, st), "keys kernel");
         CK(launch_scan(ws, st), "scan kernel");
         CK(launch_scatter(n_pairs, ws, st), "scatter kernel");
         launches += 3;
         if (timed) CK(cudaEventRecord(ctx->ev[rev ? 3 : 1], st), "event");
+        CK(cudaEventRecord(ctx->fork_ev, st), "event");
+        for (int k = 0; k < swgb_ctx::kSide; ++k)
+            CK(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0), "stream wait");
+        int rr = 0;   // round robin over {st, side...}, largest tiles first
         for (int c = 0; c < kClasses; ++c) {
-            for (int s = 0; s < kNumShapes; ++s) {
+            for (int s = kNumShapes - 1; s >= 0; --s) {
+                cudaStream_t ks = (rr % (swgb_ctx::kSide + 1)) == 0 ? st
+                                                                   : ctx->side[rr % (swgb_ctx::kSide + 1) - 1];
+                ++rr;
                 DPArgs a;
                 a.q = qv;
                 a.r = rv;
@@ -384,18 +435,23 @@ int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int
                 a.task_ctr = ws.task_ctr + dir * kNumKernels + c * kNumShapes + s;
                 a.out = out;
                 a.status = ws.status;
-                a.boundary = ws.boundary;
+                const bool chunkable = s >= kFirstChunkable;
+                a.boundary = chunkable ? ws.boundary + region_off[c][s] * ws.boundary_stride : nullptr;
                 a.boundary_stride = ws.boundary_stride;
-                a.boundary_slots = ws.boundary_slots;
+                a.boundary_slots = chunkable ? region_slots[c][s] : 0;
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
                 a.sc = sc;
                 int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[dir][c][s];
                 const int64_t need = (n_pairs + pairs_per_block(c, s) - 1) / pairs_per_block(c, s);
                 grid = std::max<int64_t>(1, std::min(grid, need));
-                CK(launch_dp(c, s, rev, a, (int)grid, st), "dp kernel");
+                CK(launch_dp(c, s, rev, a, (int)grid, ks), "dp kernel");
                 ++launches;
             }
+        }
+        for (int k = 0; k < swgb_ctx::kSide; ++k) {
+            CK(cudaEventRecord(ctx->join_ev[k], ctx->side[k]), "event");
+            CK(cudaStreamWaitEvent(st, ctx->join_ev[k], 0), "stream wait");
         }
         if (timed) CK(cudaEventRecord(ctx->ev[rev ? 4 : 2], st), "event");
     }
@@ -535,7 +591,7 @@ SWGB_EXPORT int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm
 namespace {
 
 constexpr int64_t kNoallocBytes = SWGB_NOALLOC_SCRATCH_BYTES;
-constexpr int kNoallocChunkBlocks = 152;   // grid cap of the 512-row-chunk kernels
+constexpr int kNoallocChunkBlocks = 304;   // grid cap of the kernels that tile long references
 constexpr int64_t kNoallocSlots = (int64_t)kNoallocChunkBlocks * (kDPThreads / 32);
 constexpr int kNoallocMaxDevices = 64;
 
@@ -710,11 +766,11 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
     if (host_flags & kFlagBadCode) return SWGB_EBADRES;
 
     const SeqView qv{q_codes, q_offsets, n_q}, rv{r_codes, r_offsets, n_r};
+    const ClassArgs ca = make_class_args(params->matrix, max_score, params->flags & SWGB_FORCE_INT32);
     for (int dir = 0; dir < 2; ++dir) {
         const bool rev = dir == 1;
         NA_CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st));
-        NA_CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, params->flags & SWGB_FORCE_INT32, max_score,
-                          ws, st));
+        NA_CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, ca, ws, st));
         NA_CK(launch_scan(ws, st));
         NA_CK(launch_scatter(n_pairs, ws, st));
         for (int c = 0; c < kClasses; ++c) {
@@ -735,9 +791,9 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
                 a.end_bucket = shape_end_bucket(c, s);
                 a.sc = sc;
                 int64_t grid = (int64_t)d->sm_count * d->blocks_per_sm[dir][c][s];
-                const int64_t per_block = (int64_t)(kDPThreads / 32) * (32 / kShapeG[s]) * (c == 0 ? 2 : 1);
+                const int64_t per_block = (int64_t)(kDPThreads / 32) * (32 / shape_G(s)) * (c == 0 ? 2 : 1);
                 grid = std::min(grid, (n_pairs + per_block - 1) / per_block);
-                if (s == kNumShapes - 1) grid = std::min<int64_t>(grid, kNoallocChunkBlocks);
+                if (s >= kFirstChunkable) grid = std::min<int64_t>(grid, kNoallocChunkBlocks);
                 NA_CK(launch_dp(c, s, rev, a, (int)std::max<int64_t>(grid, 1), st));
             }
         }

@@ -35,14 +35,19 @@ struct SeqView {
 
 // ---- bucketing -------------------------------------------------------------
 // A pair's DP is laid out with the reference along the lanes ("held", rows of
-// a tile) and the query streamed through the wavefront.  Tile shapes (lanes
-// per pair group G x rows per lane R):
-constexpr int kNumShapes = 5;
-constexpr int kShapeG[kNumShapes] = {4, 8, 16, 32, 32};
-constexpr int kShapeR[kNumShapes] = {8, 8, 8, 8, 16};
-constexpr int kChunkRows = 512;               // rows per chunk of the last shape
-constexpr int kChunkBuckets = 16;             // chunk-count buckets of the last shape
-constexpr int kBucketsPerClass = (kNumShapes - 1) + kChunkBuckets;
+// a tile) and the query streamed through the wavefront.  Tile shapes: G lanes
+// per pair group x R rows per lane.
+//   shape: 0      1       2      3       4       5        6       7        8
+//   (G,R): (4,8)  (4,12)  (8,8)  (8,12)  (16,8)  (16,12)  (32,8)  (32,12)  (32,16)
+//   rows:  32     48      64     96      128     192      256     384      512
+// Shapes from kFirstChunkable on (one group per warp) also cover references
+// longer than one tile, in chunks of G*R rows.
+constexpr int kNumShapes = 9;
+constexpr int kFirstChunkable = 6;
+__host__ __device__ constexpr int shape_G(int s) { return s < 2 ? 4 : s < 4 ? 8 : s < 6 ? 16 : 32; }
+__host__ __device__ constexpr int shape_R(int s) { return s == 8 ? 16 : (s & 1) ? 12 : 8; }
+constexpr int kChunkBuckets = 16;             // chunk-count buckets of a chunkable shape
+constexpr int kBucketsPerClass = kFirstChunkable + (kNumShapes - kFirstChunkable) * kChunkBuckets;
 constexpr int kClasses = 2;                   // 0 = packed 16x2, 1 = 32-bit
 constexpr int kNumBuckets = kClasses * kBucketsPerClass;
 constexpr int kQBins = 1024;                  // streamed-length bins per bucket
@@ -50,29 +55,53 @@ constexpr int kQBinShift = 2;                 // 4 residues per bin
 constexpr int kNumBins = kNumBuckets * kQBins;
 constexpr int kNumKernels = kClasses * kNumShapes;
 
-__host__ __device__ inline int shape_of(int64_t held_len) {
-    if (held_len <= 32) return 0;
-    if (held_len <= 64) return 1;
-    if (held_len <= 128) return 2;
-    if (held_len <= 256) return 3;
-    return 4;
+// Tile of a pair: the shape (and chunk count) of least modelled cost, where a
+// pair costs (streamed steps incl. the G-1 wavefront fill) x chunks x G x
+// (R + 4) -- R cell updates plus about four rows' worth of per-step work per
+// lane, shared by the 32/G groups of a warp.
+__host__ __device__ inline void choose_shape(int64_t lq, int64_t lr, int* shape, int* nch) {
+    int64_t best = -1;
+    for (int s = 0; s < kNumShapes; ++s) {
+        const int64_t rows = (int64_t)shape_G(s) * shape_R(s);
+        int64_t n = 1;
+        if (lr > rows) {
+            if (s < kFirstChunkable) continue;
+            n = (lr + rows - 1) / rows;
+        }
+        const int64_t cost = (lq + shape_G(s) - 1) * n * shape_G(s) * (shape_R(s) + 4);
+        if (best < 0 || cost < best) {
+            best = cost;
+            *shape = s;
+            *nch = (int)n;
+        }
+    }
 }
 
-__host__ __device__ inline int bucket_of(int cls, int64_t held_len) {
-    int s = shape_of(held_len);
-    if (s < kNumShapes - 1) return cls * kBucketsPerClass + s;
-    int64_t chunks = (held_len + kChunkRows - 1) / kChunkRows;
-    int cb = (int)(chunks < kChunkBuckets ? chunks : kChunkBuckets) - 1;
-    return cls * kBucketsPerClass + (kNumShapes - 1) + cb;
-}
-
-// first and one-past-last bucket of (class, shape)
 __host__ __device__ inline int shape_first_bucket(int cls, int s) {
-    return cls * kBucketsPerClass + s;
+    return cls * kBucketsPerClass +
+           (s < kFirstChunkable ? s : kFirstChunkable + (s - kFirstChunkable) * kChunkBuckets);
 }
 __host__ __device__ inline int shape_end_bucket(int cls, int s) {
-    return s < kNumShapes - 1 ? cls * kBucketsPerClass + s + 1 : (cls + 1) * kBucketsPerClass;
+    return shape_first_bucket(cls, s) + (s < kFirstChunkable ? 1 : kChunkBuckets);
 }
+// more chunks first: the longest pairs start first in the persistent grid
+__host__ __device__ inline int bucket_of(int cls, int s, int nch) {
+    const int b = shape_first_bucket(cls, s);
+    if (s < kFirstChunkable) return b;
+    return b + kChunkBuckets - (nch < kChunkBuckets ? nch : kChunkBuckets);
+}
+
+// What the keys kernel needs to put a pair on the packed 16-bit path: the
+// score can only pass 32767 if max_score * min(lq, lr) does, and never exceeds
+// min(sum_i rowmax[q_i], sum_j colmax[r_j]) (every aligned query residue
+// contributes at most its best substitution score, likewise every reference
+// residue; gaps only subtract).
+struct ClassArgs {
+    int32_t max_score;            // max(0, largest matrix entry)
+    int8_t rowmax[kMatStride];    // max(0, max_y s(x, y)) per query code x
+    int8_t colmax[kMatStride];    // max(0, max_x s(x, y)) per reference code y
+    int32_t force32;
+};
 
 // Per-call device workspace (owned by the context).
 struct Workspace {
@@ -117,7 +146,7 @@ enum Counter {
 cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
                           int32_t* bad_flag, cudaStream_t st);
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
-                        swgb_record* out, bool reverse, bool force32, int max_score,
+                        swgb_record* out, bool reverse, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scan(const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st);
@@ -127,7 +156,7 @@ cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int gri
 // Blocks per SM the DP kernel of (class, shape, direction) can keep resident.
 int dp_blocks_per_sm(int cls, int shape, bool reverse);
 // Threads per block of every DP kernel.
-constexpr int kDPThreads = 128;
+constexpr int kDPThreads = 64;
 size_t dp_smem_bytes(int cls, int shape);
 cudaError_t dp_configure(int cls, int shape, bool reverse);
 cudaError_t launch_probe_addmax(unsigned long long* cycles, uint32_t* sink, int blocks,

@@ -87,14 +87,24 @@ __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
     atomicCAS(status, 0, code);
 }
 
+// Upper bound of the score of a pair from its residues (see ClassArgs).
+__device__ int64_t score_bound(const uint8_t* __restrict__ q, int64_t lq, const uint8_t* __restrict__ r,
+                               int64_t lr, const ClassArgs& ca) {
+    int64_t bq = 0, br = 0;
+    for (int64_t i = 0; i < lq; ++i) bq += ca.rowmax[q[i]];
+    for (int64_t j = 0; j < lr; ++j) br += ca.colmax[r[j]];
+    return bq < br ? bq : br;
+}
+
 __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pairs,
-                            int64_t n_pairs, swgb_record* out, int reverse, int force32,
-                            int max_score, Workspace ws) {
+                            int64_t n_pairs, swgb_record* out, int reverse, ClassArgs ca,
+                            Workspace ws) {
     unsigned long long cells = 0, n16 = 0, n32 = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += stride) {
         int bin = -1;
         int64_t lq = 0, lr = 0;
+        int cls = 0;
         if (!reverse) {
             const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
             if (qi < 0 || qi >= q.n || ri < 0 || ri >= r.n) {
@@ -106,6 +116,10 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 if (lq == 0 || lr == 0) {
                     zero_record(&out[p]);
                     lq = lr = 0;
+                } else if (ca.force32) {
+                    cls = 1;
+                } else if ((int64_t)ca.max_score * (lq < lr ? lq : lr) > 32767) {
+                    cls = score_bound(q.res + q.off[qi], lq, r.res + r.off[ri], lr, ca) > 32767;
                 }
             }
         } else {
@@ -113,14 +127,16 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
             if (rec.score > 0) {
                 lq = (int64_t)rec.q_end + 1;
                 lr = (int64_t)rec.r_end + 1;
+                // every cell of the reversed prefixes scores at most S
+                cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
             }
         }
         if (lq > 0) {
-            const int64_t mn = lq < lr ? lq : lr;
-            const int cls = (!force32 && (int64_t)max_score * mn <= 32767) ? 0 : 1;
             int64_t qb = lq >> kQBinShift;
             if (qb > kQBins - 1) qb = kQBins - 1;
-            bin = bucket_of(cls, lr) * kQBins + (kQBins - 1 - (int)qb);
+            int shape = 0, nch = 1;
+            choose_shape(lq, lr, &shape, &nch);
+            bin = bucket_of(cls, shape, nch) * kQBins + (kQBins - 1 - (int)qb);
             atomicAdd(&ws.hist[bin], 1u);
             cells += (unsigned long long)(lq * lr);
             if (cls == 0) ++n16; else ++n32;
@@ -146,13 +162,12 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
 }
 
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
-                        swgb_record* out, bool reverse, bool force32, int max_score,
+                        swgb_record* out, bool reverse, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     int64_t blocks = (n_pairs + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, reverse ? 1 : 0,
-                                                  force32 ? 1 : 0, max_score, ws);
+    keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, reverse ? 1 : 0, ca, ws);
     return cudaGetLastError();
 }
 
@@ -246,6 +261,20 @@ struct Lane<true> {
                              ((uint32_t)((4 + b) | 8) << 12);
         return prmt(a, c, sel);
     }
+    // first row r (per half) with v[r] == m, where m is the maximum of v
+    template <int R>
+    __device__ __forceinline__ static void first_rows(const uint32_t (&v)[R], uint32_t m, int (&rows)[2]) {
+        int r0 = R - 1, r1 = R - 1;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) {
+            bool hi, lo;
+            (void)__vibmax_s16x2(v[r], m, &hi, &lo);   // v >= m  <=>  v == m
+            r0 = lo ? r : r0;
+            r1 = hi ? r : r1;
+        }
+        rows[0] = r0;
+        rows[1] = r1;
+    }
 };
 
 template <>
@@ -264,7 +293,42 @@ struct Lane<false> {
         const uint32_t sel = (uint32_t)b | (s << 4) | (s << 8) | (s << 12);
         return prmt(a, 0u, sel);
     }
+    template <int R>
+    __device__ __forceinline__ static void first_rows(const uint32_t (&v)[R], uint32_t m, int (&rows)[1]) {
+        int r0 = R - 1;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) r0 = (v[r] == m) ? r : r0;
+        rows[0] = r0;
+    }
 };
+
+// Maximum of v[0..R) and init as a tree of 3-input maxima (depth 2-3).
+template <bool P16, int R>
+__device__ __forceinline__ uint32_t tree_max(const uint32_t (&v)[R], uint32_t init) {
+    using L = Lane<P16>;
+    if constexpr (R == 8) {
+        const uint32_t a = L::max3(v[0], v[1], v[2]);
+        const uint32_t b = L::max3(v[3], v[4], v[5]);
+        const uint32_t c = L::max3(v[6], v[7], init);
+        return L::max3(a, b, c);
+    } else if constexpr (R == 12) {
+        const uint32_t a = L::max3(v[0], v[1], v[2]);
+        const uint32_t b = L::max3(v[3], v[4], v[5]);
+        const uint32_t c = L::max3(v[6], v[7], v[8]);
+        const uint32_t d = L::max3(v[9], v[10], v[11]);
+        return L::max3(L::max3(a, b, c), d, init);
+    } else {
+        static_assert(R == 16, "rows per lane must be 8, 12 or 16");
+        const uint32_t a = L::max3(v[0], v[1], v[2]);
+        const uint32_t b = L::max3(v[3], v[4], v[5]);
+        const uint32_t c = L::max3(v[6], v[7], v[8]);
+        const uint32_t d = L::max3(v[9], v[10], v[11]);
+        const uint32_t e = L::max3(v[12], v[13], v[14]);
+        const uint32_t f = L::max3(a, b, c);
+        const uint32_t g = L::max3(d, e, v[15]);
+        return L::max3(f, g, init);
+    }
+}
 
 // R profile bytes as R/4 words
 template <int R>
@@ -272,6 +336,8 @@ struct ProfWords {
     uint32_t w[R / 4];
 };
 
+// A lane's R profile bytes start at a multiple of R, so R = 8 and 16 load as
+// one 8- or 16-byte word and R = 12 as three 4-byte words.
 template <int R>
 __device__ __forceinline__ ProfWords<R> load_prof(const int8_t* p) {
     ProfWords<R> out;
@@ -279,8 +345,12 @@ __device__ __forceinline__ ProfWords<R> load_prof(const int8_t* p) {
         const uint2 v = *reinterpret_cast<const uint2*>(p);
         out.w[0] = v.x;
         out.w[1] = v.y;
+    } else if constexpr (R == 12) {
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+        out.w[0] = q[0];
+        out.w[1] = q[1];
+        out.w[2] = q[2];
     } else {
-        static_assert(R == 16, "rows per lane must be 8 or 16");
         const uint4 v = *reinterpret_cast<const uint4*>(p);
         out.w[0] = v.x;
         out.w[1] = v.y;
@@ -294,6 +364,11 @@ template <int R>
 __device__ __forceinline__ void store_prof(int8_t* p, const uint32_t (&w)[R / 4]) {
     if constexpr (R == 8) {
         *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    } else if constexpr (R == 12) {
+        uint32_t* q = reinterpret_cast<uint32_t*>(p);
+        q[0] = w[0];
+        q[1] = w[1];
+        q[2] = w[2];
     } else {
         *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -310,15 +385,44 @@ __device__ __forceinline__ bool better(int v, int i, int j, int bv, int bi, int 
 // ---------------------------------------------------------------------------
 constexpr int kSmatBytes = kProfileRows * kMatStride;   // 800
 constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
+constexpr int kBoundEvery = 8;   // steps between refreshes of the group's score bound
 
 template <int G, int R, bool P16>
 __host__ __device__ constexpr int dp_prof_bytes_per_warp() {
     return (32 / G) * (P16 ? 2 : 1) * kProfileRows * G * R;
 }
 
+// Packed per-half maximum over the G lanes of a group.
+template <bool P16, int G>
+__device__ __forceinline__ uint32_t group_max(uint32_t v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const uint32_t o = __shfl_xor_sync(kFull, v, off, G);
+        v = Lane<P16>::max3(v, o, o);
+    }
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ int group_min(int v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(kFull, v, off, G));
+    return v;
+}
+
 // REV = false: forward pass over q x r -> score and end cell.
 // REV = true : local DP over the reversed prefixes q[q_end..0] x r[r_end..0]
-//              of each scored pair -> start cell.
+//              of each scored pair -> start cell.  The score S is known, so the
+//              pass stops once the wavefront is past the first step holding S.
+//
+// Position of the maximum.  Every lane keeps the running maximum lb of its
+// cells.  When the maximum of a step's R rows passes lb and also reaches T --
+// a lower bound of the pair's final score: the largest lb of the group,
+// refreshed every kBoundEvery steps -- the lane copies its R registers (a
+// snapshot per pair half) and the step.  The first row holding the value is
+// read from the snapshot once per chunk.  A lane whose maximum never reached T
+// holds no cell of the final score, so skipping its positions loses nothing;
+// ties with T are recorded.
 template <int G, int R, bool P16, bool REV>
 __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     using L = Lane<P16>;
@@ -340,6 +444,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const int gl = lane % G;   // lane within the group
     int8_t* prof = reinterpret_cast<int8_t*>(smem + kSmatRegion) +
                    (size_t)warp * dp_prof_bytes_per_warp<G, R, P16>() + (size_t)g * PACK * PROF;
+    const int8_t* plane = prof + gl * R;   // this lane's rows within a profile row
 
     const int64_t begin = a.scan[(int64_t)a.first_bucket * kQBins];
     const int64_t end = a.scan[(int64_t)a.end_bucket * kQBins];
@@ -349,6 +454,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const int oe = a.sc.go + a.sc.ge;
     const uint32_t NOE = L::splat(-oe);
     const uint32_t NE = L::splat(-a.sc.ge);
+    const uint32_t ONE = L::splat(1);
 
     for (;;) {
         uint32_t task = 0;
@@ -396,6 +502,17 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             ls_w = max(ls_w, __shfl_xor_sync(kFull, ls_w, off));
             nch = max(nch, __shfl_xor_sync(kFull, nch, off));
         }
+        // a chunked task needs this warp's boundary row; a launch wider than
+        // the rows provided is a host error: report it, touch nothing
+        if (nch > 1 && (bnd == nullptr || slot >= a.boundary_slots || ls_w > a.boundary_stride)) {
+            if (lane == 0) set_status(a.status, SWGB_EINTERNAL);
+            continue;
+        }
+        // query letter of streamed position i (pad outside the pair)
+        auto code_at = [&](int h, int i) -> int {
+            if (i < 0 || i >= lq[h]) return kPadCode;
+            return REV ? qp[h][lq[h] - 1 - i] : qp[h][i];
+        };
 
         int bv[PACK], bi[PACK], bj[PACK];
 #pragma unroll
@@ -404,6 +521,13 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             bi[h] = INT_MAX;
             bj[h] = INT_MAX;
         }
+        uint32_t T = NOE;   // lower bound of the final H - (o + e), per half
+        // reverse pass: the score S is known; fi = first streamed step at which
+        // this lane recorded a cell of value S, per half
+        int fi[PACK];
+#pragma unroll
+        for (int h = 0; h < PACK; ++h) fi[h] = INT_MAX;
+        int ls_c = ls;   // streamed positions the chunk still needs
 
         for (int c = 0; c < nch; ++c) {
             const int jc = c * ROWS;          // first held row of the chunk
@@ -442,85 +566,159 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 F[r] = NOE;
             }
             uint32_t hin_prev = NOE, eout = NOE, hout = NOE;
-            uint32_t lb = NOE;   // best H - (o + e) seen by this lane in this chunk
-            int ci[PACK], cj[PACK];
+            uint32_t lb = NOE;                      // this lane's maximum in this chunk
+            uint32_t lbT = L::addmax(lb, ONE, T);   // per half max(lb + 1, T)
+            uint32_t snap[PACK][R];                 // registers at the last recorded step
+            int si[PACK], sv[PACK];
 #pragma unroll
-            for (int h = 0; h < PACK; ++h) ci[h] = cj[h] = -1;
+            for (int h = 0; h < PACK; ++h) {
+                si[h] = -1;
+                sv[h] = INT_MIN;
+#pragma unroll
+                for (int r = 0; r < R; ++r) snap[h][r] = NOE;
+            }
 
             const bool read_bnd = (c > 0) && (gl == 0);
             const bool write_bnd = (c + 1 < nch) && (gl == G - 1);
             const int steps = ls_w + G - 1;
-            for (int t = 0; t < steps; ++t) {
+            int stop_w = INT_MAX;   // reverse pass: warp-uniform last useful step
+
+            // software pipeline: profile words of the next step and the query
+            // letter of the step after are fetched one step ahead
+            ProfWords<R> pwn[PACK];
+            int xn[PACK];
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) {
+                pwn[h] = load_prof<R>(plane + h * PROF + code_at(h, -gl) * ROWS);
+                xn[h] = code_at(h, 1 - gl);
+            }
+            uint2 bcur = make_uint2(NOE, NOE);
+            if (read_bnd && ls_c > 0) bcur = bnd[0];
+            uint32_t ein = NOE, hin = NOE;   // from lane gl-1, previous step
+
+            for (int t = 0; t < steps && t <= stop_w; ++t) {
                 const int i = t - gl;
-                uint32_t ein = __shfl_up_sync(kFull, eout, 1, G);
-                uint32_t hin = __shfl_up_sync(kFull, hout, 1, G);
-                if (i < 0 || i >= ls) continue;
+                const bool active = (i >= 0) && (i < ls_c);
+                ProfWords<R> pw[PACK];
+#pragma unroll
+                for (int h = 0; h < PACK; ++h) {
+                    pw[h] = pwn[h];
+                    pwn[h] = load_prof<R>(plane + h * PROF + xn[h] * ROWS);
+                    xn[h] = code_at(h, i + 2);
+                }
                 if (gl == 0) {
                     if (read_bnd) {
-                        const uint2 v = bnd[i];
-                        ein = v.x;
-                        hin = v.y;
+                        ein = bcur.x;
+                        hin = bcur.y;
+                        if (i + 1 < ls_c) bcur = bnd[i + 1];
                     } else {
                         ein = NOE;
                         hin = NOE;
                     }
                 }
-                // profile words of the query letter at i, per pair
-                ProfWords<R> pw[PACK];
+                if (active) {
+                    uint32_t hd = hin_prev;   // H(i-1, j-1) - (o + e) for the first row
+                    uint32_t e = ein;         // E(i, first row)
 #pragma unroll
-                for (int h = 0; h < PACK; ++h) {
-                    const int x = (i < lq[h]) ? (REV ? qp[h][lq[h] - 1 - i] : qp[h][i]) : kPadCode;
-                    pw[h] = load_prof<R>(prof + h * PROF + x * ROWS + gl * R);
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
+                        const uint32_t u = L::addmax(hd, s, F[r]);       // max(Hdiag + s, F)
+                        const uint32_t U = L::addmax(u, NOE, NOE);      // max(u, 0) - (o + e)
+                        const uint32_t hn = L::addmax(e, NOE, U);       // H - (o + e)
+                        e = L::addmax(e, NE, U);                        // E of the next row
+                        F[r] = L::addmax(F[r], NE, hn);                 // F of the next query position
+                        hd = Hop[r];
+                        Hop[r] = hn;
+                    }
+                    eout = e;
+                    hout = Hop[R - 1];
+                    hin_prev = hin;
+                    if (write_bnd) bnd[i] = make_uint2(eout, hout);
                 }
-                uint32_t hd = hin_prev;   // H(i-1, j-1) - (o + e) for the first row
-                uint32_t e = ein;         // E(i, first row)
+                const uint32_t e_next = __shfl_up_sync(kFull, eout, 1, G);
+                const uint32_t h_next = __shfl_up_sync(kFull, hout, 1, G);
+                if (active) {
+                    const uint32_t m = tree_max<P16, R>(Hop, lb);
+                    bool rec_h[2];
+                    if constexpr (P16) {
+                        bool hi, lo;
+                        (void)__vibmax_s16x2(m, lbT, &hi, &lo);   // m >= max(lb + 1, T)
+                        rec_h[0] = lo;
+                        rec_h[1] = hi;
+                    } else {
+                        rec_h[0] = (int)m >= (int)lbT;
+                        rec_h[1] = false;
+                    }
+                    if (rec_h[0] || rec_h[1]) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
-                    const uint32_t u = L::addmax(hd, s, F[r]);       // max(Hdiag + s, F)
-                    const uint32_t U = L::addmax(u, NOE, NOE);      // max(u, 0) - (o + e)
-                    const uint32_t hn = L::addmax(e, NOE, U);       // H - (o + e)
-                    e = L::addmax(e, NE, U);                        // E of the next row
-                    F[r] = L::addmax(F[r], NE, hn);                 // F of the next query position
-                    hd = Hop[r];
-                    Hop[r] = hn;
-                }
-                eout = e;
-                hout = Hop[R - 1];
-                hin_prev = hin;
-                if (write_bnd) bnd[i] = make_uint2(eout, hout);
-
-                // ---- running maximum of this lane (first cell reaching it)
-                uint32_t m = lb;
+                        for (int h = 0; h < PACK; ++h) {
+                            if (rec_h[h]) {
+                                si[h] = i;
+                                sv[h] = L::get(m, h);
 #pragma unroll
-                for (int r = 0; r < R; r += 2) m = L::max3(m, Hop[r], Hop[r + 1]);
-                if (m != lb) {
-#pragma unroll
-                    for (int h = 0; h < PACK; ++h) {
-                        const int mh = L::get(m, h);
-                        if (mh > L::get(lb, h)) {
-                            int rr = R - 1;
-#pragma unroll
-                            for (int r = R - 1; r >= 0; --r)
-                                if (L::get(Hop[r], h) == mh) rr = r;
-                            ci[h] = i;
-                            cj[h] = jl + rr;
+                                for (int r = 0; r < R; ++r) snap[h][r] = Hop[r];
+                                if (REV && sv[h] == target[h] - oe && i < fi[h]) fi[h] = i;
+                            }
                         }
                     }
                     lb = m;
+                    lbT = L::addmax(m, ONE, T);
                 }
-            }
-            // ---- merge the chunk's best into the lane's best
+                if ((t & (kBoundEvery - 1)) == kBoundEvery - 1) {
+                    T = group_max<P16, G>(L::max3(lb, T, T));
+                    lbT = L::addmax(lb, ONE, T);
+                    if constexpr (REV) {
+                        // once every half of every group has met S at some step,
+                        // cells of later steps can no longer be the first such cell
+                        // after the wavefront has passed that step in all lanes
+                        int stop = 0;
 #pragma unroll
-            for (int h = 0; h < PACK; ++h) {
-                if (ci[h] >= 0) {
-                    const int v = L::get(lb, h);
-                    if (better(v, ci[h], cj[h], bv[h], bi[h], bj[h])) {
-                        bv[h] = v;
-                        bi[h] = ci[h];
-                        bj[h] = cj[h];
+                        for (int h = 0; h < PACK; ++h) {
+                            const int gm = group_min<G>(fi[h]);   // every lane shuffles
+                            const int f = pid[h] >= 0 ? gm : 0;
+                            stop = (stop == INT_MAX || f == INT_MAX) ? INT_MAX : max(stop, f);
+                        }
+                        if (stop != INT_MAX) stop += G - 1;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1)
+                            stop = max(stop, __shfl_xor_sync(kFull, stop, off));
+                        stop_w = stop;
                     }
                 }
+                ein = e_next;
+                hin = h_next;
+            }
+            // ---- the lane's candidate of this chunk: the recorded step and the
+            // first row of the snapshot holding the value, if it is the lane's
+            // maximum
+            T = group_max<P16, G>(L::max3(lb, T, T));
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) {
+                if (si[h] >= 0 && sv[h] == L::get(lb, h)) {
+                    int row = R - 1;
+#pragma unroll
+                    for (int r = R - 1; r >= 0; --r)
+                        if (L::get(snap[h][r], h) == sv[h]) row = r;
+                    if (better(sv[h], si[h], jl + row, bv[h], bi[h], bj[h])) {
+                        bv[h] = sv[h];
+                        bi[h] = si[h];
+                        bj[h] = jl + row;
+                    }
+                }
+            }
+            if constexpr (REV) {
+                // later chunks hold later reference rows: only steps before the
+                // first one that met S can still give a row-major-earlier cell
+                int need = 0;
+#pragma unroll
+                for (int h = 0; h < PACK; ++h) {
+                    const int f = group_min<G>(fi[h]);
+                    need = max(need, f == INT_MAX ? lq[h] : min(lq[h], f));
+                }
+                ls_c = need;
+                ls_w = need;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) ls_w = max(ls_w, __shfl_xor_sync(kFull, ls_w, off));
             }
             __syncwarp();
         }
@@ -569,9 +767,7 @@ using DPFn = void (*)(const DPArgs);
 
 template <int S, bool P16, bool REV>
 constexpr DPFn dp_fn() {
-    constexpr int G = S == 0 ? 4 : S == 1 ? 8 : S == 2 ? 16 : 32;
-    constexpr int R = S == 4 ? 16 : 8;
-    return &dp_kernel<G, R, P16, REV>;
+    return &dp_kernel<shape_G(S), shape_R(S), P16, REV>;
 }
 
 template <bool P16, bool REV>
@@ -581,7 +777,11 @@ DPFn dp_pick(int shape) {
         case 1: return dp_fn<1, P16, REV>();
         case 2: return dp_fn<2, P16, REV>();
         case 3: return dp_fn<3, P16, REV>();
-        default: return dp_fn<4, P16, REV>();
+        case 4: return dp_fn<4, P16, REV>();
+        case 5: return dp_fn<5, P16, REV>();
+        case 6: return dp_fn<6, P16, REV>();
+        case 7: return dp_fn<7, P16, REV>();
+        default: return dp_fn<8, P16, REV>();
     }
 }
 
@@ -591,7 +791,7 @@ static DPFn dp_lookup(int cls, int shape, bool reverse) {
 }
 
 size_t dp_smem_bytes(int cls, int shape) {
-    const int G = kShapeG[shape], R = kShapeR[shape];
+    const int G = shape_G(shape), R = shape_R(shape);
     const int pack = cls == 0 ? 2 : 1;
     const size_t per_warp = (size_t)(32 / G) * pack * kProfileRows * G * R;
     return kSmatRegion + per_warp * (kDPThreads / 32);

@@ -76,9 +76,29 @@ def test_gap_settings_and_asymmetric_matrix(aligner, oracle_mod, blosum, plain10
                 oracle_records(oracle_mod, sub, asym, 7, 2), sub)
 
 
-HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257,
-                511, 512, 513, 1023, 1024, 1025, 1537, 2999]
+HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129,
+                191, 192, 193, 255, 256, 257, 383, 384, 385, 511, 512, 513, 767, 768, 769,
+                1023, 1024, 1025, 1537, 2999]
 STREAM_LENGTHS = [1, 2, 3, 30, 31, 32, 33, 100, 257, 512, 513, 1200]
+
+
+def tile_of(lq, lr):
+    """(shape, chunks) the library's cost model gives a pair: shapes are
+    (G lanes, R rows) = (4,8) (4,12) (8,8) (8,12) (16,8) (16,12) (32,8) (32,12)
+    (32,16); the last three also tile longer references in chunks."""
+    best = None
+    for s, (G, R) in enumerate([(4, 8), (4, 12), (8, 8), (8, 12), (16, 8), (16, 12),
+                                (32, 8), (32, 12), (32, 16)]):
+        rows = G * R
+        n = 1
+        if lr > rows:
+            if s < 6:
+                continue
+            n = -(-lr // rows)
+        cost = (lq + G - 1) * n * G * (R + 4)
+        if best is None or cost < best[0]:
+            best = (cost, s, n)
+    return best[1], best[2]
 
 
 def ragged_workload(seed, mat, held=HELD_LENGTHS, stream=STREAM_LENGTHS):
@@ -105,6 +125,9 @@ def ragged_workload(seed, mat, held=HELD_LENGTHS, stream=STREAM_LENGTHS):
 
 def test_ragged_lengths_all_shapes(aligner, oracle_mod, blosum):
     wl = ragged_workload(11, blosum)
+    tiles = {tile_of(wl.q_len[q], wl.r_len[r]) for q, r in wl.pairs}
+    assert {s for s, _ in tiles} == set(range(9))
+    assert {s for s, n in tiles if n >= 2} == {7, 8}   # (32, 8) never wins once chunked
     assert_same(gpu_records(aligner, wl, params(blosum)),
                 oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
 
@@ -115,9 +138,21 @@ def test_ragged_lengths_int32(aligner, oracle_mod, blosum):
                 oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
 
 
+def int32_expected(mat, q, r):
+    """A pair needs the 32-bit path iff its score bound passes 32767: the
+    bound is min(sum of the best score of each query letter, sum of the best
+    score of each reference letter), checked only when 11 * min(lq, lr) does."""
+    m = np.asarray(mat, np.int64)
+    if max(0, int(m.max())) * min(len(q), len(r)) <= 32767:
+        return False
+    rowmax = np.maximum(m.max(axis=1), 0)
+    colmax = np.maximum(m.max(axis=0), 0)
+    return min(int(rowmax[q].sum()), int(colmax[r].sum())) > 32767
+
+
 def test_self_alignment_closed_form_across_the_int16_limit(aligner, blosum):
-    """Self-alignments have S = sum of the diagonal over the full length; past
-    2978 residues 11 * n exceeds 32767 and the pair takes the 32-bit path."""
+    """Self-alignments have S = sum of the diagonal over the full length; the
+    longest ones pass 32767 and take the 32-bit path."""
     from paper_2303_01845_gb300 import workload
     rng = np.random.default_rng(13)
     lens = [1, 5, 64, 300, 2978, 2979, 3500, 5000, 9000]
@@ -129,7 +164,8 @@ def test_self_alignment_closed_form_across_the_int16_limit(aligner, blosum):
         n = len(s)
         assert tuple(got[k]) == (int(m[s, s].sum()), 0, n - 1, 0, n - 1)
     st = aligner.stats()
-    assert st["n_int32_pairs"] == sum(1 for n in lens if 11 * n > 32767)
+    assert st["n_int32_pairs"] == sum(1 for s in seqs if int32_expected(blosum, s, s))
+    assert st["n_int32_pairs"] >= 1
 
 
 def test_tryptophan_runs_at_the_int16_limit(aligner, oracle_mod, blosum):
@@ -144,8 +180,13 @@ def test_tryptophan_runs_at_the_int16_limit(aligner, oracle_mod, blosum):
         seqs.append(s)
     pairs = [(a, b) for a in range(len(seqs)) for b in range(len(seqs))]
     wl = workload.from_sequences(seqs, seqs, pairs)
-    assert_same(gpu_records(aligner, wl, params(blosum)),
-                oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+    want = oracle_records(oracle_mod, wl, blosum, 11, 1)
+    assert_same(gpu_records(aligner, wl, params(blosum)), want, wl)
+    # scores right at the 16-bit limit are exercised on both paths
+    n32 = sum(int32_expected(blosum, seqs[a], seqs[b]) for a, b in pairs)
+    assert aligner.stats()["n_int32_pairs"] == n32
+    assert 0 < n32 < len(pairs)
+    assert want[:, 0].max() > 32767 and (want[:, 0] > 32000).sum() > n32
 
 
 def test_edge_cases(aligner, oracle_mod, blosum):
@@ -272,9 +313,12 @@ def test_batched_2m_sampled_parity(aligner, oracle_mod, blosum, batched2m, torch
     assert (out[~pos] == [0, -1, -1, -1, -1]).all()
     assert ((0 <= qs) & (qs <= qe) & (qe < ql))[pos].all()
     assert ((0 <= rs) & (rs <= re_) & (re_ < rl))[pos].all()
-    int32_pairs = np.nonzero(11 * np.minimum(ql, rl) > 32767)[0]
+    long_pairs = np.nonzero(11 * np.minimum(ql, rl) > 32767)[0]
+    int32_pairs = np.array([p for p in long_pairs if int32_expected(
+        blosum, wl.q_res[wl.q_off[p]:wl.q_off[p + 1]], wl.r_res[wl.r_off[p]:wl.r_off[p + 1]])],
+        dtype=np.int64)
     assert st["n_int32_pairs"] == len(int32_pairs)
     rng = np.random.default_rng(17)
-    sample = np.union1d(rng.choice(len(wl.pairs), size=20000, replace=False), int32_pairs)
+    sample = np.union1d(rng.choice(len(wl.pairs), size=20000, replace=False), long_pairs)
     sub = wl.subset(sample)
     assert_same(out[sample], oracle_records(oracle_mod, sub, blosum, 11, 1), sub)
