@@ -54,6 +54,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the job's step time); value itself
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput: units every rank processed in `steps` steps
+    divided by the (max over ranks) time of those steps."""
+    return world * units_per_rank * steps / (total_ms / 1e3)
+
+
 def sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
@@ -278,14 +295,10 @@ def run_ours(args):
         barrier()
     clock = clocks.summary()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     cells = stats["forward_cells"]
-    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
-    aln_per_s = world * P * args.steps / (total_ms / 1e3)
+    value = job_rate(cells, world, args.steps, total_ms) / 1e9
+    aln_per_s = job_rate(P, world, args.steps, total_ms)
     fwd_mean = statistics.mean(fwd_ms)
     achieved = cells / (fwd_mean / 1e3) / 1e9
 

@@ -183,6 +183,31 @@ int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out);
  * counter.  Also reports the SM count.  Synchronous.  Errors: EINVAL, ECUDA. */
 int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_count);
 
+/* ---- plans: one batch shape captured into a CUDA graph ----
+ * The persistent launches of swgb_align (bucketing, forward and reverse DP
+ * kernels on the context's streams) for fixed buffers, captured once into a
+ * CUDA graph and replayed by swgb_plan_launch.  A plan owns its bucketing and
+ * boundary workspace; it shares the context's status word and counters, so
+ * swgb_sync and swgb_last_stats report its launches.  The buffers (sets,
+ * pairs, out) must stay allocated while the plan exists; their CONTENTS may
+ * change between launches (new pairs of the same count, sequences reloaded
+ * into sets whose capacity and longest length do not grow).  Launches of one
+ * context (plans and swgb_align) must be ordered, as for swgb_align. */
+typedef struct swgb_plan swgb_plan;
+
+/* Captures the pipeline for (queries, refs, pairs[n_pairs], params, out).
+ * Allocates the plan's workspace.  Errors: EINVAL, ENOMEM, ECUDA. */
+int swgb_plan_create(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                     const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                     swgb_record* out, swgb_plan** plan);
+
+/* Replays the captured pipeline on `stream` (asynchronous; device errors are
+ * returned by swgb_sync).  Errors: EINVAL, ECUDA. */
+int swgb_plan_launch(swgb_plan* plan, void* stream);
+
+/* Frees a plan.  NULL is ignored. */
+void swgb_plan_destroy(swgb_plan* plan);
+
 /* ---- allocation-free variant ----
  * The paper has no counterpart of this call; it exists for callers that
  * cannot allocate device memory while they align -- code running inside a

@@ -52,13 +52,23 @@ static const char* kBlosum62Rows[kAlpha] = {
     "-4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4 -4  1",
 };
 
+// Growable device workspace of one issuing context: a context owns one for
+// swgb_align, every plan owns its own (a captured graph keeps its pointers).
+// The status word and counters are the context's and are shared.
+struct Store {
+    Workspace ws{};
+    int64_t bin_capacity = 0;    // ws.bin_of
+    int64_t order_capacity = 0;  // ws.order
+    int64_t region_off[kClasses][kNumShapes] = {};
+    int64_t region_slots[kClasses][kNumShapes] = {};
+};
+
 struct swgb_ctx {
     int device = 0;
     int sm_count = 0;
     std::string err;
-    Workspace ws{};
-    int64_t bin_capacity = 0;        // ws.bin_of
-    int64_t order_capacity = 0;      // ws.order
+    Store store;                     // workspace of swgb_align
+    Workspace& ws = store.ws;        // (status and counters live here)
     int32_t* d_pairs = nullptr;      // staging for swgb_align_host
     swgb_record* d_out = nullptr;
     int64_t d_pairs_capacity = 0;
@@ -364,44 +374,74 @@ int64_t pairs_per_block(int cls, int shape) {
     return (int64_t)(kDPThreads / 32) * (32 / shape_G(shape)) * (cls == 0 ? 2 : 1);
 }
 
-int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int32_t* pairs,
-            int64_t n_pairs, const swgb_params* params, swgb_record* out, cudaStream_t st) {
+// Fixed-size parts of a store (status and counters come from the context).
+int alloc_store_fixed(swgb_ctx* ctx, Store& st) {
+    Workspace& ws = st.ws;
+    CK(cudaMalloc(&ws.hist, sizeof(uint32_t) * kNumBins), "alloc");
+    CK(cudaMalloc(&ws.scan, sizeof(uint32_t) * (kNumBins + 1)), "alloc");
+    CK(cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins), "alloc");
+    CK(cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels), "alloc");
+    return SWGB_OK;
+}
+
+void free_store(Store& st, bool with_status) {
+    Workspace& ws = st.ws;
+    cudaFree(ws.hist);
+    cudaFree(ws.scan);
+    cudaFree(ws.cursor);
+    cudaFree(ws.bin_of);
+    cudaFree(ws.order);
+    cudaFree(ws.task_ctr);
+    cudaFree(ws.boundary);
+    if (with_status) {
+        cudaFree(ws.status);
+        cudaFree(ws.counters);
+    }
+    ws = Workspace{};
+}
+
+// Grows a store for n_pairs pairs against the query set q (may allocate).
+int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, int64_t n_pairs) {
+    Workspace& ws = store.ws;
+    CK(grow(&ws.bin_of, &store.bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
+    CK(grow(&ws.order, &store.order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
+    // chunk-boundary rows: one row per resident warp of every kernel that can
+    // tile long references; kernels run concurrently, so each has its own region
+    const int64_t stride = std::max<int64_t>(((q->max_len + 31) / 32) * 32, 32);
+    int64_t slots = 0;
+    for (int c = 0; c < kClasses; ++c)
+        for (int s = kFirstChunkable; s < kNumShapes; ++s) {
+            int64_t n = 0;
+            for (int d = 0; d < 2; ++d)
+                n = std::max<int64_t>(n, (int64_t)ctx->sm_count * ctx->blocks_per_sm[d][c][s] *
+                                             (kDPThreads / 32));
+            store.region_off[c][s] = slots;
+            store.region_slots[c][s] = n;
+            slots += n;
+        }
+    if (stride > ws.boundary_stride || slots > ws.boundary_slots || !ws.boundary) {
+        cudaFree(ws.boundary);
+        ws.boundary = nullptr;
+        ws.boundary_stride = ws.boundary_slots = 0;
+        CK(cudaMalloc(&ws.boundary, sizeof(uint2) * (size_t)stride * slots), "boundary alloc");
+        ws.boundary_stride = stride;
+        ws.boundary_slots = slots;
+    }
+    return SWGB_OK;
+}
+
+// Enqueues the whole pipeline on st (no allocation: the store is prepared).
+int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_seqset* r,
+            const int32_t* pairs, int64_t n_pairs, const swgb_params* params, swgb_record* out,
+            cudaStream_t st) {
     ScoreArgs sc;
     int max_score = 0;
     int rc = make_score_args(ctx, params, &sc, &max_score);
     if (rc) return rc;
-    Workspace& ws = ctx->ws;
+    const Workspace& ws = store.ws;
     const bool force32 = params->flags & SWGB_FORCE_INT32;
     const bool timed = params->flags & SWGB_TIMING;
     const ClassArgs ca = make_class_args(params->matrix, max_score, force32);
-    CK(grow(&ws.bin_of, &ctx->bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
-    CK(grow(&ws.order, &ctx->order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
-    // chunk-boundary rows: one row per resident warp of every kernel that can
-    // tile long references; kernels run concurrently, so each has its own region
-    int64_t region_off[kClasses][kNumShapes] = {};
-    int64_t region_slots[kClasses][kNumShapes] = {};
-    {
-        const int64_t stride = std::max<int64_t>(((q->max_len + 31) / 32) * 32, 32);
-        int64_t slots = 0;
-        for (int c = 0; c < kClasses; ++c)
-            for (int s = kFirstChunkable; s < kNumShapes; ++s) {
-                int64_t n = 0;
-                for (int d = 0; d < 2; ++d)
-                    n = std::max<int64_t>(n, (int64_t)ctx->sm_count * ctx->blocks_per_sm[d][c][s] *
-                                                 (kDPThreads / 32));
-                region_off[c][s] = slots;
-                region_slots[c][s] = n;
-                slots += n;
-            }
-        if (stride > ws.boundary_stride || slots > ws.boundary_slots || !ws.boundary) {
-            cudaFree(ws.boundary);
-            ws.boundary = nullptr;
-            ws.boundary_stride = ws.boundary_slots = 0;
-            CK(cudaMalloc(&ws.boundary, sizeof(uint2) * (size_t)stride * slots), "boundary alloc");
-            ws.boundary_stride = stride;
-            ws.boundary_slots = slots;
-        }
-    }
 
     int launches = 0;
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
@@ -436,9 +476,9 @@ int enqueue(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r, const int
                 a.out = out;
                 a.status = ws.status;
                 const bool chunkable = s >= kFirstChunkable;
-                a.boundary = chunkable ? ws.boundary + region_off[c][s] * ws.boundary_stride : nullptr;
+                a.boundary = chunkable ? ws.boundary + store.region_off[c][s] * ws.boundary_stride : nullptr;
                 a.boundary_stride = ws.boundary_stride;
-                a.boundary_slots = chunkable ? region_slots[c][s] : 0;
+                a.boundary_slots = chunkable ? store.region_slots[c][s] : 0;
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
                 a.sc = sc;
@@ -490,7 +530,9 @@ SWGB_EXPORT int swgb_align(swgb_ctx* ctx, const swgb_seqset* queries, const swgb
         CK(cudaMemsetAsync(ctx->ws.counters, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream), "memset");
         return SWGB_OK;
     }
-    return enqueue(ctx, queries, refs, pairs, n_pairs, params, out, (cudaStream_t)stream);
+    rc = prepare_store(ctx, ctx->store, queries, n_pairs);
+    if (rc) return rc;
+    return enqueue(ctx, ctx->store, queries, refs, pairs, n_pairs, params, out, (cudaStream_t)stream);
 }
 
 SWGB_EXPORT int swgb_sync(swgb_ctx* ctx, void* stream) {
@@ -802,4 +844,94 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
     NA_CK(cudaMemcpyAsync(&status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// Plans: the pipeline for fixed buffers captured once into a CUDA graph
+// ---------------------------------------------------------------------------
+struct swgb_plan {
+    swgb_ctx* ctx = nullptr;
+    Store store;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool timed = false;
+    int32_t launches = 0;
+    int64_t n_pairs = 0;
+};
+
+SWGB_EXPORT void swgb_plan_destroy(swgb_plan* plan) {
+    if (!plan) return;
+    if (plan->ctx) cudaSetDevice(plan->ctx->device);
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    free_store(plan->store, false);
+    delete plan;
+}
+
+SWGB_EXPORT int swgb_plan_create(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                                 const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                                 swgb_record* out, swgb_plan** out_plan) {
+    if (!ctx || !out_plan) return SWGB_EINVAL;
+    *out_plan = nullptr;
+    ctx->err.clear();
+    if (n_pairs < 1 || n_pairs > INT32_MAX) return fail(ctx, SWGB_EINVAL, "plan: n_pairs must be in [1, 2^31)");
+    if (!pairs || !out) return fail(ctx, SWGB_EINVAL, "pairs or out is NULL");
+    int rc = check_sets(ctx, queries, refs);
+    if (rc) return rc;
+    ScoreArgs probe;
+    int max_score = 0;
+    rc = make_score_args(ctx, params, &probe, &max_score);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    swgb_plan* plan = new (std::nothrow) swgb_plan();
+    if (!plan) return fail(ctx, SWGB_ENOMEM, "plan: host allocation");
+    plan->ctx = ctx;
+    plan->store.ws.status = ctx->ws.status;
+    plan->store.ws.counters = ctx->ws.counters;
+    rc = alloc_store_fixed(ctx, plan->store);
+    if (!rc) rc = prepare_store(ctx, plan->store, queries, n_pairs);
+    if (rc) {
+        swgb_plan_destroy(plan);
+        return rc;
+    }
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        swgb_plan_destroy(plan);
+        return cuda_fail(ctx, e, "plan: begin capture");
+    }
+    rc = enqueue(ctx, plan->store, queries, refs, pairs, n_pairs, params, out, cs);
+    e = cudaStreamEndCapture(cs, &plan->graph);
+    cudaStreamDestroy(cs);
+    if (rc == SWGB_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "plan: end capture");
+    if (rc == SWGB_OK) {
+        e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "plan: instantiate");
+    }
+    if (rc) {
+        swgb_plan_destroy(plan);
+        return rc;
+    }
+    plan->timed = ctx->timed;
+    plan->launches = ctx->last_launches;
+    plan->n_pairs = n_pairs;
+    ctx->last_pairs = 0;
+    ctx->last_launches = 0;
+    ctx->timed = false;
+    *out_plan = plan;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_plan_launch(swgb_plan* plan, void* stream) {
+    if (!plan || !plan->ctx || !plan->exec) return SWGB_EINVAL;
+    swgb_ctx* ctx = plan->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream), "graph launch");
+    ctx->timed = plan->timed;
+    ctx->last_stream = (cudaStream_t)stream;
+    ctx->last_launches = plan->launches;
+    ctx->last_pairs = plan->n_pairs;
+    return SWGB_OK;
 }

@@ -596,9 +596,14 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             if (read_bnd && ls_c > 0) bcur = bnd[0];
             uint32_t ein = NOE, hin = NOE;   // from lane gl-1, previous step
 
+            // Lanes step in lock step without branching on their own range:
+            // before its first position a lane sees only pad letters and
+            // "minus infinity" inputs from the lane before, which leaves its
+            // initial state unchanged; after its last position it computes pad
+            // cells, which score below the best real cell feeding them and can
+            // never be the pair's maximum.  Only the boundary store is guarded.
             for (int t = 0; t < steps && t <= stop_w; ++t) {
                 const int i = t - gl;
-                const bool active = (i >= 0) && (i < ls_c);
                 ProfWords<R> pw[PACK];
 #pragma unroll
                 for (int h = 0; h < PACK; ++h) {
@@ -607,37 +612,43 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                     xn[h] = code_at(h, i + 2);
                 }
                 if (gl == 0) {
-                    if (read_bnd) {
-                        ein = bcur.x;
-                        hin = bcur.y;
-                        if (i + 1 < ls_c) bcur = bnd[i + 1];
-                    } else {
-                        ein = NOE;
-                        hin = NOE;
-                    }
+                    // past the rows the previous chunk handed over, lane 0 sees
+                    // "minus infinity": cells there score alignments confined to
+                    // this chunk, never above the pair's score
+                    const bool take = read_bnd && i < ls_c;
+                    ein = take ? bcur.x : NOE;
+                    hin = take ? bcur.y : NOE;
                 }
-                if (active) {
-                    uint32_t hd = hin_prev;   // H(i-1, j-1) - (o + e) for the first row
-                    uint32_t e = ein;         // E(i, first row)
+                if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
+                // phase 1, independent rows: u = max(Hdiag + s, F), U = max(u, 0) - (o + e)
+                uint32_t U[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
-                        const uint32_t u = L::addmax(hd, s, F[r]);       // max(Hdiag + s, F)
-                        const uint32_t U = L::addmax(u, NOE, NOE);      // max(u, 0) - (o + e)
-                        const uint32_t hn = L::addmax(e, NOE, U);       // H - (o + e)
-                        e = L::addmax(e, NE, U);                        // E of the next row
-                        F[r] = L::addmax(F[r], NE, hn);                 // F of the next query position
-                        hd = Hop[r];
-                        Hop[r] = hn;
-                    }
-                    eout = e;
-                    hout = Hop[R - 1];
-                    hin_prev = hin;
-                    if (write_bnd) bnd[i] = make_uint2(eout, hout);
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
+                    const uint32_t hd = r == 0 ? hin_prev : Hop[r - 1];
+                    U[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
                 }
+                // phase 2, the chain along the rows: H - (o + e) and E of the next row
+                uint32_t e = ein;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t hn = L::addmax(e, NOE, U[r]);
+                    e = L::addmax(e, NE, U[r]);
+                    U[r] = hn;
+                }
+                // phase 3, independent rows: F of the next query position
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    F[r] = L::addmax(F[r], NE, U[r]);
+                    Hop[r] = U[r];
+                }
+                eout = e;
+                hout = Hop[R - 1];
+                hin_prev = hin;
+                if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(eout, hout);
                 const uint32_t e_next = __shfl_up_sync(kFull, eout, 1, G);
                 const uint32_t h_next = __shfl_up_sync(kFull, hout, 1, G);
-                if (active) {
+                {
                     const uint32_t m = tree_max<P16, R>(Hop, lb);
                     bool rec_h[2];
                     if constexpr (P16) {

@@ -87,6 +87,10 @@ _SIGS = [
     ("swgb_last_stats", ctypes.c_int, [_VP, ctypes.POINTER(swgb_stats)]),
     ("swgb_probe_addmax_rate", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int)]),
+    ("swgb_plan_create", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64,
+                                        ctypes.POINTER(swgb_params), _VP, ctypes.POINTER(_VP)]),
+    ("swgb_plan_launch", ctypes.c_int, [_VP, _VP]),
+    ("swgb_plan_destroy", None, [_VP]),
     ("swgb_align_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                           _VP, ctypes.c_int64, ctypes.POINTER(swgb_params), _VP,
                                           _VP]),
@@ -267,6 +271,23 @@ def swgb_probe_addmax_rate(ctx):
     n = ctypes.c_int()
     _check(ctx, load().swgb_probe_addmax_rate(ctx, ctypes.byref(r), ctypes.byref(n)))
     return r.value, n.value
+
+
+def swgb_plan_create(ctx, queries, refs, pairs, params, out):
+    """Captures the pipeline for these CUDA buffers into a CUDA graph."""
+    h = _VP()
+    rc = load().swgb_plan_create(ctx, queries, refs, _ptr(pairs), pairs.shape[0],
+                                 ctypes.byref(params), _ptr(out), ctypes.byref(h))
+    _check(ctx, rc)
+    return h
+
+
+def swgb_plan_launch(ctx, plan, stream=None):
+    _check(ctx, load().swgb_plan_launch(plan, _stream_handle(stream)))
+
+
+def swgb_plan_destroy(plan):
+    load().swgb_plan_destroy(plan)
 
 
 def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, out, stream=None):

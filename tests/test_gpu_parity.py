@@ -322,3 +322,33 @@ def test_batched_2m_sampled_parity(aligner, oracle_mod, blosum, batched2m, torch
     sample = np.union1d(rng.choice(len(wl.pairs), size=20000, replace=False), long_pairs)
     sub = wl.subset(sample)
     assert_same(out[sample], oracle_records(oracle_mod, sub, blosum, 11, 1), sub)
+
+
+def test_plan_replays_the_pipeline(aligner, blosum, plain10k, torch_cuda):
+    """A plan captured into a CUDA graph gives the records swgb_align gives,
+    and replays new pair lists written into the same buffer."""
+    torch = torch_cuda
+    from paper_2303_01845_gb300 import swgb
+    q, r = device_sets(aligner, plain10k)
+    prm = params(blosum)
+    rng = np.random.default_rng(18)
+    pick1 = rng.choice(10000, size=3000, replace=False)
+    pick2 = rng.choice(10000, size=3000, replace=False)
+    pairs = torch.from_numpy(plain10k.pairs[pick1].copy()).cuda()
+    out = torch.zeros((3000, 5), dtype=torch.int32, device="cuda")
+    plan = swgb.swgb_plan_create(aligner.ctx, q.handle, r.handle, pairs, prm, out)
+    try:
+        want1 = aligner.align(q, r, pairs.clone(), prm).cpu().numpy()
+        swgb.swgb_plan_launch(aligner.ctx, plan)
+        swgb.swgb_sync(aligner.ctx)
+        assert (out.cpu().numpy() == want1).all()
+        assert aligner.stats()["forward_cells"] == int(
+            (plain10k.q_len[plain10k.pairs[pick1, 0]] * plain10k.r_len[plain10k.pairs[pick1, 1]]).sum())
+        pairs.copy_(torch.from_numpy(plain10k.pairs[pick2].copy()))
+        want2 = aligner.align(q, r, pairs.clone(), prm).cpu().numpy()
+        out.zero_()
+        swgb.swgb_plan_launch(aligner.ctx, plan)
+        swgb.swgb_sync(aligner.ctx)
+        assert (out.cpu().numpy() == want2).all()
+    finally:
+        swgb.swgb_plan_destroy(plan)
