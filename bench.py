@@ -44,6 +44,10 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune-pairs", type=int, default=200000,
+                    help="pairs of the batch the tile selection is tuned on")
+    ap.add_argument("--tile-overhead", type=int, default=-1,
+                    help="fixed tile-cost overhead instead of tuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -262,6 +266,19 @@ def run_ours(args):
     params = swgb.make_params(mat, 11, 1, timing=True)
     P = len(wl.pairs)
 
+    # tile selection tuned on an evenly strided sample of the batch (untimed)
+    if args.tile_overhead >= 0:
+        swgb.swgb_set_tile_overhead(al.ctx, args.tile_overhead)
+        tile_overhead = args.tile_overhead
+    else:
+        tune_n = min(P, args.tune_pairs)
+        tune_idx = torch.from_numpy(np.linspace(0, P - 1, tune_n).astype(np.int64)).to(dev)
+        tune_pairs = pairs[tune_idx].contiguous()
+        tune_out = torch.empty((tune_n, 5), dtype=torch.int32, device=dev)
+        tile_overhead, _ = swgb.swgb_autotune(al.ctx, q.handle, r.handle, tune_pairs, params,
+                                              tune_out, stream)
+        del tune_pairs, tune_out
+
     def step():
         swgb.swgb_align(al.ctx, q.handle, r.handle, pairs, params, out, stream)
 
@@ -327,7 +344,7 @@ def run_ours(args):
         "config": {"workload": workload_name(args), "pairs": P, "forward_cells": cells,
                    "reverse_cells": stats["reverse_cells"],
                    "int32_pairs": stats["n_int32_pairs"], "gap_open": 11, "gap_extend": 1,
-                   "matrix": "BLOSUM62",
+                   "matrix": "BLOSUM62", "tile_overhead": tile_overhead,
                    "l2": "inputs (%.2f GB of residues) exceed L2; no flush" %
                          ((len(wl.q_res) + len(wl.r_res)) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},

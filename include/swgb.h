@@ -183,6 +183,23 @@ int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out);
  * counter.  Also reports the SM count.  Synchronous.  Errors: EINVAL, ECUDA. */
 int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_count);
 
+/* ---- tile selection ----
+ * Every pair gets the tile (G lanes x R reference rows per lane, and a chunk
+ * count for long references) of least modelled cost
+ *     (query length + G - 1) x chunks x G x (R + overhead),
+ * where overhead is the per-step work of a lane counted in rows.  It is a
+ * context setting (default 6), read by each swgb_align and swgb_plan_create. */
+int swgb_set_tile_overhead(swgb_ctx* ctx, int overhead);  /* EINVAL unless 0..64 */
+int swgb_get_tile_overhead(const swgb_ctx* ctx);          /* current value */
+
+/* Times swgb_align on the given batch (device buffers, like swgb_align) for a
+ * fixed list of overhead values, keeps the fastest in ctx and reports it and
+ * its whole-call time in ms.  Synchronous; out receives the batch's records.
+ * The records do not depend on the setting.  Errors: those of swgb_align. */
+int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                  const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                  swgb_record* out, void* stream, int* best_overhead, float* best_ms);
+
 /* ---- plans: one batch shape captured into a CUDA graph ----
  * The persistent launches of swgb_align (bucketing, forward and reverse DP
  * kernels on the context's streams) for fixed buffers, captured once into a

@@ -73,8 +73,11 @@ struct swgb_ctx {
     swgb_record* d_out = nullptr;
     int64_t d_pairs_capacity = 0;
     int64_t d_out_capacity = 0;
-    int32_t* d_encode_flag = nullptr;  // residue check of seqset loads
-    int blocks_per_sm[2][kClasses][kNumShapes] = {};
+    int32_t* d_encode_flag = nullptr;  // [2]: residue check and largest code of seqset loads
+    // resident blocks per SM of each DP kernel, [profile variant][direction]:
+    // variant 0 = 21 profile rows (standard letters), 1 = all 25 rows
+    int blocks_per_sm[2][2][kClasses][kNumShapes] = {};
+    int tile_overhead = kTileOverhead;
     cudaEvent_t ev[6] = {};
     // the DP kernels of one direction run on the caller's stream and these
     // side streams (forked and joined with events), so that their tails overlap
@@ -100,6 +103,7 @@ struct swgb_seqset {
     int64_t n = 0;
     int64_t total = 0;
     int64_t max_len = 0;
+    int32_t max_code = 0;   // largest residue code in the set
 };
 
 namespace {
@@ -194,7 +198,7 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
     if ((e = cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.status, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
-    if ((e = cudaMalloc(&ctx->d_encode_flag, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ctx->d_encode_flag, 2 * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMemset(ws.status, 0, sizeof(int32_t))) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemset(ws.counters, 0, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "memset");
@@ -202,7 +206,9 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
         for (int c = 0; c < kClasses; ++c)
             for (int s = 0; s < kNumShapes; ++s) {
                 if ((e = dp_configure(c, s, d == 1)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
-                ctx->blocks_per_sm[d][c][s] = std::max(1, dp_blocks_per_sm(c, s, d == 1));
+                for (int v = 0; v < 2; ++v)
+                    ctx->blocks_per_sm[v][d][c][s] =
+                        std::max(1, dp_blocks_per_sm(c, s, d == 1, v ? kProfileRows : kStdLetters + 1));
             }
     for (auto& ev : ctx->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "cudaEventCreate");
@@ -297,15 +303,16 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
             src = set->d_res;   // encode in place
         }
     }
-    CK(cudaMemsetAsync(ctx->d_encode_flag, 0, sizeof(int32_t), st), "memset");
+    CK(cudaMemsetAsync(ctx->d_encode_flag, 0, 2 * sizeof(int32_t), st), "memset");
     CK(launch_encode(src, set->d_res, total, flags & SWGB_SEQ_ASCII, ctx->d_encode_flag, st), "encode kernel");
-    int32_t bad = 0;
-    CK(cudaMemcpyAsync(&bad, ctx->d_encode_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "flag D2H");
+    int32_t fl[2] = {0, 0};
+    CK(cudaMemcpyAsync(fl, ctx->d_encode_flag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "flag D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
     set->n = n_seqs;
     set->total = total;
     set->max_len = max_len;
-    if (bad) return fail(ctx, SWGB_EBADRES, "seqset: residue outside the alphabet");
+    set->max_code = fl[1];
+    if (fl[0]) return fail(ctx, SWGB_EBADRES, "seqset: residue outside the alphabet");
     return SWGB_OK;
 }
 
@@ -365,6 +372,7 @@ int make_score_args(swgb_ctx* ctx, const swgb_params* params, ScoreArgs* sc, int
         }
     sc->go = params->gap_open;
     sc->ge = params->gap_extend;
+    sc->prof_rows = kProfileRows;
     *max_score = mx;
     return SWGB_OK;
 }
@@ -413,8 +421,9 @@ int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, int64_t n_p
         for (int s = kFirstChunkable; s < kNumShapes; ++s) {
             int64_t n = 0;
             for (int d = 0; d < 2; ++d)
-                n = std::max<int64_t>(n, (int64_t)ctx->sm_count * ctx->blocks_per_sm[d][c][s] *
-                                             (kDPThreads / 32));
+                for (int v = 0; v < 2; ++v)
+                    n = std::max<int64_t>(n, (int64_t)ctx->sm_count * ctx->blocks_per_sm[v][d][c][s] *
+                                                 (kDPThreads / 32));
             store.region_off[c][s] = slots;
             store.region_slots[c][s] = n;
             slots += n;
@@ -441,7 +450,10 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     const Workspace& ws = store.ws;
     const bool force32 = params->flags & SWGB_FORCE_INT32;
     const bool timed = params->flags & SWGB_TIMING;
-    const ClassArgs ca = make_class_args(params->matrix, max_score, force32);
+    ClassArgs ca = make_class_args(params->matrix, max_score, force32);
+    ca.tile_overhead = ctx->tile_overhead;
+    const int pv = q->max_code < kStdLetters ? 0 : 1;   // profile variant
+    sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;
 
     int launches = 0;
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
@@ -482,7 +494,7 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
                 a.sc = sc;
-                int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[dir][c][s];
+                int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[pv][dir][c][s];
                 const int64_t need = (n_pairs + pairs_per_block(c, s) - 1) / pairs_per_block(c, s);
                 grid = std::max<int64_t>(1, std::min(grid, need));
                 CK(launch_dp(c, s, rev, a, (int)grid, ks), "dp kernel");
@@ -662,7 +674,7 @@ struct NoallocDevice {
     bool ready = false;
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch
     int sm_count = 0;
-    int blocks_per_sm[2][kClasses][kNumShapes] = {};
+    int blocks_per_sm[2][kClasses][kNumShapes] = {};   // all 25 profile rows
 };
 
 NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
@@ -710,6 +722,7 @@ int noalloc_score_args(const swgb_params* params, ScoreArgs* sc, int* max_score)
         }
     sc->go = params->gap_open;
     sc->ge = params->gap_extend;
+    sc->prof_rows = kProfileRows;
     *max_score = mx;
     return SWGB_OK;
 }
@@ -738,7 +751,7 @@ int noalloc_setup(int dev, NoallocDevice** out) {
             for (int c = 0; c < kClasses; ++c)
                 for (int s = 0; s < kNumShapes; ++s) {
                     NA_CK(dp_configure(c, s, dir == 1));
-                    d.blocks_per_sm[dir][c][s] = std::max(1, dp_blocks_per_sm(c, s, dir == 1));
+                    d.blocks_per_sm[dir][c][s] = std::max(1, dp_blocks_per_sm(c, s, dir == 1, kProfileRows));
                 }
         d.base = static_cast<unsigned char*>(ptr);
         d.ready = true;
@@ -808,7 +821,9 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
     if (host_flags & kFlagBadCode) return SWGB_EBADRES;
 
     const SeqView qv{q_codes, q_offsets, n_q}, rv{r_codes, r_offsets, n_r};
-    const ClassArgs ca = make_class_args(params->matrix, max_score, params->flags & SWGB_FORCE_INT32);
+    ClassArgs ca = make_class_args(params->matrix, max_score, params->flags & SWGB_FORCE_INT32);
+    ca.tile_overhead = kTileOverhead;
+    sc.prof_rows = kProfileRows;
     for (int dir = 0; dir < 2; ++dir) {
         const bool rev = dir == 1;
         NA_CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st));
@@ -933,5 +948,54 @@ SWGB_EXPORT int swgb_plan_launch(swgb_plan* plan, void* stream) {
     ctx->last_stream = (cudaStream_t)stream;
     ctx->last_launches = plan->launches;
     ctx->last_pairs = plan->n_pairs;
+    return SWGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile selection tuning
+// ---------------------------------------------------------------------------
+SWGB_EXPORT int swgb_set_tile_overhead(swgb_ctx* ctx, int overhead) {
+    if (!ctx) return SWGB_EINVAL;
+    if (overhead < 0 || overhead > 64) return fail(ctx, SWGB_EINVAL, "tile overhead must be in [0, 64]");
+    ctx->tile_overhead = overhead;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_get_tile_overhead(const swgb_ctx* ctx) {
+    return ctx ? ctx->tile_overhead : SWGB_EINVAL;
+}
+
+SWGB_EXPORT int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                              const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
+                              swgb_record* out, void* stream, int* best_overhead, float* best_ms) {
+    if (!ctx || !params) return SWGB_EINVAL;
+    static const int kCandidates[] = {2, 4, 6, 8, 10, 14, 20};
+    swgb_params p = *params;
+    p.flags |= SWGB_TIMING;
+    const int saved = ctx->tile_overhead;
+    int best = saved;
+    float best_t = -1.0f;
+    for (int c : kCandidates) {
+        ctx->tile_overhead = c;
+        float t = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {   // first run warms up the workspace
+            int rc = swgb_align(ctx, queries, refs, pairs, n_pairs, &p, out, stream);
+            if (!rc) rc = swgb_sync(ctx, stream);
+            swgb_stats st;
+            if (!rc) rc = swgb_last_stats(ctx, &st);
+            if (rc) {
+                ctx->tile_overhead = saved;
+                return rc;
+            }
+            t = st.total_ms;
+        }
+        if (best_t < 0.0f || t < best_t) {
+            best_t = t;
+            best = c;
+        }
+    }
+    ctx->tile_overhead = best;
+    if (best_overhead) *best_overhead = best;
+    if (best_ms) *best_ms = best_t;
     return SWGB_OK;
 }

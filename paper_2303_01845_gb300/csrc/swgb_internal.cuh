@@ -25,7 +25,12 @@ struct ScoreArgs {
     // the pad code.  Row = query code, column = reference code.
     int8_t prof[kProfileRows][kMatStride];
     int32_t go, ge;
+    // rows of the per-pair profile: one per query letter the query set uses
+    // plus one for padding.  Sets of the 20 standard letters (codes 0..19)
+    // need 21; otherwise all 25.  The pad row is the last.
+    int32_t prof_rows;
 };
+constexpr int kStdLetters = 20;
 
 struct SeqView {
     const uint8_t* res;   // codes
@@ -37,29 +42,38 @@ struct SeqView {
 // A pair's DP is laid out with the reference along the lanes ("held", rows of
 // a tile) and the query streamed through the wavefront.  Tile shapes: G lanes
 // per pair group x R rows per lane.
-//   shape: 0      1       2      3       4       5        6       7        8
-//   (G,R): (4,8)  (4,12)  (8,8)  (8,12)  (16,8)  (16,12)  (32,8)  (32,12)  (32,16)
-//   rows:  32     48      64     96      128     192      256     384      512
-// Shapes from kFirstChunkable on (one group per warp) also cover references
-// longer than one tile, in chunks of G*R rows.
-constexpr int kNumShapes = 9;
-constexpr int kFirstChunkable = 6;
-__host__ __device__ constexpr int shape_G(int s) { return s < 2 ? 4 : s < 4 ? 8 : s < 6 ? 16 : 32; }
-__host__ __device__ constexpr int shape_R(int s) { return s == 8 ? 16 : (s & 1) ? 12 : 8; }
+//   shape: 0     1      2     3      4      5      6      7      8
+//   (G,R): (4,8) (4,12) (8,8) (8,12) (16,8) (16,10) (16,12) (16,14) (16,16)
+//   shape: 9       10      11      12
+//   (G,R): (32,10) (32,12) (32,14) (32,16)
+// (32,8) would never win over (16,16), which has the same rows and half the
+// wavefront fill.  Shapes from kFirstChunkable on (one group per warp) also
+// cover references longer than one tile, in chunks of G*R rows.
+constexpr int kNumShapes = 13;
+constexpr int kFirstChunkable = 9;
+__host__ __device__ constexpr int shape_G(int s) { return s < 2 ? 4 : s < 4 ? 8 : s < 9 ? 16 : 32; }
+__host__ __device__ constexpr int shape_R(int s) {
+    return s < 4 ? ((s & 1) ? 12 : 8) : s < 9 ? 8 + 2 * (s - 4) : 10 + 2 * (s - 9);
+}
+// bytes of profile per lane and query letter: R rounded up to whole words
+__host__ __device__ constexpr int shape_LS(int s) { return (shape_R(s) + 3) / 4 * 4; }
 constexpr int kChunkBuckets = 16;             // chunk-count buckets of a chunkable shape
 constexpr int kBucketsPerClass = kFirstChunkable + (kNumShapes - kFirstChunkable) * kChunkBuckets;
 constexpr int kClasses = 2;                   // 0 = packed 16x2, 1 = 32-bit
 constexpr int kNumBuckets = kClasses * kBucketsPerClass;
-constexpr int kQBins = 1024;                  // streamed-length bins per bucket
-constexpr int kQBinShift = 2;                 // 4 residues per bin
+constexpr int kQBins = 512;                   // streamed-length bins per bucket
+constexpr int kQBinShift = 3;                 // 8 residues per bin
 constexpr int kNumBins = kNumBuckets * kQBins;
 constexpr int kNumKernels = kClasses * kNumShapes;
 
 // Tile of a pair: the shape (and chunk count) of least modelled cost, where a
 // pair costs (streamed steps incl. the G-1 wavefront fill) x chunks x G x
-// (R + 4) -- R cell updates plus about four rows' worth of per-step work per
-// lane, shared by the 32/G groups of a warp.
-__host__ __device__ inline void choose_shape(int64_t lq, int64_t lr, int* shape, int* nch) {
+// (R + overhead) -- R cell updates plus the per-step work of a lane counted in
+// rows (loop control, letter fetch, max tracking), shared by the 32/G groups
+// of a warp.  The overhead is a context setting (default kTileOverhead), tuned
+// by swgb_autotune.
+constexpr int kTileOverhead = 6;
+__host__ __device__ inline void choose_shape(int64_t lq, int64_t lr, int overhead, int* shape, int* nch) {
     int64_t best = -1;
     for (int s = 0; s < kNumShapes; ++s) {
         const int64_t rows = (int64_t)shape_G(s) * shape_R(s);
@@ -68,7 +82,7 @@ __host__ __device__ inline void choose_shape(int64_t lq, int64_t lr, int* shape,
             if (s < kFirstChunkable) continue;
             n = (lr + rows - 1) / rows;
         }
-        const int64_t cost = (lq + shape_G(s) - 1) * n * shape_G(s) * (shape_R(s) + 4);
+        const int64_t cost = (lq + shape_G(s) - 1) * n * shape_G(s) * (shape_R(s) + overhead);
         if (best < 0 || cost < best) {
             best = cost;
             *shape = s;
@@ -101,6 +115,7 @@ struct ClassArgs {
     int8_t rowmax[kMatStride];    // max(0, max_y s(x, y)) per query code x
     int8_t colmax[kMatStride];    // max(0, max_x s(x, y)) per reference code y
     int32_t force32;
+    int32_t tile_overhead;        // per-step lane work in rows (choose_shape)
 };
 
 // Per-call device workspace (owned by the context).
@@ -143,8 +158,9 @@ enum Counter {
 };
 
 // ---- launchers (swgb_kernels.cu) -------------------------------------------
+// flags[0] |= 1 on a residue outside the alphabet; flags[1] = max(flags[1], code)
 cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
-                          int32_t* bad_flag, cudaStream_t st);
+                          int32_t* flags, cudaStream_t st);
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
                         swgb_record* out, bool reverse, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st);
@@ -153,11 +169,12 @@ cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st
 // Launches the DP kernel of (class, shape); grid sized from occupancy.
 cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
                       cudaStream_t st);
-// Blocks per SM the DP kernel of (class, shape, direction) can keep resident.
-int dp_blocks_per_sm(int cls, int shape, bool reverse);
+// Blocks per SM the DP kernel of (class, shape, direction) can keep resident
+// with prof_rows profile rows.
+int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows);
 // Threads per block of every DP kernel.
 constexpr int kDPThreads = 64;
-size_t dp_smem_bytes(int cls, int shape);
+size_t dp_smem_bytes(int cls, int shape, int prof_rows);
 cudaError_t dp_configure(int cls, int shape, bool reverse);
 cudaError_t launch_probe_addmax(unsigned long long* cycles, uint32_t* sink, int blocks,
                                 int iters, cudaStream_t st);

@@ -49,12 +49,14 @@ __device__ __forceinline__ uint8_t ascii_code(int c) {
 }
 
 __global__ void encode_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                              int64_t n, int ascii, int32_t* bad) {
+                              int64_t n, int ascii, int32_t* flags) {
     __shared__ uint8_t tab[256];
+    __shared__ int32_t block_max;
     for (int k = threadIdx.x; k < 256; k += blockDim.x)
         tab[k] = ascii ? ascii_code(k) : (k < kAlpha ? (uint8_t)k : (uint8_t)255);
+    if (threadIdx.x == 0) block_max = 0;
     __syncthreads();
-    int any_bad = 0;
+    int any_bad = 0, mx = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         uint8_t c = tab[in[k]];
@@ -62,17 +64,21 @@ __global__ void encode_kernel(const uint8_t* __restrict__ in, uint8_t* __restric
             any_bad = 1;
             c = 0;
         }
+        mx = max(mx, (int)c);
         out[k] = c;
     }
-    if (__syncthreads_or(any_bad) && threadIdx.x == 0) atomicOr(bad, 1);
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&block_max, mx);
+    if (__syncthreads_or(any_bad) && threadIdx.x == 0) atomicOr(&flags[0], 1);
+    if (threadIdx.x == 0) atomicMax(&flags[1], block_max);
 }
 
 cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
-                          int32_t* bad_flag, cudaStream_t st) {
+                          int32_t* flags, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, n, ascii ? 1 : 0, bad_flag);
+    encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, n, ascii ? 1 : 0, flags);
     return cudaGetLastError();
 }
 
@@ -135,7 +141,7 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
             int64_t qb = lq >> kQBinShift;
             if (qb > kQBins - 1) qb = kQBins - 1;
             int shape = 0, nch = 1;
-            choose_shape(lq, lr, &shape, &nch);
+            choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
             bin = bucket_of(cls, shape, nch) * kQBins + (kQBins - 1 - (int)qb);
             atomicAdd(&ws.hist[bin], 1u);
             cells += (unsigned long long)(lq * lr);
@@ -302,55 +308,58 @@ struct Lane<false> {
     }
 };
 
-// Maximum of v[0..R) and init as a tree of 3-input maxima (depth 2-3).
-template <bool P16, int R>
-__device__ __forceinline__ uint32_t tree_max(const uint32_t (&v)[R], uint32_t init) {
-    using L = Lane<P16>;
-    if constexpr (R == 8) {
-        const uint32_t a = L::max3(v[0], v[1], v[2]);
-        const uint32_t b = L::max3(v[3], v[4], v[5]);
-        const uint32_t c = L::max3(v[6], v[7], init);
-        return L::max3(a, b, c);
-    } else if constexpr (R == 12) {
-        const uint32_t a = L::max3(v[0], v[1], v[2]);
-        const uint32_t b = L::max3(v[3], v[4], v[5]);
-        const uint32_t c = L::max3(v[6], v[7], v[8]);
-        const uint32_t d = L::max3(v[9], v[10], v[11]);
-        return L::max3(L::max3(a, b, c), d, init);
+// Maximum of N values as a tree of 3-input maxima: every level takes the
+// values three at a time and carries the one or two left over, so N values cost
+// ceil((N - 1) / 2) instructions at depth about log3(N).
+template <bool P16, int N>
+__device__ __forceinline__ uint32_t max_reduce(const uint32_t (&x)[N]) {
+    if constexpr (N == 1) {
+        return x[0];
+    } else if constexpr (N == 2) {
+        return Lane<P16>::max3(x[0], x[1], x[1]);
     } else {
-        static_assert(R == 16, "rows per lane must be 8, 12 or 16");
-        const uint32_t a = L::max3(v[0], v[1], v[2]);
-        const uint32_t b = L::max3(v[3], v[4], v[5]);
-        const uint32_t c = L::max3(v[6], v[7], v[8]);
-        const uint32_t d = L::max3(v[9], v[10], v[11]);
-        const uint32_t e = L::max3(v[12], v[13], v[14]);
-        const uint32_t f = L::max3(a, b, c);
-        const uint32_t g = L::max3(d, e, v[15]);
-        return L::max3(f, g, init);
+        constexpr int NG = N / 3, NL = N % 3, M = NG + NL;
+        uint32_t y[M];
+#pragma unroll
+        for (int k = 0; k < NG; ++k) y[k] = Lane<P16>::max3(x[3 * k], x[3 * k + 1], x[3 * k + 2]);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) y[NG + k] = x[3 * NG + k];
+        return max_reduce<P16, M>(y);
     }
 }
 
-// R profile bytes as R/4 words
-template <int R>
+// Maximum of v[0..R) and init.
+template <bool P16, int R>
+__device__ __forceinline__ uint32_t tree_max(const uint32_t (&v)[R], uint32_t init) {
+    uint32_t x[R + 1];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = v[k];
+    x[R] = init;
+    return max_reduce<P16, R + 1>(x);
+}
+
+// A lane's profile bytes for one query letter: R rows rounded up to whole
+// words (LS bytes, 8, 12 or 16), loaded as one 8-byte, three 4-byte or one
+// 16-byte access; they start at a multiple of LS.
+template <int LS>
 struct ProfWords {
-    uint32_t w[R / 4];
+    uint32_t w[LS / 4];
 };
 
-// A lane's R profile bytes start at a multiple of R, so R = 8 and 16 load as
-// one 8- or 16-byte word and R = 12 as three 4-byte words.
-template <int R>
-__device__ __forceinline__ ProfWords<R> load_prof(const int8_t* p) {
-    ProfWords<R> out;
-    if constexpr (R == 8) {
+template <int LS>
+__device__ __forceinline__ ProfWords<LS> load_prof(const int8_t* p) {
+    ProfWords<LS> out;
+    if constexpr (LS == 8) {
         const uint2 v = *reinterpret_cast<const uint2*>(p);
         out.w[0] = v.x;
         out.w[1] = v.y;
-    } else if constexpr (R == 12) {
+    } else if constexpr (LS == 12) {
         const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
         out.w[0] = q[0];
         out.w[1] = q[1];
         out.w[2] = q[2];
     } else {
+        static_assert(LS == 16, "lane stride must be 8, 12 or 16 bytes");
         const uint4 v = *reinterpret_cast<const uint4*>(p);
         out.w[0] = v.x;
         out.w[1] = v.y;
@@ -360,11 +369,11 @@ __device__ __forceinline__ ProfWords<R> load_prof(const int8_t* p) {
     return out;
 }
 
-template <int R>
-__device__ __forceinline__ void store_prof(int8_t* p, const uint32_t (&w)[R / 4]) {
-    if constexpr (R == 8) {
+template <int LS>
+__device__ __forceinline__ void store_prof(int8_t* p, const uint32_t (&w)[LS / 4]) {
+    if constexpr (LS == 8) {
         *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
-    } else if constexpr (R == 12) {
+    } else if constexpr (LS == 12) {
         uint32_t* q = reinterpret_cast<uint32_t*>(p);
         q[0] = w[0];
         q[1] = w[1];
@@ -387,9 +396,9 @@ constexpr int kSmatBytes = kProfileRows * kMatStride;   // 800
 constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
 constexpr int kBoundEvery = 8;   // steps between refreshes of the group's score bound
 
-template <int G, int R, bool P16>
-__host__ __device__ constexpr int dp_prof_bytes_per_warp() {
-    return (32 / G) * (P16 ? 2 : 1) * kProfileRows * G * R;
+// bytes of profile a warp stages: per group and pair, prof_rows x G x LS
+__host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16, int prof_rows) {
+    return (32 / G) * (P16 ? 2 : 1) * prof_rows * G * ((R + 3) / 4 * 4);
 }
 
 // Packed per-half maximum over the G lanes of a group.
@@ -428,9 +437,13 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     using L = Lane<P16>;
     constexpr int PACK = L::kPack;
     constexpr int GROUPS = 32 / G;
-    constexpr int ROWS = G * R;
-    constexpr int PROF = kProfileRows * ROWS;  // bytes per pair
-    constexpr int NW = R / 4;
+    constexpr int ROWS = G * R;                // reference rows per tile
+    constexpr int LS = (R + 3) / 4 * 4;        // profile bytes per lane and letter
+    constexpr int RS = G * LS;                 // profile bytes per letter
+    const int prows = a.sc.prof_rows;          // profile rows, the pad row last
+    const int pad_row = prows - 1;
+    const int PROF = prows * RS;               // profile bytes per pair
+    constexpr int NW = LS / 4;
 
     extern __shared__ __align__(16) uint8_t smem[];
     int8_t* smat = reinterpret_cast<int8_t*>(smem);
@@ -443,8 +456,8 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const int g = lane / G;    // pair group within the warp
     const int gl = lane % G;   // lane within the group
     int8_t* prof = reinterpret_cast<int8_t*>(smem + kSmatRegion) +
-                   (size_t)warp * dp_prof_bytes_per_warp<G, R, P16>() + (size_t)g * PACK * PROF;
-    const int8_t* plane = prof + gl * R;   // this lane's rows within a profile row
+                   (size_t)warp * dp_prof_bytes_per_warp(G, R, P16, prows) + (size_t)g * PACK * PROF;
+    const int8_t* plane = prof + gl * LS;   // this lane's rows within a profile row
 
     const int64_t begin = a.scan[(int64_t)a.first_bucket * kQBins];
     const int64_t end = a.scan[(int64_t)a.end_bucket * kQBins];
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const int oe = a.sc.go + a.sc.ge;
     const uint32_t NOE = L::splat(-oe);
     const uint32_t NE = L::splat(-a.sc.ge);
-    const uint32_t ONE = L::splat(1);
+    const uint32_t MONE = L::splat(-1);
 
     for (;;) {
         uint32_t task = 0;
@@ -508,9 +521,10 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             if (lane == 0) set_status(a.status, SWGB_EINTERNAL);
             continue;
         }
-        // query letter of streamed position i (pad outside the pair)
+        // profile row of the query letter at streamed position i (the pad
+        // row outside the pair; letters are their own rows)
         auto code_at = [&](int h, int i) -> int {
-            if (i < 0 || i >= lq[h]) return kPadCode;
+            if (i < 0 || i >= lq[h]) return pad_row;
             return REV ? qp[h][lq[h] - 1 - i] : qp[h][i];
         };
 
@@ -536,15 +550,16 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             __syncwarp();
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                uint8_t y[R];
+                uint8_t y[LS];
 #pragma unroll
-                for (int k = 0; k < R; ++k) {
+                for (int k = 0; k < LS; ++k) {
                     const int j = jl + k;
-                    y[k] = (j < lr[h]) ? (REV ? rp[h][lr[h] - 1 - j] : rp[h][j]) : (uint8_t)kPadCode;
+                    y[k] = (k < R && j < lr[h]) ? (REV ? rp[h][lr[h] - 1 - j] : rp[h][j])
+                                                : (uint8_t)kPadCode;
                 }
-                int8_t* dst = prof + h * PROF + gl * R;
-                for (int x = 0; x < kProfileRows; ++x) {
-                    const int8_t* row = smat + x * kMatStride;
+                int8_t* dst = prof + h * PROF + gl * LS;
+                for (int x = 0; x < prows; ++x) {
+                    const int8_t* row = smat + (x == pad_row ? kPadCode : x) * kMatStride;
                     uint32_t w[NW];
 #pragma unroll
                     for (int k4 = 0; k4 < NW; ++k4) {
@@ -553,7 +568,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                                 ((uint32_t)(uint8_t)row[y[4 * k4 + 2]] << 16) |
                                 ((uint32_t)(uint8_t)row[y[4 * k4 + 3]] << 24);
                     }
-                    store_prof<R>(dst + x * ROWS, w);
+                    store_prof<LS>(dst + x * RS, w);
                 }
             }
             __syncwarp();
@@ -567,7 +582,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             }
             uint32_t hin_prev = NOE, eout = NOE, hout = NOE;
             uint32_t lb = NOE;                      // this lane's maximum in this chunk
-            uint32_t lbT = L::addmax(lb, ONE, T);   // per half max(lb + 1, T)
+            uint32_t lb1 = L::addmax(T, MONE, lb);  // per half max(lb, T - 1)
             uint32_t snap[PACK][R];                 // registers at the last recorded step
             int si[PACK], sv[PACK];
 #pragma unroll
@@ -585,11 +600,11 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
 
             // software pipeline: profile words of the next step and the query
             // letter of the step after are fetched one step ahead
-            ProfWords<R> pwn[PACK];
+            ProfWords<LS> pwn[PACK];
             int xn[PACK];
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                pwn[h] = load_prof<R>(plane + h * PROF + code_at(h, -gl) * ROWS);
+                pwn[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
                 xn[h] = code_at(h, 1 - gl);
             }
             uint2 bcur = make_uint2(NOE, NOE);
@@ -604,11 +619,11 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             // never be the pair's maximum.  Only the boundary store is guarded.
             for (int t = 0; t < steps && t <= stop_w; ++t) {
                 const int i = t - gl;
-                ProfWords<R> pw[PACK];
+                ProfWords<LS> pw[PACK];
 #pragma unroll
                 for (int h = 0; h < PACK; ++h) {
                     pw[h] = pwn[h];
-                    pwn[h] = load_prof<R>(plane + h * PROF + xn[h] * ROWS);
+                    pwn[h] = load_prof<LS>(plane + h * PROF + xn[h] * RS);
                     xn[h] = code_at(h, i + 2);
                 }
                 if (gl == 0) {
@@ -649,21 +664,13 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 const uint32_t e_next = __shfl_up_sync(kFull, eout, 1, G);
                 const uint32_t h_next = __shfl_up_sync(kFull, hout, 1, G);
                 {
+                    // a half records when its maximum m passes lb and reaches T,
+                    // i.e. m > max(lb, T - 1) = lb1; in no half iff max(m, lb1) == lb1
                     const uint32_t m = tree_max<P16, R>(Hop, lb);
-                    bool rec_h[2];
-                    if constexpr (P16) {
-                        bool hi, lo;
-                        (void)__vibmax_s16x2(m, lbT, &hi, &lo);   // m >= max(lb + 1, T)
-                        rec_h[0] = lo;
-                        rec_h[1] = hi;
-                    } else {
-                        rec_h[0] = (int)m >= (int)lbT;
-                        rec_h[1] = false;
-                    }
-                    if (rec_h[0] || rec_h[1]) {
+                    if (L::max3(m, lb1, lb1) != lb1) {
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
-                            if (rec_h[h]) {
+                            if (L::get(m, h) > L::get(lb1, h)) {
                                 si[h] = i;
                                 sv[h] = L::get(m, h);
 #pragma unroll
@@ -673,11 +680,11 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                         }
                     }
                     lb = m;
-                    lbT = L::addmax(m, ONE, T);
+                    lb1 = L::addmax(T, MONE, m);
                 }
                 if ((t & (kBoundEvery - 1)) == kBoundEvery - 1) {
                     T = group_max<P16, G>(L::max3(lb, T, T));
-                    lbT = L::addmax(lb, ONE, T);
+                    lb1 = L::addmax(T, MONE, lb);
                     if constexpr (REV) {
                         // once every half of every group has met S at some step,
                         // cells of later steps can no longer be the first such cell
@@ -792,7 +799,11 @@ DPFn dp_pick(int shape) {
         case 5: return dp_fn<5, P16, REV>();
         case 6: return dp_fn<6, P16, REV>();
         case 7: return dp_fn<7, P16, REV>();
-        default: return dp_fn<8, P16, REV>();
+        case 8: return dp_fn<8, P16, REV>();
+        case 9: return dp_fn<9, P16, REV>();
+        case 10: return dp_fn<10, P16, REV>();
+        case 11: return dp_fn<11, P16, REV>();
+        default: return dp_fn<12, P16, REV>();
     }
 }
 
@@ -801,23 +812,21 @@ static DPFn dp_lookup(int cls, int shape, bool reverse) {
     return reverse ? dp_pick<false, true>(shape) : dp_pick<false, false>(shape);
 }
 
-size_t dp_smem_bytes(int cls, int shape) {
-    const int G = shape_G(shape), R = shape_R(shape);
-    const int pack = cls == 0 ? 2 : 1;
-    const size_t per_warp = (size_t)(32 / G) * pack * kProfileRows * G * R;
+size_t dp_smem_bytes(int cls, int shape, int prof_rows) {
+    const size_t per_warp = dp_prof_bytes_per_warp(shape_G(shape), shape_R(shape), cls == 0, prof_rows);
     return kSmatRegion + per_warp * (kDPThreads / 32);
 }
 
 cudaError_t dp_configure(int cls, int shape, bool reverse) {
     return cudaFuncSetAttribute(dp_lookup(cls, shape, reverse),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dp_smem_bytes(cls, shape));
+                                (int)dp_smem_bytes(cls, shape, kProfileRows));
 }
 
-int dp_blocks_per_sm(int cls, int shape, bool reverse) {
+int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows) {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dp_lookup(cls, shape, reverse), kDPThreads,
-                                                      dp_smem_bytes(cls, shape)) != cudaSuccess)
+                                                      dp_smem_bytes(cls, shape, prof_rows)) != cudaSuccess)
         return 0;
     return n;
 }
@@ -825,7 +834,7 @@ int dp_blocks_per_sm(int cls, int shape, bool reverse) {
 cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
                       cudaStream_t st) {
     DPFn fn = dp_lookup(cls, shape, reverse);
-    fn<<<grid_blocks, kDPThreads, dp_smem_bytes(cls, shape), st>>>(a);
+    fn<<<grid_blocks, kDPThreads, dp_smem_bytes(cls, shape, a.sc.prof_rows), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,11 @@ _SIGS = [
     ("swgb_last_stats", ctypes.c_int, [_VP, ctypes.POINTER(swgb_stats)]),
     ("swgb_probe_addmax_rate", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int)]),
+    ("swgb_set_tile_overhead", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("swgb_get_tile_overhead", ctypes.c_int, [_VP]),
+    ("swgb_autotune", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(swgb_params),
+                                     _VP, _VP, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]),
     ("swgb_plan_create", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64,
                                         ctypes.POINTER(swgb_params), _VP, ctypes.POINTER(_VP)]),
     ("swgb_plan_launch", ctypes.c_int, [_VP, _VP]),
@@ -271,6 +276,25 @@ def swgb_probe_addmax_rate(ctx):
     n = ctypes.c_int()
     _check(ctx, load().swgb_probe_addmax_rate(ctx, ctypes.byref(r), ctypes.byref(n)))
     return r.value, n.value
+
+
+def swgb_set_tile_overhead(ctx, overhead):
+    _check(ctx, load().swgb_set_tile_overhead(ctx, int(overhead)))
+
+
+def swgb_get_tile_overhead(ctx):
+    return load().swgb_get_tile_overhead(ctx)
+
+
+def swgb_autotune(ctx, queries, refs, pairs, params, out, stream=None):
+    """Times the tile-cost overhead candidates on this batch (CUDA buffers),
+    keeps the fastest in the context; returns (overhead, ms)."""
+    best = ctypes.c_int()
+    ms = ctypes.c_float()
+    rc = load().swgb_autotune(ctx, queries, refs, _ptr(pairs), pairs.shape[0], ctypes.byref(params),
+                              _ptr(out), _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms))
+    _check(ctx, rc)
+    return best.value, ms.value
 
 
 def swgb_plan_create(ctx, queries, refs, pairs, params, out):

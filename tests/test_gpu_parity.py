@@ -77,22 +77,26 @@ def test_gap_settings_and_asymmetric_matrix(aligner, oracle_mod, blosum, plain10
 
 
 HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129,
-                191, 192, 193, 255, 256, 257, 383, 384, 385, 511, 512, 513, 767, 768, 769,
-                1023, 1024, 1025, 1537, 2999]
+                159, 160, 161, 191, 192, 193, 223, 224, 225, 255, 256, 257, 319, 320, 321,
+                383, 384, 385, 447, 448, 449, 511, 512, 513, 767, 768, 769, 1023, 1024, 1025,
+                1537, 2999]
 STREAM_LENGTHS = [1, 2, 3, 30, 31, 32, 33, 100, 257, 512, 513, 1200]
+
+TILE_SHAPES = [(4, 8), (4, 12), (8, 8), (8, 12), (16, 8), (16, 10), (16, 12), (16, 14), (16, 16),
+               (32, 10), (32, 12), (32, 14), (32, 16)]
+FIRST_CHUNKABLE = 9
 
 
 def tile_of(lq, lr):
-    """(shape, chunks) the library's cost model gives a pair: shapes are
-    (G lanes, R rows) = (4,8) (4,12) (8,8) (8,12) (16,8) (16,12) (32,8) (32,12)
-    (32,16); the last three also tile longer references in chunks."""
+    """(shape, chunks) the library's cost model gives a pair: (G lanes, R rows)
+    from TILE_SHAPES, the 32-lane ones also tiling longer references in
+    chunks; cost (lq + G - 1) * chunks * G * (R + 4)."""
     best = None
-    for s, (G, R) in enumerate([(4, 8), (4, 12), (8, 8), (8, 12), (16, 8), (16, 12),
-                                (32, 8), (32, 12), (32, 16)]):
+    for s, (G, R) in enumerate(TILE_SHAPES):
         rows = G * R
         n = 1
         if lr > rows:
-            if s < 6:
+            if s < FIRST_CHUNKABLE:
                 continue
             n = -(-lr // rows)
         cost = (lq + G - 1) * n * G * (R + 4)
@@ -126,8 +130,9 @@ def ragged_workload(seed, mat, held=HELD_LENGTHS, stream=STREAM_LENGTHS):
 def test_ragged_lengths_all_shapes(aligner, oracle_mod, blosum):
     wl = ragged_workload(11, blosum)
     tiles = {tile_of(wl.q_len[q], wl.r_len[r]) for q, r in wl.pairs}
-    assert {s for s, _ in tiles} == set(range(9))
-    assert {s for s, n in tiles if n >= 2} == {7, 8}   # (32, 8) never wins once chunked
+    assert {s for s, _ in tiles} == set(range(len(TILE_SHAPES)))
+    chunked = {s for s, n in tiles if n >= 2}
+    assert chunked <= set(range(FIRST_CHUNKABLE, len(TILE_SHAPES))) and len(chunked) >= 3
     assert_same(gpu_records(aligner, wl, params(blosum)),
                 oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
 
@@ -352,3 +357,32 @@ def test_plan_replays_the_pipeline(aligner, blosum, plain10k, torch_cuda):
         assert (out.cpu().numpy() == want2).all()
     finally:
         swgb.swgb_plan_destroy(plan)
+
+
+def test_tile_selection_does_not_change_records(aligner, blosum, plain10k, torch_cuda):
+    """Records are identical under every tile-cost setting, and the autotuner
+    keeps one of its candidates."""
+    torch = torch_cuda
+    from paper_2303_01845_gb300 import swgb
+    q, r = device_sets(aligner, plain10k)
+    prm = params(blosum)
+    pairs = torch.from_numpy(plain10k.pairs[::3].copy()).cuda()
+    saved = swgb.swgb_get_tile_overhead(aligner.ctx)
+    try:
+        ref = None
+        for c in [0, 3, 6, 12, 64]:
+            swgb.swgb_set_tile_overhead(aligner.ctx, c)
+            assert swgb.swgb_get_tile_overhead(aligner.ctx) == c
+            got = aligner.align(q, r, pairs, prm).cpu().numpy()
+            if ref is None:
+                ref = got
+            assert (got == ref).all()
+        with pytest.raises(swgb.SwgbError):
+            swgb.swgb_set_tile_overhead(aligner.ctx, 65)
+        out = torch.zeros((pairs.shape[0], 5), dtype=torch.int32, device="cuda")
+        best, ms = swgb.swgb_autotune(aligner.ctx, q.handle, r.handle, pairs, prm, out)
+        assert best in (2, 4, 6, 8, 10, 14, 20) and ms > 0
+        assert swgb.swgb_get_tile_overhead(aligner.ctx) == best
+        assert (out.cpu().numpy() == ref).all()
+    finally:
+        swgb.swgb_set_tile_overhead(aligner.ctx, saved)
