@@ -24,6 +24,7 @@
 // (precision class, tile shape) pulls pair groups from an atomic counter.
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "swgb_internal.cuh"
 
@@ -607,9 +608,15 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 pwn[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
                 xn[h] = code_at(h, 1 - gl);
             }
-            uint2 bcur = make_uint2(NOE, NOE);
-            if (read_bnd && ls_c > 0) bcur = bnd[0];
             uint32_t ein = NOE, hin = NOE;   // from lane gl-1, previous step
+
+            // The step loop, compiled twice for the 32-lane tiles: with the
+            // chunk-boundary exchange (BND, references longer than one tile) and
+            // without it (one tile, and every smaller shape).
+            auto wavefront = [&](auto bnd_tag) {
+            constexpr bool BND = decltype(bnd_tag)::value;
+            uint2 bcur = make_uint2(NOE, NOE);
+            if (BND && read_bnd && ls_c > 0) bcur = bnd[0];
 
             // Lanes step in lock step without branching on their own range:
             // before its first position a lane sees only pad letters and
@@ -626,15 +633,22 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                     pwn[h] = load_prof<LS>(plane + h * PROF + xn[h] * RS);
                     xn[h] = code_at(h, i + 2);
                 }
-                if (gl == 0) {
-                    // past the rows the previous chunk handed over, lane 0 sees
-                    // "minus infinity": cells there score alignments confined to
-                    // this chunk, never above the pair's score
-                    const bool take = read_bnd && i < ls_c;
-                    ein = take ? bcur.x : NOE;
-                    hin = take ? bcur.y : NOE;
+                if constexpr (BND) {
+                    if (gl == 0) {
+                        // past the rows the previous chunk handed over, lane 0 sees
+                        // "minus infinity": cells there score alignments confined
+                        // to this chunk, never above the pair's score
+                        const bool take = read_bnd && i < ls_c;
+                        ein = take ? bcur.x : NOE;
+                        hin = take ? bcur.y : NOE;
+                    }
+                    if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
+                } else {
+                    if (gl == 0) {
+                        ein = NOE;
+                        hin = NOE;
+                    }
                 }
-                if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
                 // phase 1, independent rows: u = max(Hdiag + s, F), U = max(u, 0) - (o + e)
                 uint32_t U[R];
 #pragma unroll
@@ -660,7 +674,9 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 eout = e;
                 hout = Hop[R - 1];
                 hin_prev = hin;
-                if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(eout, hout);
+                if constexpr (BND) {
+                    if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(eout, hout);
+                }
                 const uint32_t e_next = __shfl_up_sync(kFull, eout, 1, G);
                 const uint32_t h_next = __shfl_up_sync(kFull, hout, 1, G);
                 {
@@ -706,6 +722,14 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 ein = e_next;
                 hin = h_next;
             }
+            };
+            if constexpr (G == 32) {
+                if (nch > 1) wavefront(std::true_type{});
+                else wavefront(std::false_type{});
+            } else {
+                wavefront(std::false_type{});
+            }
+
             // ---- the lane's candidate of this chunk: the recorded step and the
             // first row of the snapshot holding the value, if it is the lane's
             // maximum
