@@ -87,7 +87,9 @@ typedef struct {
  *   matrix:     host pointer to 24 x 24 int8, row = query code, column =
  *               reference code (need not be symmetric).  Read during the call.
  *   gap_open:   o >= 0;  gap_extend: e >= 1.  The 8-bit query profile holds
- *               s + o + e, so max(matrix) + o + e must be <= 127.
+ *               s + o + e, so max(matrix) + o + e must be <= 127.  A matrix
+ *               with some s + o + e < 0 runs every pair on the 32-bit path
+ *               (same results, about half the speed).
  *   flags:      SWGB_FORCE_INT32 | SWGB_TIMING. */
 typedef struct {
     const int8_t* matrix;

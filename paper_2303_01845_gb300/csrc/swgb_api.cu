@@ -140,8 +140,26 @@ cudaError_t grow(T** p, int64_t* cap, int64_t need) {
 
 SeqView view(const swgb_seqset* s) { return SeqView{s->d_res, s->d_off, s->n}; }
 
-// Row / column maxima of a validated 24 x 24 matrix for the 16-bit test.
-ClassArgs make_class_args(const int8_t* m, int max_score, bool force32) {
+// Both profile tables of a validated matrix and gap setting (o + e = oe).
+void fill_profiles(const int8_t* m, int go, int ge, ScoreArgs* sc) {
+    const int oe = go + ge;
+    for (int x = 0; x < kProfileRows; ++x)
+        for (int y = 0; y < kMatStride; ++y) {
+            const bool real = x < kAlpha && y < kAlpha;
+            const int s = real ? m[x * kAlpha + y] : 0;
+            sc->prof[x][y] = (int8_t)(real ? s + oe : kPadProfile);
+            sc->profu[x][y] = (uint8_t)std::min(std::max(real ? s + oe : 0, 0), 127);
+        }
+    sc->go = go;
+    sc->ge = ge;
+    sc->one = 1;
+    sc->prof_rows = kProfileRows;
+}
+
+// Row / column maxima of a validated 24 x 24 matrix for the 16-bit test.  The
+// packed path also needs every s + o + e >= 0 (its profile bytes are
+// unsigned); other matrices run on the 32-bit path.
+ClassArgs make_class_args(const int8_t* m, int oe, int max_score, bool force32) {
     ClassArgs ca{};
     ca.max_score = max_score;
     for (int x = 0; x < kAlpha; ++x) {
@@ -153,7 +171,10 @@ ClassArgs make_class_args(const int8_t* m, int max_score, bool force32) {
         ca.rowmax[x] = (int8_t)rmax;
         ca.colmax[x] = (int8_t)cmax;
     }
-    ca.force32 = force32 ? 1 : 0;
+    bool packable = true;
+    for (int k = 0; k < kAlpha * kAlpha; ++k)
+        packable = packable && m[k] + oe >= 0;
+    ca.force32 = (force32 || !packable) ? 1 : 0;
     return ca;
 }
 
@@ -364,15 +385,7 @@ int make_score_args(swgb_ctx* ctx, const swgb_params* params, ScoreArgs* sc, int
     for (int k = 0; k < kAlpha * kAlpha; ++k) mx = std::max<int>(mx, params->matrix[k]);
     if (oe > 127 || mx + oe > 127)
         return fail(ctx, SWGB_EINVAL, "max(matrix) + gap_open + gap_extend must be <= 127");
-    for (int x = 0; x < kProfileRows; ++x)
-        for (int y = 0; y < kMatStride; ++y) {
-            int v = kPadProfile;
-            if (x < kAlpha && y < kAlpha) v = params->matrix[x * kAlpha + y] + oe;
-            sc->prof[x][y] = (int8_t)v;
-        }
-    sc->go = params->gap_open;
-    sc->ge = params->gap_extend;
-    sc->prof_rows = kProfileRows;
+    fill_profiles(params->matrix, params->gap_open, params->gap_extend, sc);
     *max_score = mx;
     return SWGB_OK;
 }
@@ -450,7 +463,8 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     const Workspace& ws = store.ws;
     const bool force32 = params->flags & SWGB_FORCE_INT32;
     const bool timed = params->flags & SWGB_TIMING;
-    ClassArgs ca = make_class_args(params->matrix, max_score, force32);
+    ClassArgs ca = make_class_args(params->matrix, params->gap_open + params->gap_extend, max_score,
+                                   force32);
     ca.tile_overhead = ctx->tile_overhead;
     const int pv = q->max_code < kStdLetters ? 0 : 1;   // profile variant
     sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;
@@ -714,15 +728,7 @@ int noalloc_score_args(const swgb_params* params, ScoreArgs* sc, int* max_score)
     int mx = 0;
     for (int k = 0; k < kAlpha * kAlpha; ++k) mx = std::max<int>(mx, params->matrix[k]);
     if (oe > 127 || mx + oe > 127) return SWGB_EINVAL;
-    for (int x = 0; x < kProfileRows; ++x)
-        for (int y = 0; y < kMatStride; ++y) {
-            int v = kPadProfile;
-            if (x < kAlpha && y < kAlpha) v = params->matrix[x * kAlpha + y] + oe;
-            sc->prof[x][y] = (int8_t)v;
-        }
-    sc->go = params->gap_open;
-    sc->ge = params->gap_extend;
-    sc->prof_rows = kProfileRows;
+    fill_profiles(params->matrix, params->gap_open, params->gap_extend, sc);
     *max_score = mx;
     return SWGB_OK;
 }
@@ -821,7 +827,8 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
     if (host_flags & kFlagBadCode) return SWGB_EBADRES;
 
     const SeqView qv{q_codes, q_offsets, n_q}, rv{r_codes, r_offsets, n_r};
-    ClassArgs ca = make_class_args(params->matrix, max_score, params->flags & SWGB_FORCE_INT32);
+    ClassArgs ca = make_class_args(params->matrix, params->gap_open + params->gap_extend, max_score,
+                                   params->flags & SWGB_FORCE_INT32);
     ca.tile_overhead = kTileOverhead;
     sc.prof_rows = kProfileRows;
     for (int dir = 0; dir < 2; ++dir) {

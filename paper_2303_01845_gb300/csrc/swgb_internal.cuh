@@ -24,7 +24,12 @@ struct ScoreArgs {
     // prof[x][y] = s(x, y) + o + e for x, y < 24; kPadProfile where x or y is
     // the pad code.  Row = query code, column = reference code.
     int8_t prof[kProfileRows][kMatStride];
+    // The packed 16-bit path's table: the same for x, y < 24, and 0 (a score
+    // of -(o + e)) at the pad code.  That path takes a matrix only if every
+    // s(x, y) + o + e >= 0, so all entries are 0..127.
+    uint8_t profu[kProfileRows][kMatStride];
     int32_t go, ge;
+    int32_t one;   // always 1; a run-time multiplier the compiler cannot fold
     // rows of the per-pair profile: one per query letter the query set uses
     // plus one for padding.  Sets of the 20 standard letters (codes 0..19)
     // need 21; otherwise all 25.  The pad row is the last.

@@ -12,9 +12,12 @@
 //     receives the values of the row above its first row from lane k-1 by a
 //     warp shuffle (the previous step's output of that lane);
 //   * on the packed path every register holds two independent pairs (low and
-//     high 16 bits) and every cell update is five __viaddmax_s16x2 (dual
-//     add-then-max) instructions;  pairs whose score could pass 32767 run the
-//     same code on 32-bit registers;
+//     high 16 bits, every value biased by kBias so both halves stay unsigned);
+//     a cell update is four unsigned dual add-max / max instructions on the
+//     integer pipe plus two packed adds issued as multiply-adds on the FMA
+//     pipe (a biased 32-bit add never carries between the halves);  pairs
+//     whose score could pass 32767 run on 32-bit registers, five add-max
+//     instructions per cell;
 //   * substitution scores come from a per-pair profile in shared memory,
 //     prof[query code][held row] = s + o + e (8-bit), read as R bytes per
 //     lane per step and widened by one byte-permute per register.
@@ -246,41 +249,34 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 template <bool P16>
 struct Lane;
 
+// Packed path: two pairs per register, every score kept biased by kBias so
+// that both 16-bit halves stay in [0, 65535]; unsigned add-max / max then act
+// per half, and a 32-bit add of two such words never carries from one half
+// into the other (which lets constant shifts run as integer multiply-adds).
+constexpr int kBias = 16384;
+
 template <>
 struct Lane<true> {
     static constexpr int kPack = 2;
     __device__ __forceinline__ static uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
-        return __viaddmax_s16x2(a, b, c);
+        return __viaddmax_u16x2(a, b, c);
     }
     __device__ __forceinline__ static uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
-        return __vimax3_s16x2(a, b, c);
+        return __vimax3_u16x2(a, b, c);
     }
     __device__ __forceinline__ static uint32_t splat(int v) {
         return ((uint32_t)v & 0xffffu) * 0x10001u;
     }
     __device__ __forceinline__ static int get(uint32_t w, int h) {
-        return h ? (int)(int16_t)(w >> 16) : (int)(int16_t)(w & 0xffffu);
+        return h ? (int)(w >> 16) : (int)(w & 0xffffu);
     }
     // score of row b (0..3) of the word pair: low half from a (pair 0),
-    // high half from c (pair 1), each byte sign-extended to 16 bits
+    // high half from c (pair 1); packed-path profile bytes are 0..127, so
+    // extending the sign bit fills zeros
     __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t c, int b) {
         const uint32_t sel = (uint32_t)b | ((uint32_t)(b | 8) << 4) | ((uint32_t)(4 + b) << 8) |
                              ((uint32_t)((4 + b) | 8) << 12);
         return prmt(a, c, sel);
-    }
-    // first row r (per half) with v[r] == m, where m is the maximum of v
-    template <int R>
-    __device__ __forceinline__ static void first_rows(const uint32_t (&v)[R], uint32_t m, int (&rows)[2]) {
-        int r0 = R - 1, r1 = R - 1;
-#pragma unroll
-        for (int r = R - 1; r >= 0; --r) {
-            bool hi, lo;
-            (void)__vibmax_s16x2(v[r], m, &hi, &lo);   // v >= m  <=>  v == m
-            r0 = lo ? r : r0;
-            r1 = hi ? r : r1;
-        }
-        rows[0] = r0;
-        rows[1] = r1;
     }
 };
 
@@ -299,13 +295,6 @@ struct Lane<false> {
         const uint32_t s = (uint32_t)(b | 8);
         const uint32_t sel = (uint32_t)b | (s << 4) | (s << 8) | (s << 12);
         return prmt(a, 0u, sel);
-    }
-    template <int R>
-    __device__ __forceinline__ static void first_rows(const uint32_t (&v)[R], uint32_t m, int (&rows)[1]) {
-        int r0 = R - 1;
-#pragma unroll
-        for (int r = R - 1; r >= 0; --r) r0 = (v[r] == m) ? r : r0;
-        rows[0] = r0;
     }
 };
 
@@ -449,7 +438,8 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     int8_t* smat = reinterpret_cast<int8_t*>(smem);
     for (int k = threadIdx.x; k < kSmatBytes; k += blockDim.x)
-        smat[k] = a.sc.prof[k / kMatStride][k % kMatStride];
+        smat[k] = P16 ? (int8_t)a.sc.profu[k / kMatStride][k % kMatStride]
+                      : a.sc.prof[k / kMatStride][k % kMatStride];
     __syncthreads();
 
     const int warp = threadIdx.x >> 5;
@@ -469,6 +459,15 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const uint32_t NOE = L::splat(-oe);
     const uint32_t NE = L::splat(-a.sc.ge);
     const uint32_t MONE = L::splat(-1);
+    // Row state Hop = H - (o + e), kept biased by kBias on the packed path;
+    // the profile holds s + o + e, so the diagonal term Hop + prof = H + s is
+    // one add.  HZ is the value of Hop at H = 0, which is also the value of
+    // E and F at -(o + e), their "minus infinity" at the borders.
+    const int zero_h = P16 ? kBias - oe : -oe;
+    const uint32_t HZ = L::splat(zero_h);
+    const uint32_t BV = L::splat(kBias);                  // H = 0 on the packed path
+    const uint32_t one = (uint32_t)a.sc.one;              // 1 at run time: adds issue as multiply-adds
+    const uint32_t C_UOP = (uint32_t)(-(oe * 65537));    // U -> U - (o + e) in both halves
 
     for (;;) {
         uint32_t task = 0;
@@ -532,11 +531,11 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
         int bv[PACK], bi[PACK], bj[PACK];
 #pragma unroll
         for (int h = 0; h < PACK; ++h) {
-            bv[h] = -oe;
+            bv[h] = zero_h;
             bi[h] = INT_MAX;
             bj[h] = INT_MAX;
         }
-        uint32_t T = NOE;   // lower bound of the final H - (o + e), per half
+        uint32_t T = HZ;   // lower bound of the final score (tracked units), per half
         // reverse pass: the score S is known; fi = first streamed step at which
         // this lane recorded a cell of value S, per half
         int fi[PACK];
@@ -578,11 +577,11 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             uint32_t Hop[R], F[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                Hop[r] = NOE;   // H - (o + e) of the previous query position
-                F[r] = NOE;
+                Hop[r] = HZ;   // H = 0 before the first query position
+                F[r] = HZ;
             }
-            uint32_t hin_prev = NOE, eout = NOE, hout = NOE;
-            uint32_t lb = NOE;                      // this lane's maximum in this chunk
+            uint32_t hin_prev = HZ, eout = HZ, hout = HZ;
+            uint32_t lb = HZ;                       // this lane's maximum in this chunk
             uint32_t lb1 = L::addmax(T, MONE, lb);  // per half max(lb, T - 1)
             uint32_t snap[PACK][R];                 // registers at the last recorded step
             int si[PACK], sv[PACK];
@@ -591,7 +590,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 si[h] = -1;
                 sv[h] = INT_MIN;
 #pragma unroll
-                for (int r = 0; r < R; ++r) snap[h][r] = NOE;
+                for (int r = 0; r < R; ++r) snap[h][r] = HZ;
             }
 
             const bool read_bnd = (c > 0) && (gl == 0);
@@ -608,14 +607,14 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 pwn[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
                 xn[h] = code_at(h, 1 - gl);
             }
-            uint32_t ein = NOE, hin = NOE;   // from lane gl-1, previous step
+            uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
 
             // The step loop, compiled twice for the 32-lane tiles: with the
             // chunk-boundary exchange (BND, references longer than one tile) and
             // without it (one tile, and every smaller shape).
             auto wavefront = [&](auto bnd_tag) {
             constexpr bool BND = decltype(bnd_tag)::value;
-            uint2 bcur = make_uint2(NOE, NOE);
+            uint2 bcur = make_uint2(HZ, HZ);
             if (BND && read_bnd && ls_c > 0) bcur = bnd[0];
 
             // Lanes step in lock step without branching on their own range:
@@ -639,23 +638,28 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                         // "minus infinity": cells there score alignments confined
                         // to this chunk, never above the pair's score
                         const bool take = read_bnd && i < ls_c;
-                        ein = take ? bcur.x : NOE;
-                        hin = take ? bcur.y : NOE;
+                        ein = take ? bcur.x : HZ;
+                        hin = take ? bcur.y : HZ;
                     }
                     if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
                 } else {
                     if (gl == 0) {
-                        ein = NOE;
-                        hin = NOE;
+                        ein = HZ;
+                        hin = HZ;
                     }
                 }
-                // phase 1, independent rows: u = max(Hdiag + s, F), U = max(u, 0) - (o + e)
+                // phase 1, independent rows: U = max(Hdiag + s, F, 0) - (o + e)
                 uint32_t U[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
                     const uint32_t hd = r == 0 ? hin_prev : Hop[r - 1];
-                    U[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
+                    if constexpr (P16) {
+                        const uint32_t d = s * one + hd;                 // H_diag + s (biased)
+                        U[r] = L::max3(d, F[r], BV) * one + C_UOP;       // max(., F, 0) - (o + e)
+                    } else {
+                        U[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
+                    }
                 }
                 // phase 2, the chain along the rows: H - (o + e) and E of the next row
                 uint32_t e = ein;
@@ -691,7 +695,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                                 sv[h] = L::get(m, h);
 #pragma unroll
                                 for (int r = 0; r < R; ++r) snap[h][r] = Hop[r];
-                                if (REV && sv[h] == target[h] - oe && i < fi[h]) fi[h] = i;
+                                if (REV && sv[h] == target[h] + zero_h && i < fi[h]) fi[h] = i;
                             }
                         }
                     }
@@ -781,7 +785,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 }
             }
             if (gl == 0 && pid[h] >= 0) {
-                const int S = v + oe;
+                const int S = v - zero_h;
                 swgb_record* rec = &a.out[pid[h]];
                 if (!REV) {
                     if (S > 0 && ii != INT_MAX) {

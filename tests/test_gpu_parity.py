@@ -76,6 +76,29 @@ def test_gap_settings_and_asymmetric_matrix(aligner, oracle_mod, blosum, plain10
                 oracle_records(oracle_mod, sub, asym, 7, 2), sub)
 
 
+def test_matrices_at_the_packed_score_range(aligner, oracle_mod, plain10k):
+    """The packed path holds s + o + e in a byte of 0..127: a matrix reaching
+    both ends of that range stays packed; one entry with s + o + e < 0 moves
+    every pair to the 32-bit path, with the same records."""
+    sub = plain10k.subset(np.arange(5, 10000, 17))
+    go, ge = 40, 3
+    lo, hi = -(go + ge), 127 - (go + ge)
+    rng = np.random.default_rng(11)
+    wide = rng.integers(lo, hi + 1, size=(24, 24)).astype(np.int8)
+    wide[0, 0], wide[1, 2] = hi, lo
+    np.fill_diagonal(wide[4:], 40)
+    want = oracle_records(oracle_mod, sub, wide, go, ge)
+    assert_same(gpu_records(aligner, sub, params(wide, go, ge)), want, sub)
+    st = aligner.stats()
+    assert st["n_int16_pairs"] + st["n_int32_pairs"] == len(sub.pairs)
+    assert st["n_int16_pairs"] > 0
+    out = wide.copy()
+    out[3, 3] = lo - 1
+    want = oracle_records(oracle_mod, sub, out, go, ge)
+    assert_same(gpu_records(aligner, sub, params(out, go, ge)), want, sub)
+    assert aligner.stats()["n_int16_pairs"] == 0
+
+
 HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129,
                 159, 160, 161, 191, 192, 193, 223, 224, 225, 255, 256, 257, 319, 320, 321,
                 383, 384, 385, 447, 448, 449, 511, 512, 513, 767, 768, 769, 1023, 1024, 1025,
