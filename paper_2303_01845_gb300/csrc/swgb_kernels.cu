@@ -270,6 +270,9 @@ struct Lane<true> {
     __device__ __forceinline__ static int get(uint32_t w, int h) {
         return h ? (int)(w >> 16) : (int)(w & 0xffffu);
     }
+    __device__ __forceinline__ static uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
+        return __vimin3_u16x2(a, b, c);
+    }
     // score of row b (0..3) of the word pair: low half from a (pair 0),
     // high half from c (pair 1); packed-path profile bytes are 0..127, so
     // extending the sign bit fills zeros
@@ -291,6 +294,9 @@ struct Lane<false> {
     }
     __device__ __forceinline__ static uint32_t splat(int v) { return (uint32_t)v; }
     __device__ __forceinline__ static int get(uint32_t w, int) { return (int)w; }
+    __device__ __forceinline__ static uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
+        return (uint32_t)__vimin3_s32((int)a, (int)b, (int)c);
+    }
     __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t, int b) {
         const uint32_t s = (uint32_t)(b | 8);
         const uint32_t sel = (uint32_t)b | (s << 4) | (s << 8) | (s << 12);
@@ -422,8 +428,13 @@ __device__ __forceinline__ int group_min(int v) {
 // read from the snapshot once per chunk.  A lane whose maximum never reached T
 // holds no cell of the final score, so skipping its positions loses nothing;
 // ties with T are recorded.
+// Blocks per SM the shared-memory profile of a 21-row, R-row-per-lane launch
+// leaves room for (8-, 12- or 16-byte lane strides), given to the compiler as
+// the register budget: 65536 / (64 threads x blocks) registers per thread.
+__host__ __device__ constexpr int dp_min_blocks(int R) { return R <= 8 ? 8 : R <= 12 ? 6 : 5; }
+
 template <int G, int R, bool P16, bool REV>
-__global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
+__global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const DPArgs a) {
     using L = Lane<P16>;
     constexpr int PACK = L::kPack;
     constexpr int GROUPS = 32 / G;
@@ -467,6 +478,8 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
     const uint32_t HZ = L::splat(zero_h);
     const uint32_t BV = L::splat(kBias);                  // H = 0 on the packed path
     const uint32_t one = (uint32_t)a.sc.one;              // 1 at run time: adds issue as multiply-adds
+    const uint32_t neg_one = 0u - one;
+    const uint32_t ONE = L::splat(1);
     const uint32_t C_UOP = (uint32_t)(-(oe * 65537));    // U -> U - (o + e) in both halves
 
     for (;;) {
@@ -574,23 +587,30 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             __syncwarp();
 
             // ---- wavefront over the streamed query
-            uint32_t Hop[R], F[R];
+            // Row state of the last two steps: the step loop is unrolled by two
+            // and alternates the roles of HopA / HopB (and of the profile words
+            // pwA / pwB), so the previous step's registers stay available
+            // without copies.  Between pairs of steps the state is in the A set.
+            uint32_t HopA[R], HopB[R], F[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                Hop[r] = HZ;   // H = 0 before the first query position
+                HopA[r] = HZ;   // H = 0 before the first query position
                 F[r] = HZ;
             }
-            uint32_t hin_prev = HZ, eout = HZ, hout = HZ;
+            uint32_t hin_prev = HZ;
             uint32_t lb = HZ;                       // this lane's maximum in this chunk
             uint32_t lb1 = L::addmax(T, MONE, lb);  // per half max(lb, T - 1)
-            uint32_t snap[PACK][R];                 // registers at the last recorded step
+            // the kept event's row values of each half; on the packed path two
+            // rows per register (row 2k low, row 2k + 1 high)
+            constexpr int NS = P16 ? R / 2 : R;
+            uint32_t snap[PACK][NS];
             int si[PACK], sv[PACK];
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
                 si[h] = -1;
                 sv[h] = INT_MIN;
 #pragma unroll
-                for (int r = 0; r < R; ++r) snap[h][r] = HZ;
+                for (int k = 0; k < NS; ++k) snap[h][k] = HZ;
             }
 
             const bool read_bnd = (c > 0) && (gl == 0);
@@ -599,14 +619,25 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             int stop_w = INT_MAX;   // reverse pass: warp-uniform last useful step
 
             // software pipeline: profile words of the next step and the query
-            // letter of the step after are fetched one step ahead
-            ProfWords<LS> pwn[PACK];
-            int xn[PACK];
+            // letter of the step after are fetched one step ahead.  A lane's
+            // streamed position is one behind the lane before it, so the letter
+            // it needs next is the one that lane holds now: letters move down
+            // the group by shuffle, and lane 0 reads them from a batch of
+            // kBatch letters (xb); the group loads the batch after it (xc) one
+            // batch period ahead.
+            constexpr int kBatch = G < kBoundEvery ? G : kBoundEvery;
+            ProfWords<LS> pwA[PACK], pwB[PACK];
+            int xn[PACK], xb[PACK], xc[PACK];
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                pwn[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
+                pwA[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
                 xn[h] = code_at(h, 1 - gl);
+                xb[h] = code_at(h, 2 + gl);            // positions for steps 0 .. kBatch - 1
+                xc[h] = code_at(h, 2 + kBatch + gl);   // steps kBatch .. 2 kBatch - 1
             }
+            // per half 1 where the previous step had an event whose registers
+            // are not kept yet, else 0
+            uint32_t pend = 0;
             uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
 
             // The step loop, compiled twice for the 32-lane tiles: with the
@@ -617,20 +648,41 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
             uint2 bcur = make_uint2(HZ, HZ);
             if (BND && read_bnd && ls_c > 0) bcur = bnd[0];
 
+            // keeps the registers of an event at streamed position ii (Hp holds
+            // that step's values) as half h's candidate
+            auto keep = [&](int h, int ii, const uint32_t (&Hp)[R]) {
+                si[h] = ii;
+                sv[h] = L::get(lb, h);
+                if constexpr (P16) {
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        snap[h][k] = prmt(Hp[2 * k], Hp[2 * k + 1], h ? 0x7632u : 0x5410u);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) snap[h][r] = Hp[r];
+                }
+                if (REV && sv[h] == target[h] + zero_h && ii < fi[h]) fi[h] = ii;
+            };
+
+            // One step: query position i = t - gl against the lane's rows.  Hp
+            // holds the previous step's row state, Hn receives this step's; pw
+            // holds this step's profile words and pwn receives the next step's.
+            //
             // Lanes step in lock step without branching on their own range:
             // before its first position a lane sees only pad letters and
             // "minus infinity" inputs from the lane before, which leaves its
             // initial state unchanged; after its last position it computes pad
             // cells, which score below the best real cell feeding them and can
             // never be the pair's maximum.  Only the boundary store is guarded.
-            for (int t = 0; t < steps && t <= stop_w; ++t) {
+            auto step = [&](int t, const uint32_t (&Hp)[R], uint32_t (&Hn)[R],
+                            const ProfWords<LS> (&pw)[PACK], ProfWords<LS> (&pwn)[PACK]) {
                 const int i = t - gl;
-                ProfWords<LS> pw[PACK];
 #pragma unroll
                 for (int h = 0; h < PACK; ++h) {
-                    pw[h] = pwn[h];
                     pwn[h] = load_prof<LS>(plane + h * PROF + xn[h] * RS);
-                    xn[h] = code_at(h, i + 2);
+                    const int from_prev = __shfl_up_sync(kFull, xn[h], 1, G);
+                    const int from_batch = __shfl_sync(kFull, xb[h], t & (kBatch - 1), G);
+                    xn[h] = gl == 0 ? from_batch : from_prev;   // letter of position i + 2
                 }
                 if constexpr (BND) {
                     if (gl == 0) {
@@ -649,60 +701,74 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                     }
                 }
                 // phase 1, independent rows: U = max(Hdiag + s, F, 0) - (o + e)
-                uint32_t U[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t s = L::widen(pw[0].w[r >> 2], pw[PACK - 1].w[r >> 2], r & 3);
-                    const uint32_t hd = r == 0 ? hin_prev : Hop[r - 1];
+                    const uint32_t hd = r == 0 ? hin_prev : Hp[r - 1];
                     if constexpr (P16) {
                         const uint32_t d = s * one + hd;                 // H_diag + s (biased)
-                        U[r] = L::max3(d, F[r], BV) * one + C_UOP;       // max(., F, 0) - (o + e)
+                        Hn[r] = L::max3(d, F[r], BV) * one + C_UOP;      // max(., F, 0) - (o + e)
                     } else {
-                        U[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
+                        Hn[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
                     }
                 }
                 // phase 2, the chain along the rows: H - (o + e) and E of the next row
                 uint32_t e = ein;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t hn = L::addmax(e, NOE, U[r]);
-                    e = L::addmax(e, NE, U[r]);
-                    U[r] = hn;
+                    const uint32_t hn = L::addmax(e, NOE, Hn[r]);
+                    e = L::addmax(e, NE, Hn[r]);
+                    Hn[r] = hn;
                 }
                 // phase 3, independent rows: F of the next query position
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    F[r] = L::addmax(F[r], NE, U[r]);
-                    Hop[r] = U[r];
-                }
-                eout = e;
-                hout = Hop[R - 1];
+                for (int r = 0; r < R; ++r) F[r] = L::addmax(F[r], NE, Hn[r]);
                 hin_prev = hin;
                 if constexpr (BND) {
-                    if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(eout, hout);
+                    if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(e, Hn[R - 1]);
                 }
-                const uint32_t e_next = __shfl_up_sync(kFull, eout, 1, G);
-                const uint32_t h_next = __shfl_up_sync(kFull, hout, 1, G);
+                const uint32_t e_next = __shfl_up_sync(kFull, e, 1, G);
+                const uint32_t h_next = __shfl_up_sync(kFull, Hn[R - 1], 1, G);
                 {
-                    // a half records when its maximum m passes lb and reaches T,
-                    // i.e. m > max(lb, T - 1) = lb1; in no half iff max(m, lb1) == lb1
-                    const uint32_t m = tree_max<P16, R>(Hop, lb);
-                    if (L::max3(m, lb1, lb1) != lb1) {
+                    // A half has an event when its maximum m passes lb and reaches
+                    // T, i.e. m > max(lb, T - 1) = lb1.  Events come in runs while
+                    // an alignment grows through the lane's rows; only the last of
+                    // a run can hold the lane's maximum, so its registers are kept
+                    // at the step after the run ends, from Hp.
+                    const uint32_t m = tree_max<P16, R>(Hn, lb);
+                    const uint32_t nlb1 = L::max3(lb1, m, m);
+                    // nlb1 >= lb1 in each half, so the 32-bit difference is exact
+                    // per half; up = 1 in the halves with an event, else 0
+                    const uint32_t up = L::min3(nlb1 + lb1 * neg_one, ONE, ONE);
+                    const uint32_t ended = pend & ~up;
+                    if (ended != 0) {
+#pragma unroll
+                        for (int h = 0; h < PACK; ++h)
+                            if (L::get(ended, h) != 0) keep(h, i - 1, Hp);
+                    }
+                    pend = up;
+                    lb = m;
+                    lb1 = nlb1;
+                }
+                // the batch of the steps from t + 1 on was loaded a period ago;
+                // load the one after it
+                if constexpr (kBatch < kBoundEvery) {
+                    if ((t & (kBatch - 1)) == kBatch - 1) {
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
-                            if (L::get(m, h) > L::get(lb1, h)) {
-                                si[h] = i;
-                                sv[h] = L::get(m, h);
-#pragma unroll
-                                for (int r = 0; r < R; ++r) snap[h][r] = Hop[r];
-                                if (REV && sv[h] == target[h] + zero_h && i < fi[h]) fi[h] = i;
-                            }
+                            xb[h] = xc[h];
+                            xc[h] = code_at(h, t + 3 + kBatch + gl);
                         }
                     }
-                    lb = m;
-                    lb1 = L::addmax(T, MONE, m);
                 }
                 if ((t & (kBoundEvery - 1)) == kBoundEvery - 1) {
+                    if constexpr (kBatch == kBoundEvery) {
+#pragma unroll
+                        for (int h = 0; h < PACK; ++h) {
+                            xb[h] = xc[h];
+                            xc[h] = code_at(h, t + 3 + kBatch + gl);
+                        }
+                    }
                     T = group_max<P16, G>(L::max3(lb, T, T));
                     lb1 = L::addmax(T, MONE, lb);
                     if constexpr (REV) {
@@ -725,7 +791,25 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                 }
                 ein = e_next;
                 hin = h_next;
+            };
+
+            int t = 0;
+            for (;;) {
+                if (!(t < steps && t <= stop_w)) break;
+                step(t, HopA, HopB, pwA, pwB);
+                ++t;
+                if (!(t < steps && t <= stop_w)) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) HopA[r] = HopB[r];
+                    break;
+                }
+                step(t, HopB, HopA, pwB, pwA);
+                ++t;
             }
+            // a run of events still open at the last step
+#pragma unroll
+            for (int h = 0; h < PACK; ++h)
+                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA);
             };
             if constexpr (G == 32) {
                 if (nch > 1) wavefront(std::true_type{});
@@ -744,7 +828,7 @@ __global__ void __launch_bounds__(kDPThreads) dp_kernel(const DPArgs a) {
                     int row = R - 1;
 #pragma unroll
                     for (int r = R - 1; r >= 0; --r)
-                        if (L::get(snap[h][r], h) == sv[h]) row = r;
+                        if ((P16 ? L::get(snap[h][r / 2], r & 1) : L::get(snap[h][r], h)) == sv[h]) row = r;
                     if (better(sv[h], si[h], jl + row, bv[h], bi[h], bj[h])) {
                         bv[h] = sv[h];
                         bi[h] = si[h];
