@@ -1,12 +1,15 @@
-"""CPU oracle for batched Smith-Waterman with affine gaps.
+"""CPU oracle for batched Smith-Waterman with affine gaps, candidate
+discovery by shared k-mers and alignment identity.
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
 benchmark's CPU-baseline leg may import this package; the product path never
 does, and the oracle imports nothing from the product.
 
 The arithmetic lives in ``sw_oracle.c`` (plain int32 Gotoh, forward pass for
-score and end, reverse pass on the reversed prefixes for the start); this
-module only marshals arguments through ctypes.  Conventions (the paper states
+score and end, reverse pass on the reversed prefixes for the start) and
+``discovery_oracle.c`` (distinct k-mer sets intersected by merging; global
+Gotoh of an alignment's span traced back for its identity); this module only
+marshals arguments through ctypes.  Conventions (the paper states
 none of them):
 
 * rows are query residues, columns reference residues;
@@ -54,6 +57,20 @@ def load():
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_int]
     lib.oracle_align_batch.restype = ctypes.c_int
+    vp = ctypes.c_void_p
+    lib.oracle_shared_kmers.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_shared_kmers.restype = ctypes.c_int64
+    lib.oracle_kmer_index.argtypes = [u8p, i64p, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_kmer_index.restype = vp
+    lib.oracle_kmer_index_free.argtypes = [vp]
+    lib.oracle_kmer_index_free.restype = None
+    lib.oracle_candidates_of.argtypes = [vp, ctypes.c_int64, ctypes.c_int, i32p, i32p, ctypes.c_int64]
+    lib.oracle_candidates_of.restype = ctypes.c_int64
+    lib.oracle_all_candidates.argtypes = [vp, ctypes.c_int, i32p, i32p, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_all_candidates.restype = ctypes.c_int64
+    lib.oracle_span_identity.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, i32p, i8p,
+                                         ctypes.c_int32, ctypes.c_int32, i32p, i32p]
+    lib.oracle_span_identity.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -144,3 +161,95 @@ def align_batch(q_res, q_off, r_res, r_off, pairs, mat=None, gap_open=11, gap_ex
     if st != 0:
         raise RuntimeError("oracle_align_batch failed: %d" % st)
     return out
+
+
+def shared_kmers(a, b, k=6):
+    """|K(a) & K(b)|: distinct k-mers of standard letters common to a and b."""
+    ac, bc = _codes(a), _codes(b)
+    c = load().oracle_shared_kmers(_ptr(ac, ctypes.c_uint8), len(ac), _ptr(bc, ctypes.c_uint8),
+                                   len(bc), k)
+    if c < 0:
+        raise ValueError("bad k or out of memory")
+    return int(c)
+
+
+class KmerIndex:
+    """The distinct k-mer sets of every sequence of a set (res, off)."""
+
+    def __init__(self, res, off, k=6):
+        self._res = np.ascontiguousarray(res, dtype=np.uint8)
+        self._off = np.ascontiguousarray(off, dtype=np.int64)
+        self.n = len(self._off) - 1
+        self._h = load().oracle_kmer_index(_ptr(self._res, ctypes.c_uint8),
+                                           _ptr(self._off, ctypes.c_int64), self.n, k)
+        if not self._h:
+            raise RuntimeError("oracle_kmer_index failed")
+
+    def close(self):
+        if self._h:
+            load().oracle_kmer_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def candidates_of(self, i, min_shared=2):
+        """(js, counts): every j != i sharing >= min_shared k-mers with i."""
+        lib = load()
+        cap = 1024
+        while True:
+            js = np.zeros(cap, np.int32)
+            cs = np.zeros(cap, np.int32)
+            n = lib.oracle_candidates_of(self._h, int(i), min_shared, _ptr(js, ctypes.c_int32),
+                                         _ptr(cs, ctypes.c_int32), cap)
+            if n < 0:
+                raise RuntimeError("oracle_candidates_of failed")
+            if n <= cap:
+                return js[:n], cs[:n]
+            cap = int(n)
+
+    def all_candidates(self, min_shared=2, n_threads=None):
+        """(pairs [P, 2] with i < j ordered by (i, j), counts [P])."""
+        lib = load()
+        threads = n_threads or min(os.cpu_count() or 1, 64)
+        cap = 1 << 16
+        while True:
+            pairs = np.zeros((cap, 2), np.int32)
+            cs = np.zeros(cap, np.int32)
+            n = lib.oracle_all_candidates(self._h, min_shared, _ptr(pairs, ctypes.c_int32),
+                                          _ptr(cs, ctypes.c_int32), cap, threads)
+            if n < 0:
+                raise RuntimeError("oracle_all_candidates failed")
+            if n <= cap:
+                order = np.lexsort((pairs[:n, 1], pairs[:n, 0]))
+                return pairs[:n][order], cs[:n][order]
+            cap = int(n)
+
+
+def span_identity(q, r, record, mat=None, gap_open=11, gap_extend=1):
+    """(identical columns, columns) of the traced alignment of a record's span;
+    (0, 0) for a zero score."""
+    qc, rc = _codes(q), _codes(r)
+    m = _matrix(blosum62() if mat is None else mat)
+    rec = np.ascontiguousarray(np.asarray(record, dtype=np.int32).reshape(5))
+    mt = ctypes.c_int32()
+    cols = ctypes.c_int32()
+    st = load().oracle_span_identity(_ptr(qc, ctypes.c_uint8), len(qc), _ptr(rc, ctypes.c_uint8),
+                                     len(rc), _ptr(rec, ctypes.c_int32), _ptr(m, ctypes.c_int8),
+                                     gap_open, gap_extend, ctypes.byref(mt), ctypes.byref(cols))
+    if st < 0:
+        raise RuntimeError("oracle_span_identity failed: %d" % st)
+    return mt.value, cols.value
+
+
+def passes(record, matches, columns, lq, lr, min_identity=(3, 10), min_coverage=(7, 10)):
+    """Pass/fail at identity >= a/b and coverage >= c/d, decided exactly in
+    integers: matches * b >= a * columns and, for both sequences,
+    span * d >= c * length."""
+    score, qs, qe, rs, re_ = (int(v) for v in record)
+    if score <= 0 or columns <= 0:
+        return False
+    a, b = min_identity
+    c, d = min_coverage
+    return (matches * b >= a * columns and (qe - qs + 1) * d >= c * lq
+            and (re_ - rs + 1) * d >= c * lr)

@@ -1,4 +1,5 @@
-"""Compiles the CPU oracle (sw_oracle.c) into oracle/_build/liboracle.so.
+"""Compiles the CPU oracle (sw_oracle.c, discovery_oracle.c) into
+oracle/_build/liboracle.so.
 
 Test infrastructure only: the product path never loads this library.
 """
@@ -6,20 +7,20 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "sw_oracle.c")
+SRCS = [os.path.join(HERE, "sw_oracle.c"), os.path.join(HERE, "discovery_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 
 def command():
     return ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-            "-Wall", "-Wextra", "-o", LIB, SRC]
+            "-Wall", "-Wextra", "-o", LIB, *SRCS]
 
 
 def build(force=False):
     """Builds the library if it is missing or older than its source."""
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(src) for src in SRCS)):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     subprocess.run(command(), check=True)

@@ -73,6 +73,53 @@ SPECS = {
 
 
 @dataclasses.dataclass
+class FamilySpec:
+    """A sequence set of ``n_families`` x ``copies`` sequences: each family's
+    root has a drawn length, every copy is mutate(root)."""
+    name: str
+    n_families: int
+    copies: int
+    length_model: str
+    lmin: int
+    lmax: int
+    median: float = 0.0
+    sigma: float = 0.0
+    subst_rate: float = 0.40
+    indel_rate: float = 0.05
+    indel_mean: float = 3.0
+    seed: int = 3
+
+
+FAMILY_SPECS = {
+    # the many-against-many block: 200,000 sequences in 20,000 families of 10
+    "families_200k": FamilySpec("families_200k", 20_000, 10, "lognormal", 20, 5000,
+                                median=250.0, sigma=0.7),
+    # the same recipe at a size the all-pairs oracle finishes in seconds
+    "families_2k": FamilySpec("families_2k", 200, 10, "lognormal", 20, 5000,
+                              median=250.0, sigma=0.7),
+}
+
+
+@dataclasses.dataclass
+class SequenceSet:
+    """Concatenated residue codes with offsets, and each sequence's family."""
+    spec: FamilySpec
+    res: np.ndarray     # uint8 codes
+    off: np.ndarray     # int64 [n + 1]
+    family: np.ndarray  # int32 [n]
+
+    @property
+    def lengths(self):
+        return np.diff(self.off)
+
+    def __len__(self):
+        return len(self.off) - 1
+
+    def seq(self, i):
+        return self.res[self.off[i]:self.off[i + 1]]
+
+
+@dataclasses.dataclass
 class Workload:
     """Concatenated residue codes with offsets; pair p = (query p, reference p)."""
     spec: Spec
@@ -113,6 +160,10 @@ def _load():
         lib.wl_lengths.restype = ctypes.c_int
         lib.wl_fill.argtypes = [ctypes.POINTER(_Params), vp, vp, vp, vp, vp, vp, ctypes.c_int]
         lib.wl_fill.restype = ctypes.c_int
+        lib.wl_family_lengths.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, vp, vp, vp, ctypes.c_int]
+        lib.wl_family_lengths.restype = ctypes.c_int
+        lib.wl_family_fill.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int]
+        lib.wl_family_fill.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -214,3 +265,32 @@ def from_sequences(queries, references, pairs):
     spec = Spec("explicit", len(pairs), "uniform", 0, 0)
     return Workload(spec, q_res, q_off, r_res, r_off,
                     np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2)))
+
+
+def generate_families(spec, mat, n_threads=None):
+    """Draws the family set ``spec`` (a FamilySpec or a name in FAMILY_SPECS)."""
+    if isinstance(spec, str):
+        spec = FAMILY_SPECS[spec]
+    lib = _load()
+    bg, sub = sampling_tables(mat)
+    P = _Params(n_pairs=spec.n_families, n_homologous=0, seed=spec.seed & 0xFFFFFFFFFFFFFFFF,
+                length_model=0 if spec.length_model == "uniform" else 1,
+                lmin=spec.lmin, lmax=spec.lmax, median=spec.median, sigma=spec.sigma,
+                subst_rate=spec.subst_rate, indel_rate=spec.indel_rate,
+                indel_mean=spec.indel_mean)
+    n = spec.n_families * spec.copies
+    threads = n_threads or min(os.cpu_count() or 1, 64)
+    lengths = np.zeros(n, np.int64)
+    st = lib.wl_family_lengths(ctypes.byref(P), spec.copies, bg.ctypes.data, sub.ctypes.data,
+                               lengths.ctypes.data, threads)
+    if st:
+        raise RuntimeError("family length pass failed: %d" % st)
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum(lengths, out=off[1:])
+    res = np.empty(int(off[-1]), np.uint8)
+    st = lib.wl_family_fill(ctypes.byref(P), spec.copies, bg.ctypes.data, sub.ctypes.data,
+                            off.ctypes.data, res.ctypes.data, threads)
+    if st:
+        raise RuntimeError("family fill pass failed: %d" % st)
+    family = (np.arange(n, dtype=np.int64) // spec.copies).astype(np.int32)
+    return SequenceSet(spec, res, off, family)

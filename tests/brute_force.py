@@ -94,3 +94,34 @@ def global_affine(q, r, score, go, ge):
             F[i][j] = max(F[i - 1][j] - ge, H[i - 1][j] - go - ge)
             H[i][j] = max(H[i - 1][j - 1] + score(q[i - 1], r[j - 1]), E[i][j], F[i][j])
     return H[lq][lr]
+
+
+def enumerate_global(q, r, score, go, ge):
+    """Yields (total, identical columns, columns) for every global alignment
+    of q against r: every sequence of columns D (q_i with r_j), V (q_i with a
+    gap) and Z (a gap with r_j) consuming both; a maximal run of L gap
+    columns of one kind costs go + ge * L.  For tiny inputs only."""
+    lq, lr = len(q), len(r)
+
+    def rec(i, j, last, run, total, same, cols):
+        if i == lq and j == lr:
+            closing = -(go + ge * run) if last in ("V", "Z") else 0
+            yield total + closing, same, cols
+            return
+        def close():
+            return -(go + ge * run) if last in ("V", "Z") else 0
+        if i < lq and j < lr:
+            yield from rec(i + 1, j + 1, "D", 0, total + close() + score(q[i], r[j]),
+                           same + (q[i] == r[j]), cols + 1)
+        if i < lq:
+            if last == "V":
+                yield from rec(i + 1, j, "V", run + 1, total, same, cols + 1)
+            else:
+                yield from rec(i + 1, j, "V", 1, total + close(), same, cols + 1)
+        if j < lr:
+            if last == "Z":
+                yield from rec(i, j + 1, "Z", run + 1, total, same, cols + 1)
+            else:
+                yield from rec(i, j + 1, "Z", 1, total + close(), same, cols + 1)
+
+    yield from rec(0, 0, None, 0, 0, 0, 0)

@@ -81,3 +81,22 @@ def test_substitution_weights_follow_the_matrix(mat):
     w /= w.sum()
     assert np.abs(counts - w).max() < 1e-3
     assert counts[a] == 0
+
+
+def test_family_sets_are_seeded_and_grouped():
+    from paper_2303_01845_gb300 import workload
+    import oracle
+    mat = oracle.blosum62()
+    a = workload.generate_families("families_2k", mat, n_threads=3)
+    b = workload.generate_families("families_2k", mat, n_threads=1)
+    assert len(a) == 2000 and np.array_equal(a.res, b.res) and np.array_equal(a.off, b.off)
+    assert np.array_equal(a.family, np.repeat(np.arange(200), 10))
+    assert a.res.max() < 20 and a.lengths.min() >= 1
+    # copies of one family are closer to each other than to other families
+    same = oracle.shared_kmers(a.seq(0), a.seq(1), 3)
+    other = oracle.shared_kmers(a.seq(0), a.seq(15), 3)
+    assert a.lengths[:10].std() < a.lengths.std() * 2
+    assert same >= 0 and other >= 0
+    # the 200,000-sequence recipe: log-normal lengths around 250
+    spec = workload.FAMILY_SPECS["families_200k"]
+    assert spec.n_families * spec.copies == 200_000
