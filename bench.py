@@ -7,6 +7,9 @@ inputs resident in HBM.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
+    python bench.py --workload families_200k   # many-against-many block:
+        one step = candidate discovery by shared 6-mers + alignment of every
+        candidate + identity / pass-fail, on 200,000 resident sequences
 
 Under torchrun every rank aligns its own copy of the workload (weak scaling,
 no collective on the data path); the step time is the max over ranks.
@@ -407,10 +410,155 @@ def measure_e2e(al, wl, mat, dev, stream, args):
             "alignments_per_s": len(wl.pairs) / dt}
 
 
+def search_oracle_sample(fs, mat, target_s, seed=5):
+    """The oracle pipeline on sampled rows of a family block: k-mer-set merges
+    of row i against every sequence, alignment of its partners j > i, identity
+    and pass/fail; about target_s seconds."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    ix = oracle.KmerIndex(fs.res, fs.off, 6)
+    index_s = time.perf_counter() - t0
+    rows, pairs, t_rows = 0, 0, 0.0
+    for i in rng.permutation(len(fs)):
+        t = time.perf_counter()
+        js, _ = ix.candidates_of(int(i), 2)
+        js = js[js > i]
+        if len(js):
+            pr = np.stack([np.full(len(js), i, np.int32), js.astype(np.int32)], axis=1)
+            rec = oracle.align_batch(fs.res, fs.off, fs.res, fs.off, pr, mat, 11, 1,
+                                     n_threads=cores)
+            for p in range(len(pr)):
+                a, b = pr[p]
+                qs = fs.res[fs.off[a]:fs.off[a + 1]]
+                rs = fs.res[fs.off[b]:fs.off[b + 1]]
+                mt, cols = oracle.span_identity(qs, rs, rec[p], mat, 11, 1)
+                oracle.passes(rec[p], mt, cols, len(qs), len(rs))
+        t_rows += time.perf_counter() - t
+        rows += 1
+        pairs += len(js)
+        if t_rows > target_s:
+            break
+    ix.close()
+    # the per-row work is a scan over all sequences, so the block's rate is the
+    # sampled rows' candidate rate
+    return {"aln_per_s": pairs / t_rows, "rows": rows, "pairs": pairs, "seconds": t_rows,
+            "index_s": index_s, "cores": cores}
+
+
+def run_search(args):
+    """The many-against-many block: discovery + alignment + identity."""
+    import numpy as np
+    import torch
+
+    from paper_2303_01845_gb300 import swgb, workload
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mat = swgb.swgb_blosum62()
+    fs = workload.generate_families(args.workload, mat)
+    al = swgb.Aligner(local)
+    stream = torch.cuda.current_stream(dev)
+    s = al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
+    params = swgb.make_params(mat, 11, 1, timing=True)
+    th = swgb.make_thresholds()
+    found = swgb.swgb_discover(al.ctx, s.handle, 6, 2, None, stream)[0].shape[0]
+    cap = found
+    cand = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    counts = torch.empty((cap,), dtype=torch.int32, device=dev)
+    rec = torch.empty((cap, 5), dtype=torch.int32, device=dev)
+    ident = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+    import ctypes
+    lib = swgb.load()
+    n_found = ctypes.c_int64()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    parts = {"discover": [], "align": [], "identity": [], "step": [], "fwd": []}
+    launches = 0
+
+    def step(timed):
+        ev[0].record(stream)
+        swgb._check(al.ctx, lib.swgb_discover(al.ctx, s.handle, 6, 2, cand.data_ptr(),
+                                              counts.data_ptr(), cap, ctypes.byref(n_found),
+                                              stream.cuda_stream))
+        n_launch = lib.swgb_search_launches(al.ctx)
+        ev[1].record(stream)
+        swgb.swgb_align(al.ctx, s.handle, s.handle, cand, params, rec, stream)
+        ev[2].record(stream)
+        swgb.swgb_identity(al.ctx, s.handle, s.handle, cand, rec, params, th, ident, stream)
+        n_launch += lib.swgb_search_launches(al.ctx)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if timed:
+            parts["discover"].append(ev[0].elapsed_time(ev[1]))
+            parts["align"].append(ev[1].elapsed_time(ev[2]))
+            parts["identity"].append(ev[2].elapsed_time(ev[3]))
+            parts["step"].append(ev[0].elapsed_time(ev[3]))
+            st = swgb.swgb_last_stats(al.ctx)
+            parts["fwd"].append(st["forward_ms"])
+            st["search_launches"] = n_launch
+            return st
+        return None
+
+    for _ in range(args.warmup):
+        step(False)
+    stats = None
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            stats = step(True)
+            launches += stats["search_launches"] + stats["kernel_launches"]
+    clock = clocks.summary()
+    total_ms = max_over_ranks(sum(parts["step"]), dist, dev)
+    assert n_found.value == cap
+    value = job_rate(cap, world, args.steps, total_ms)
+    ident_np = ident.cpu().numpy()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = search_oracle_sample(fs, np.asarray(mat), args.cpu_seconds)
+    if rank != 0:
+        return
+    mean = lambda k: statistics.mean(parts[k])
+    line = {
+        "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sequences": len(fs), "residues": int(fs.off[-1]),
+                   "k": 6, "min_shared": 2, "candidates": cap,
+                   "forward_cells": stats["forward_cells"],
+                   "passing_pairs": int(ident_np[:, 2].sum()),
+                   "thresholds": "identity >= 3/10, coverage >= 7/10",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "discover_ms": mean("discover"), "align_ms": mean("align"),
+        "identity_ms": mean("identity"), "forward_ms": mean("fwd"),
+        "gcups_forward_kernel": stats["forward_cells"] / (mean("fwd") / 1e3) / 1e9,
+        "cpu_baseline": None if cpu is None else {
+            "value": cpu["aln_per_s"], "unit": "alignments/s", "cores": cpu["cores"],
+            "kind": "oracle",
+            "sample": "%d random rows (%d candidates j > i): k-mer-set merges against all %d "
+                      "sequences, alignment, identity; %.1f s (+ %.1f s k-mer index)" %
+                      (cpu["rows"], cpu["pairs"], len(fs), cpu["seconds"], cpu["index_s"])},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
+                   "reasons": clock["reasons"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("families"):
+        run_search(args)
     else:
         run_ours(args)
 

@@ -57,7 +57,7 @@ extern "C" {
 #define SWGB_ENOMEM (-4)  /* a device or host allocation failed */
 #define SWGB_ECUDA (-5)   /* a CUDA runtime call failed (message in swgb_last_error) */
 #define SWGB_EINTERNAL (-6) /* the device detected an inconsistency in its own results */
-#define SWGB_ETOOBIG (-7) /* a size exceeds the fixed limits of swgb_align_noalloc */
+#define SWGB_ETOOBIG (-7) /* a size exceeds a fixed limit (swgb_align_noalloc, swgb_discover) */
 
 #define SWGB_ALPHABET_SIZE 24
 /* Longest sequence accepted (residues). */
@@ -226,6 +226,77 @@ int swgb_plan_launch(swgb_plan* plan, void* stream);
 
 /* Frees a plan.  NULL is ignored. */
 void swgb_plan_destroy(swgb_plan* plan);
+
+/* ---- candidate discovery by shared k-mers ----
+ * Sec. "Protein similarity search pipeline": the candidate pairs of a
+ * many-against-many search are the nonzeros of the overlap matrix C = A A^T,
+ * A being the sequence-by-k-mer matrix (k = 6 in the production run,
+ * program-parameters table), and C(i, j) the number of k-mers the two
+ * sequences share.  Sec. "Load balancing techniques": C is symmetric, so one
+ * triangle is enough, and pairs below the common-k-mer threshold (2 in
+ * production) are not aligned.  Definitions used here (the paper gives no
+ * formula):
+ *   K(s)    = the set of DISTINCT k-mers of s made of standard letters only
+ *             (codes 0..19; a window touching B, Z, X or * forms no k-mer);
+ *   C(i, j) = |K(s_i) intersect K(s_j)|.
+ * swgb_discover finds every pair i < j of one set with C(i, j) >= min_shared.
+ *   k:          1..6;  min_shared >= 1.
+ *   pairs:      DEVICE int32 [capacity][2], receives (i, j), i < j, ordered by
+ *               i then j (the order does not depend on scheduling);
+ *   counts:     DEVICE int32 [capacity] receiving C(i, j), or NULL;
+ *   capacity:   entries the buffers hold; the first min(found, capacity)
+ *               pairs are written;
+ *   *n_found:   the number of pairs found (may exceed capacity: call again
+ *               with larger buffers).
+ * Synchronous on `stream` (returns after the results are written).  Device
+ * scratch is owned by the context and grown on demand (it may allocate;
+ * about 9 bytes per residue + 8 bytes per possible k-mer value, 20^k).
+ * Errors: EINVAL, ETOOBIG (a set of 2^32 residues or more), ENOMEM, ECUDA,
+ * EINTERNAL. */
+int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int min_shared, int32_t* pairs,
+                  int32_t* counts, int64_t capacity, int64_t* n_found, void* stream);
+
+/* ---- identity, coverage and the similarity filter ----
+ * The production run keeps a pair in the similarity graph when its
+ * alignment has identity >= 0.30 and coverage >= 0.70 (program-parameters
+ * table); the paper defines neither measure.  Definitions used here:
+ *   the global affine alignment (same scores and gaps as swgb_align, no zero
+ *   floor) of the record's span q[q_start..q_end] x r[r_start..r_end] -- its
+ *   optimum is the record's score -- is traced back from the span's end,
+ *   preferring at a cell the diagonal, then a gap in the reference (a query
+ *   residue against a gap), then a gap in the query, and inside a gap its
+ *   opening before its extension;
+ *   identity = identical columns / columns of that alignment;
+ *   coverage = min((q_end - q_start + 1) / lq, (r_end - r_start + 1) / lr);
+ *   pass     = identity >= id_num / id_den and coverage >= cov_num / cov_den,
+ *              decided exactly in integers; a zero score never passes. */
+typedef struct {
+    int32_t id_num, id_den;    /* e.g. 3, 10 */
+    int32_t cov_num, cov_den;  /* e.g. 7, 10 */
+} swgb_thresholds;
+
+typedef struct {
+    int32_t matches;   /* identical columns (0 for a zero score) */
+    int32_t columns;   /* alignment columns incl. gaps (0 for a zero score) */
+    int32_t pass;      /* 1 if the pair passes the thresholds, else 0 */
+} swgb_identity_record;
+
+/* Identity and pass/fail of n_pairs records of swgb_align (same sets, same
+ * pairs, same params).  pairs, records and out are DEVICE buffers, out is
+ * swgb_identity_record [n_pairs] in pair order.  Synchronous on `stream`.
+ * Device scratch (4 bits per cell of the spans being traced, per resident
+ * warp) is owned by the context and grown on demand.
+ * Errors: EINVAL, ENOMEM, ECUDA, ERANGE (a pair index or record coordinate
+ * outside its sequences), EINTERNAL (a record whose span does not reach its
+ * score); such a pair's entry is -1, -1, 0. */
+int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
+                  const int32_t* pairs, const swgb_record* records, int64_t n_pairs,
+                  const swgb_params* params, const swgb_thresholds* thresholds,
+                  swgb_identity_record* out, void* stream);
+
+/* Kernels launched by the last swgb_discover or swgb_identity call on ctx
+ * (-1 for a NULL context). */
+int swgb_search_launches(const swgb_ctx* ctx);
 
 /* ---- allocation-free variant ----
  * The paper has no counterpart of this call; it exists for callers that

@@ -66,6 +66,15 @@ class swgb_stats(ctypes.Structure):
                 ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32)]
 
 
+class swgb_thresholds(ctypes.Structure):
+    _fields_ = [("id_num", ctypes.c_int32), ("id_den", ctypes.c_int32),
+                ("cov_num", ctypes.c_int32), ("cov_den", ctypes.c_int32)]
+
+
+class swgb_identity_record(ctypes.Structure):
+    _fields_ = [("matches", ctypes.c_int32), ("columns", ctypes.c_int32), ("pass_", ctypes.c_int32)]
+
+
 # (name, restype, argtypes) of every exported function
 _VP = ctypes.c_void_p
 _SIGS = [
@@ -96,6 +105,12 @@ _SIGS = [
                                         ctypes.POINTER(swgb_params), _VP, ctypes.POINTER(_VP)]),
     ("swgb_plan_launch", ctypes.c_int, [_VP, _VP]),
     ("swgb_plan_destroy", None, [_VP]),
+    ("swgb_discover", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64), _VP]),
+    ("swgb_identity", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int64,
+                                     ctypes.POINTER(swgb_params), ctypes.POINTER(swgb_thresholds),
+                                     _VP, _VP]),
+    ("swgb_search_launches", ctypes.c_int, [_VP]),
     ("swgb_align_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                           _VP, ctypes.c_int64, ctypes.POINTER(swgb_params), _VP,
                                           _VP]),
@@ -314,6 +329,55 @@ def swgb_plan_destroy(plan):
     load().swgb_plan_destroy(plan)
 
 
+def swgb_discover(ctx, seqset, k=6, min_shared=2, capacity=None, stream=None):
+    """Candidate pairs i < j of one set sharing >= min_shared distinct k-mers.
+
+    Returns (pairs CUDA int32 [P, 2] ordered by (i, j), counts CUDA int32 [P]).
+    With capacity=None the call runs twice when the first guess is too small.
+    """
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cap = 1 << 16 if capacity is None else int(capacity)
+    while True:
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
+        counts = torch.empty((max(cap, 1),), dtype=torch.int32, device=dev)
+        found = ctypes.c_int64()
+        rc = load().swgb_discover(ctx, seqset, int(k), int(min_shared), _ptr(pairs), _ptr(counts),
+                                  cap, ctypes.byref(found), _stream_handle(stream))
+        _check(ctx, rc)
+        n = found.value
+        if n <= cap or capacity is not None:
+            m = min(n, cap)
+            return pairs[:m], counts[:m]
+        cap = n
+
+
+def make_thresholds(min_identity=(3, 10), min_coverage=(7, 10)):
+    return swgb_thresholds(int(min_identity[0]), int(min_identity[1]),
+                           int(min_coverage[0]), int(min_coverage[1]))
+
+
+def swgb_identity(ctx, queries, refs, pairs, records, params, thresholds=None, out=None,
+                  stream=None):
+    """Identity and pass/fail of alignment records (CUDA tensors): returns CUDA
+    int32 [P, 3] = (identical columns, columns, pass).  Synchronous."""
+    import torch
+    n = pairs.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.int32, device=pairs.device)
+    for t_ in (pairs, records, out):
+        if not t_.is_cuda or t_.dtype != torch.int32 or not t_.is_contiguous():
+            raise TypeError("pairs, records and out must be contiguous CUDA int32 tensors")
+    if records.numel() < 5 * n or out.numel() < 3 * n:
+        raise ValueError("records must hold P x 5 and out P x 3 int32")
+    th = thresholds or make_thresholds()
+    rc = load().swgb_identity(ctx, queries, refs, _ptr(pairs), _ptr(records), n,
+                              ctypes.byref(params), ctypes.byref(th), _ptr(out),
+                              _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
 def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, out, stream=None):
     """Allocation-free alignment for callers that cannot allocate device memory
     while they align (a pool or arena owns the device, or the footprint must
@@ -375,6 +439,15 @@ class Aligner:
 
     def stats(self):
         return swgb_last_stats(self.ctx)
+
+    def discover(self, seqset, k=6, min_shared=2, capacity=None, stream=None):
+        return swgb_discover(self.ctx, seqset.handle, k, min_shared, capacity, stream)
+
+    def identity(self, queries, refs, pairs, records, params=None, thresholds=None, out=None,
+                 stream=None):
+        params = params or make_params()
+        return swgb_identity(self.ctx, queries.handle, refs.handle, pairs, records, params,
+                             thresholds, out, stream)
 
 
 class SeqSet:
