@@ -1,5 +1,6 @@
 """CPU oracle for batched Smith-Waterman with affine gaps, candidate
-discovery by shared k-mers and alignment identity.
+discovery by shared k-mers, alignment identity, and the learned candidate
+filter (pair features here; the network in ``mlp_oracle``).
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
 benchmark's CPU-baseline leg may import this package; the product path never
@@ -8,7 +9,8 @@ does, and the oracle imports nothing from the product.
 The arithmetic lives in ``sw_oracle.c`` (plain int32 Gotoh, forward pass for
 score and end, reverse pass on the reversed prefixes for the start) and
 ``discovery_oracle.c`` (distinct k-mer sets intersected by merging; global
-Gotoh of an alignment's span traced back for its identity); this module only
+Gotoh of an alignment's span traced back for its identity) and
+``filter_oracle.c`` (the 32 features of a candidate pair); this module only
 marshals arguments through ctypes.  Conventions (the paper states
 none of them):
 
@@ -71,6 +73,12 @@ def load():
     lib.oracle_span_identity.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, i32p, i8p,
                                          ctypes.c_int32, ctypes.c_int32, i32p, i32p]
     lib.oracle_span_identity.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.oracle_pair_features.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, ctypes.c_int, fp]
+    lib.oracle_pair_features.restype = ctypes.c_int
+    lib.oracle_pair_features_batch.argtypes = [u8p, i64p, u8p, i64p, i32p, ctypes.c_int64,
+                                               ctypes.c_int, fp]
+    lib.oracle_pair_features_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -253,3 +261,34 @@ def passes(record, matches, columns, lq, lr, min_identity=(3, 10), min_coverage=
     c, d = min_coverage
     return (matches * b >= a * columns and (qe - qs + 1) * d >= c * lq
             and (re_ - rs + 1) * d >= c * lr)
+
+
+N_FEATURES = 32
+
+
+def pair_features(a, b, k=6):
+    """The 32 float32 features of the candidate pair (a, b)."""
+    ac, bc = _codes(a), _codes(b)
+    out = np.zeros(N_FEATURES, np.float32)
+    rc = load().oracle_pair_features(_ptr(ac, ctypes.c_uint8), len(ac), _ptr(bc, ctypes.c_uint8),
+                                     len(bc), k, _ptr(out, ctypes.c_float))
+    if rc:
+        raise ValueError("bad k or out of memory")
+    return out
+
+
+def pair_features_batch(res_a, off_a, res_b, off_b, pairs, k=6):
+    """Features of pairs[p] = (index into set a, index into set b): float32 [P, 32]."""
+    res_a = np.ascontiguousarray(res_a, dtype=np.uint8)
+    res_b = np.ascontiguousarray(res_b, dtype=np.uint8)
+    off_a = np.ascontiguousarray(off_a, dtype=np.int64)
+    off_b = np.ascontiguousarray(off_b, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros((len(pairs), N_FEATURES), np.float32)
+    rc = load().oracle_pair_features_batch(_ptr(res_a, ctypes.c_uint8), _ptr(off_a, ctypes.c_int64),
+                                           _ptr(res_b, ctypes.c_uint8), _ptr(off_b, ctypes.c_int64),
+                                           _ptr(pairs, ctypes.c_int32), len(pairs), k,
+                                           _ptr(out, ctypes.c_float))
+    if rc:
+        raise ValueError("bad k or out of memory")
+    return out

@@ -1,4 +1,4 @@
-"""Compiles the CPU oracle (sw_oracle.c, discovery_oracle.c) into
+"""Compiles the CPU oracle (sw_oracle.c, discovery_oracle.c, filter_oracle.c) into
 oracle/_build/liboracle.so.
 
 Test infrastructure only: the product path never loads this library.
@@ -7,7 +7,8 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, "sw_oracle.c"), os.path.join(HERE, "discovery_oracle.c")]
+SRCS = [os.path.join(HERE, "sw_oracle.c"), os.path.join(HERE, "discovery_oracle.c"),
+        os.path.join(HERE, "filter_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
