@@ -51,6 +51,10 @@ def parse():
                     help="pairs of the batch the tile selection is tuned on")
     ap.add_argument("--tile-overhead", type=int, default=-1,
                     help="fixed tile-cost overhead instead of tuning (profiling runs)")
+    ap.add_argument("--filter-epochs", type=int, default=20,
+                    help="family blocks: training epochs of the learned filter")
+    ap.add_argument("--filter-recall", type=float, default=0.995,
+                    help="family blocks: recall of the training positives the threshold keeps")
     return ap.parse_args()
 
 
@@ -450,10 +454,15 @@ def search_oracle_sample(fs, mat, target_s, seed=5):
 
 
 def run_search(args):
-    """The many-against-many block: discovery + alignment + identity."""
+    """The many-against-many block: discovery + alignment + identity, plain and
+    with the learned filter (trained beforehand, untimed, on a block drawn
+    with another seed)."""
+    import ctypes
+
     import numpy as np
     import torch
 
+    from paper_2303_01845_gb300 import filter as F
     from paper_2303_01845_gb300 import swgb, workload
 
     rank, world, local = dist_env()
@@ -464,89 +473,174 @@ def run_search(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     mat = swgb.swgb_blosum62()
-    fs = workload.generate_families(args.workload, mat)
+    spec = workload.FAMILY_SPECS[args.workload]
     al = swgb.Aligner(local)
     stream = torch.cuda.current_stream(dev)
-    s = al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
     params = swgb.make_params(mat, 11, 1, timing=True)
     th = swgb.make_thresholds()
-    found = swgb.swgb_discover(al.ctx, s.handle, 6, 2, None, stream)[0].shape[0]
-    cap = found
+    lib = swgb.load()
+
+    def load_block(seed):
+        import dataclasses
+        fs = workload.generate_families(dataclasses.replace(spec, seed=seed), mat)
+        return fs, al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
+
+    # ---- training block (untimed): exact labels, features, network, threshold
+    t_train = time.perf_counter()
+    _, s_tr = load_block(spec.seed + 1)
+    cand_tr, _ = al.discover(s_tr, 6, 2)
+    _, ident_tr = F.exact_labels(al, s_tr, cand_tr, params, th)
+    X_tr = swgb.swgb_pair_features(al.ctx, s_tr.handle, s_tr.handle, cand_tr)
+    y_tr = ident_tr[:, 2].to(torch.float32).contiguous()
+    net, losses = F.train(al, X_tr, y_tr, epochs=args.filter_epochs, batch=8192, lr=3e-3, seed=1)
+    threshold = F.calibrate(net, X_tr, y_tr, args.filter_recall)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    n_train, n_train_pos = int(cand_tr.shape[0]), int(y_tr.sum().item())
+    del cand_tr, ident_tr, X_tr, y_tr
+    s_tr.close()
+
+    # ---- the measured block
+    fs, s = load_block(spec.seed)
+    cap = al.discover(s, 6, 2)[0].shape[0]
     cand = torch.empty((cap, 2), dtype=torch.int32, device=dev)
     counts = torch.empty((cap,), dtype=torch.int32, device=dev)
     rec = torch.empty((cap, 5), dtype=torch.int32, device=dev)
     ident = torch.empty((cap, 3), dtype=torch.int32, device=dev)
-    import ctypes
-    lib = swgb.load()
+    feats = torch.empty((cap, 32), dtype=torch.float32, device=dev)
+    logits = torch.empty((cap,), dtype=torch.float32, device=dev)
+    kept = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    kept_index = torch.empty((cap,), dtype=torch.int64, device=dev)
+    rec_k = torch.empty((cap, 5), dtype=torch.int32, device=dev)
+    ident_k = torch.empty((cap, 3), dtype=torch.int32, device=dev)
     n_found = ctypes.c_int64()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    parts = {"discover": [], "align": [], "identity": [], "step": [], "fwd": []}
-    launches = 0
+    n_kept = ctypes.c_int64()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    plain = {"discover": [], "align": [], "identity": [], "step": [], "fwd": []}
+    filt = {"features": [], "network": [], "select": [], "align": [], "identity": [], "step": []}
+    launches = {"plain": 0, "filtered": 0}
 
-    def step(timed):
-        ev[0].record(stream)
+    def discover():
         swgb._check(al.ctx, lib.swgb_discover(al.ctx, s.handle, 6, 2, cand.data_ptr(),
                                               counts.data_ptr(), cap, ctypes.byref(n_found),
                                               stream.cuda_stream))
-        n_launch = lib.swgb_search_launches(al.ctx)
+        return lib.swgb_search_launches(al.ctx)
+
+    def plain_step(timed):
+        ev[0].record(stream)
+        nl = discover()
         ev[1].record(stream)
         swgb.swgb_align(al.ctx, s.handle, s.handle, cand, params, rec, stream)
         ev[2].record(stream)
         swgb.swgb_identity(al.ctx, s.handle, s.handle, cand, rec, params, th, ident, stream)
-        n_launch += lib.swgb_search_launches(al.ctx)
+        nl += lib.swgb_search_launches(al.ctx)
         ev[3].record(stream)
         torch.cuda.synchronize()
         if timed:
-            parts["discover"].append(ev[0].elapsed_time(ev[1]))
-            parts["align"].append(ev[1].elapsed_time(ev[2]))
-            parts["identity"].append(ev[2].elapsed_time(ev[3]))
-            parts["step"].append(ev[0].elapsed_time(ev[3]))
+            plain["discover"].append(ev[0].elapsed_time(ev[1]))
+            plain["align"].append(ev[1].elapsed_time(ev[2]))
+            plain["identity"].append(ev[2].elapsed_time(ev[3]))
+            plain["step"].append(ev[0].elapsed_time(ev[3]))
             st = swgb.swgb_last_stats(al.ctx)
-            parts["fwd"].append(st["forward_ms"])
-            st["search_launches"] = n_launch
+            plain["fwd"].append(st["forward_ms"])
+            launches["plain"] += nl + st["kernel_launches"]
             return st
         return None
 
+    def filtered_step(timed):
+        ev[0].record(stream)
+        nl = discover()
+        ev[1].record(stream)
+        swgb.swgb_pair_features(al.ctx, s.handle, s.handle, cand, 6, feats, stream)
+        nl += lib.swgb_search_launches(al.ctx)
+        ev[2].record(stream)
+        net.forward(feats, logits, stream)
+        ev[3].record(stream)
+        swgb._check(al.ctx, lib.swgb_select_pairs(al.ctx, cand.data_ptr(), logits.data_ptr(), cap,
+                                                  ctypes.c_float(threshold), kept.data_ptr(),
+                                                  kept_index.data_ptr(), ctypes.byref(n_kept),
+                                                  stream.cuda_stream))
+        nl += lib.swgb_search_launches(al.ctx) + 1
+        ev[4].record(stream)
+        k = n_kept.value
+        kp = kept[:k]
+        swgb.swgb_align(al.ctx, s.handle, s.handle, kp, params, rec_k[:k], stream)
+        ev[5].record(stream)
+        swgb.swgb_identity(al.ctx, s.handle, s.handle, kp, rec_k[:k], params, th, ident_k[:k], stream)
+        nl += lib.swgb_search_launches(al.ctx)
+        ev[6].record(stream)
+        torch.cuda.synchronize()
+        if timed:
+            for key, a, b in (("features", 1, 2), ("network", 2, 3), ("select", 3, 4),
+                              ("align", 4, 5), ("identity", 5, 6), ("step", 0, 6)):
+                filt[key].append(ev[a].elapsed_time(ev[b]))
+            filt.setdefault("discover", []).append(ev[0].elapsed_time(ev[1]))
+            launches["filtered"] += nl + swgb.swgb_last_stats(al.ctx)["kernel_launches"]
+
     for _ in range(args.warmup):
-        step(False)
+        plain_step(False)
+        filtered_step(False)
     stats = None
     with ClockSampler(local) as clocks:
         torch.cuda.synchronize()
         for _ in range(args.steps):
-            stats = step(True)
-            launches += stats["search_launches"] + stats["kernel_launches"]
+            stats = plain_step(True)
+            filtered_step(True)
     clock = clocks.summary()
-    total_ms = max_over_ranks(sum(parts["step"]), dist, dev)
     assert n_found.value == cap
-    value = job_rate(cap, world, args.steps, total_ms)
-    ident_np = ident.cpu().numpy()
+    plain_ms = max_over_ranks(sum(plain["step"]), dist, dev)
+    filt_ms = max_over_ranks(sum(filt["step"]), dist, dev)
+    plain_rate = job_rate(cap, world, args.steps, plain_ms)
+    filt_rate = job_rate(cap, world, args.steps, filt_ms)
+    # recall of the filter against the exact pass / fail of every candidate
+    y = ident[:, 2].cpu().numpy() > 0
+    keep = np.zeros(cap, bool)
+    keep[kept_index[:n_kept.value].cpu().numpy()] = True
+    same = bool(np.array_equal(ident_k[:n_kept.value].cpu().numpy(), ident.cpu().numpy()[keep]))
+    recall = float(keep[y].mean()) if y.any() else None
+    cnt = counts.cpu().numpy()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = search_oracle_sample(fs, np.asarray(mat), args.cpu_seconds)
     if rank != 0:
         return
-    mean = lambda k: statistics.mean(parts[k])
+    mean = lambda d, k: statistics.mean(d[k])
     line = {
-        "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32",
-        "data": "synthetic",
+        "metric": METRIC, "value": filt_rate, "unit": "alignments/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": filt_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i16x2+i32 align, bf16 net", "data": "synthetic",
         "config": {"workload": args.workload, "sequences": len(fs), "residues": int(fs.off[-1]),
                    "k": 6, "min_shared": 2, "candidates": cap,
                    "forward_cells": stats["forward_cells"],
-                   "passing_pairs": int(ident_np[:, 2].sum()),
+                   "passing_pairs": int(y.sum()),
                    "thresholds": "identity >= 3/10, coverage >= 7/10",
+                   "value_is": "candidates judged per second by the filtered pipeline "
+                               "(discovery, features, network, selection, exact alignment and "
+                               "identity of the kept pairs)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "discover_ms": mean("discover"), "align_ms": mean("align"),
-        "identity_ms": mean("identity"), "forward_ms": mean("fwd"),
-        "gcups_forward_kernel": stats["forward_cells"] / (mean("fwd") / 1e3) / 1e9,
+        "filter": {"recall": recall, "kept": int(n_kept.value), "kept_fraction": n_kept.value / cap,
+                   "kept_results_exact": same, "threshold": threshold,
+                   "trained_on": "%s seed %d: %d candidates, %d passing; %d epochs, %.1f s "
+                                 "(labels, features, training)" %
+                                 (args.workload, spec.seed + 1, n_train, n_train_pos,
+                                  args.filter_epochs, t_train),
+                   "final_loss": losses[-1],
+                   "kmer_threshold_3": {"recall": float((cnt[y] >= 3).mean()) if y.any() else None,
+                                        "kept_fraction": float((cnt >= 3).mean())},
+                   "speedup_vs_plain": filt_rate / plain_rate,
+                   "ms": {k: mean(filt, k) for k in filt}},
+        "plain": {"alignments_per_s": plain_rate, "ms_per_step": plain_ms / args.steps,
+                  "discover_ms": mean(plain, "discover"), "align_ms": mean(plain, "align"),
+                  "identity_ms": mean(plain, "identity"), "forward_ms": mean(plain, "fwd"),
+                  "gcups_forward_kernel": stats["forward_cells"] / (mean(plain, "fwd") / 1e3) / 1e9},
         "cpu_baseline": None if cpu is None else {
             "value": cpu["aln_per_s"], "unit": "alignments/s", "cores": cpu["cores"],
             "kind": "oracle",
             "sample": "%d random rows (%d candidates j > i): k-mer-set merges against all %d "
                       "sequences, alignment, identity; %.1f s (+ %.1f s k-mer index)" %
                       (cpu["rows"], cpu["pairs"], len(fs), cpu["seconds"], cpu["index_s"])},
-        "gpu_launches": launches,
+        "gpu_launches": launches["filtered"],
         "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                    "reasons": clock["reasons"]},
     }

@@ -57,7 +57,8 @@ extern "C" {
 #define SWGB_ENOMEM (-4)  /* a device or host allocation failed */
 #define SWGB_ECUDA (-5)   /* a CUDA runtime call failed (message in swgb_last_error) */
 #define SWGB_EINTERNAL (-6) /* the device detected an inconsistency in its own results */
-#define SWGB_ETOOBIG (-7) /* a size exceeds a fixed limit (swgb_align_noalloc, swgb_discover) */
+#define SWGB_ETOOBIG (-7) /* a size exceeds a fixed limit (swgb_align_noalloc, swgb_discover, server) */
+#define SWGB_ETIMEDOUT (-8) /* swgb_server_wait: the request did not finish in time */
 
 #define SWGB_ALPHABET_SIZE 24
 /* Longest sequence accepted (residues). */
@@ -73,6 +74,7 @@ extern "C" {
 
 typedef struct swgb_ctx swgb_ctx;
 typedef struct swgb_seqset swgb_seqset;
+typedef struct swgb_server swgb_server;
 
 /* One alignment result, 20 bytes. */
 typedef struct {
@@ -294,9 +296,188 @@ int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* 
                   const swgb_params* params, const swgb_thresholds* thresholds,
                   swgb_identity_record* out, void* stream);
 
-/* Kernels launched by the last swgb_discover or swgb_identity call on ctx
- * (-1 for a NULL context). */
+/* Kernels launched by the last swgb_discover, swgb_identity,
+ * swgb_pair_features, swgb_select_pairs or swgb_mlp_train call on ctx (-1 for
+ * a NULL context). */
 int swgb_search_launches(const swgb_ctx* ctx);
+
+/* ---- resident k-mer index of a reference set ----
+ * For the search of query sets against a fixed reference set (the paper's
+ * problem statement allows two distinct sets, Sec. "Overview of the
+ * Problem"): the references' distinct k-mers and their buckets (the columns
+ * of the sequence-by-k-mer matrix, with first positions) stay in device
+ * memory, so a query batch costs only its own k-mer sets and the join. */
+typedef struct swgb_index swgb_index;
+
+/* Builds the index of `refs` (which must outlive it) on ctx's device with k
+ * in 1..6; about 17 bytes per reference residue + 4 (20^k + 1) bytes.
+ * Synchronous on `stream`.  Errors: EINVAL, ETOOBIG, ENOMEM, ECUDA. */
+int swgb_index_create(swgb_ctx* ctx, const swgb_seqset* refs, int k, void* stream,
+                      swgb_index** out);
+void swgb_index_destroy(swgb_index* index);
+/* Reference count, k and device bytes held. */
+int swgb_index_info(const swgb_index* index, int64_t* n_refs, int* k, int64_t* bytes);
+
+/* Candidates of a query set against the index: every (query i, reference j)
+ * with |K(q_i) intersect K(r_j)| >= min_shared (same K as swgb_discover),
+ * ordered by (i, j), into DEVICE pairs [capacity][2] (and DEVICE counts
+ * [capacity] or NULL); *n_found = their number (may exceed capacity).
+ * Synchronous on `stream`.  Errors: as swgb_discover. */
+int swgb_index_query(swgb_ctx* ctx, const swgb_index* index, const swgb_seqset* queries,
+                     int min_shared, int32_t* pairs, int32_t* counts, int64_t capacity,
+                     int64_t* n_found, void* stream);
+
+/* swgb_pair_features for pairs (query i, reference j) of swgb_index_query,
+ * using the index's tables for the references.  Synchronous on `stream`. */
+int swgb_index_features(swgb_ctx* ctx, const swgb_index* index, const swgb_seqset* queries,
+                        const int32_t* pairs, int64_t n_pairs, float* features, void* stream);
+
+/* ---- the learned candidate filter ----
+ * The paper keeps every candidate with at least two shared k-mers and notes
+ * that few of them end in the similarity graph (Sec. "Blocked 2D Sparse
+ * SUMMA"); the filter scores candidates from k-mer features with a small
+ * network trained on the exact aligner's pass/fail labels, so that pairs it
+ * predicts to fail are not aligned.  The paper has no such network: it is
+ * this library's, defined below.
+ *
+ * Pair features (32 floats per pair (i of set A, j of set B)).  K(s) = the
+ * distinct k-mers of standard letters of s with their FIRST start positions
+ * p_s(x); for the c shared k-mers x: diagonal d(x) = p_i(x) - p_j(x),
+ * D = li + lj - 2k + 1, bin(x) = floor(24 (d(x) + lj - k) / D), hist[0..23];
+ * n_s(y) = occurrences of standard letter y.  Each feature is an integer
+ * ratio num / den evaluated as the double quotient rounded to float (0 when
+ * den = 0):
+ *   0: c / (c + 16)            1: min(li, lj) / max(li, lj)
+ *   2..25: hist[t] / c          26: sum_y |n_i(y) lj - n_j(y) li| / (2 li lj)
+ *   27: li / (li + 256)         28: lj / (lj + 256)
+ *   29: max_t hist[t] / c       30: c / min(|K(i)|, |K(j)|)
+ *   31: (max d - min d) / D when c >= 2, else 0. */
+int swgb_pair_features(swgb_ctx* ctx, const swgb_seqset* set_a, const swgb_seqset* set_b,
+                       const int32_t* pairs, int64_t n_pairs, int k, float* features,
+                       void* stream);
+/* pairs: DEVICE int32 [n_pairs][2]; features: DEVICE float [n_pairs][32].
+ * Pairs sorted by their first index share work (swgb_discover's order).
+ * Synchronous on `stream`; may grow the context's scratch.
+ * Errors: EINVAL, ERANGE (an index outside its set), ENOMEM, ECUDA. */
+
+/* Network: 32 -> 64 -> 128 -> 1, ReLU, bfloat16 weights and activations,
+ * float32 accumulation (x = bf16(features); a1 = bf16(relu(x W1 + b1));
+ * a2 = bf16(relu(a1 W2 + b2)); logit = a2 . w3 + b3, with W1, W2 used as
+ * their bfloat16 copies).  Parameters are float32, packed as W1 [32][64]
+ * (row = input), b1 [64], W2 [64][128], b2 [128], w3 [128], b3 [1].
+ * Training minimises the weighted mean binary cross-entropy of the logits
+ * (weight pos_weight on label 1) with Adam (beta 0.9 / 0.999, eps 1e-8);
+ * the gradient rounds dz2 = g3 w3 [z2 > 0] and dz1 = dz2 W2^T [z1 > 0] to
+ * bfloat16 before their products. */
+#define SWGB_MLP_PARAMS 10561
+#define SWGB_FEATURES 32
+typedef struct swgb_mlp swgb_mlp;
+
+/* Creates a network on ctx's device with HOST parameters init[SWGB_MLP_PARAMS]
+ * (the caller draws the initial values).  Errors: EINVAL, ENOMEM, ECUDA. */
+int swgb_mlp_create(swgb_ctx* ctx, const float* init, swgb_mlp** out);
+void swgb_mlp_destroy(swgb_mlp* mlp);
+/* Replaces the parameters (HOST array) and resets the optimiser state. */
+int swgb_mlp_set(swgb_mlp* mlp, const float* params);
+/* Copies the parameters to HOST params[SWGB_MLP_PARAMS] (waits for the device). */
+int swgb_mlp_get(swgb_mlp* mlp, float* params);
+/* logits[p] for DEVICE features [n][32] into DEVICE logits [n]; asynchronous. */
+int swgb_mlp_forward(swgb_mlp* mlp, const float* features, int64_t n, float* logits, void* stream);
+/* Gradient of the loss over the DEVICE batch (features [n][32], labels [n]
+ * of 0 / 1) into DEVICE grad [SWGB_MLP_PARAMS] and DEVICE loss [1], without
+ * changing the parameters; asynchronous. */
+int swgb_mlp_grad(swgb_mlp* mlp, const float* features, const float* labels, int64_t n,
+                  float pos_weight, float* grad, float* loss, void* stream);
+/* One pass over n samples in minibatches of `batch`: sample order[r] (a
+ * DEVICE int32 permutation chosen by the caller, or NULL for 0..n-1) at
+ * position r; an Adam step of learning rate lr per minibatch.  *mean_loss
+ * (may be NULL) receives the mean of the minibatch losses.  Synchronous. */
+int swgb_mlp_train(swgb_mlp* mlp, const float* features, const float* labels,
+                   const int32_t* order, int64_t n, int64_t batch, float lr, float pos_weight,
+                   float* mean_loss, void* stream);
+
+/* Keeps the pairs whose logit is >= threshold, in order: kept (DEVICE int32
+ * [n_pairs][2]) receives them, kept_index (DEVICE int64 [n_pairs], or NULL)
+ * their positions in `pairs`, *n_kept their number.  Synchronous. */
+int swgb_select_pairs(swgb_ctx* ctx, const int32_t* pairs, const float* logits, int64_t n_pairs,
+                      float threshold, int32_t* kept, int64_t* kept_index, int64_t* n_kept,
+                      void* stream);
+
+/* ---- serving: a query server over a resident reference set ----
+ * The paper runs one batch job; this server answers a stream of requests
+ * (batches of query sequences) against references kept on the device.  Each
+ * request goes through the whole search: candidates from the resident
+ * k-mer index (swgb_index_query), optionally the learned filter
+ * (swgb_index_features, the network, swgb_select_pairs), exact alignment
+ * (swgb_align) and identity / pass-fail (swgb_identity).
+ *
+ * Scheduling: `slots` worker threads, each with its own context and CUDA
+ * stream.  A free worker admits the longest FIFO prefix of the waiting
+ * requests that fits one batch (max_batch_queries, max_batch_residues) and
+ * the device-memory budget (the reservations of the requests in flight,
+ * reservation = 24 bytes per residue + candidates_per_query x 172 bytes per
+ * query, stay within max_inflight_bytes; the blocked formation of the
+ * overlap matrix bounds memory the same way, Sec. "Blocked 2D Sparse
+ * SUMMA"), and runs it; the batches of different workers overlap on the
+ * GPU.  Requests that arrive while others run are admitted as workers and
+ * memory free up.  A request's results do not depend on the batch it joins
+ * or on what runs beside it: every pair's computation is independent. */
+typedef struct {
+    int32_t slots;                 /* worker slots (batches in flight), 1..64 */
+    int32_t max_batch_queries;     /* queries of one batch */
+    int64_t max_batch_residues;    /* query residues of one batch */
+    int64_t max_inflight_bytes;    /* budget of the in-flight reservations */
+    int32_t candidates_per_query;  /* reservation model (see above) */
+    int32_t min_shared;            /* common k-mers of a candidate */
+    float threshold;               /* logit threshold of the filter */
+    swgb_thresholds identity;      /* pass / fail thresholds */
+} swgb_server_config;
+
+/* The results of one request (valid until swgb_server_release). */
+typedef struct {
+    int32_t status;                /* SWGB_OK or the failing call's code */
+    int64_t n_pairs;               /* pairs aligned (kept by the filter) */
+    int64_t n_candidates;          /* candidates before the filter */
+    const int32_t* pairs;          /* [n_pairs][2]: (query index in the request, reference index), ordered */
+    const int32_t* counts;         /* [n_pairs] common k-mers */
+    const swgb_record* records;    /* [n_pairs] */
+    const swgb_identity_record* identity;   /* [n_pairs] */
+    double queue_ms;               /* submission to admission */
+    double latency_ms;             /* submission to completion */
+    int64_t batch_id;              /* the batch the request ran in */
+    int32_t slot;                  /* the worker that ran it */
+} swgb_server_result;
+
+/* Defaults: 3 slots, 4096 queries / 2^20 residues per batch, 4 GiB budget,
+ * 256 candidates per query, min_shared 2, threshold 0, identity 3/10 and
+ * coverage 7/10. */
+void swgb_server_default_config(swgb_server_config* cfg);
+
+/* Starts a server on CUDA device `device` over `refs` and its `index` (both
+ * must outlive the server).  mlp_params: HOST float [SWGB_MLP_PARAMS] of a
+ * trained network (copied), or NULL for no filter.  params->matrix is
+ * copied.  Errors: EINVAL. */
+int swgb_server_create(int device, const swgb_seqset* refs, const swgb_index* index,
+                       const float* mlp_params, const swgb_params* params,
+                       const swgb_server_config* cfg, swgb_server** out);
+/* Stops the workers after the batches in flight and frees the server. */
+void swgb_server_destroy(swgb_server* server);
+
+/* Queues a request of n_queries HOST sequences (codes 0..23, offsets
+ * n_queries + 1 entries; the data are copied) and returns its ticket.
+ * Errors: EINVAL, ERANGE (decreasing offsets), EBADRES, ETOOBIG (larger than
+ * one batch or than the whole budget). */
+int swgb_server_submit(swgb_server* server, const uint8_t* codes, const int64_t* offsets,
+                       int64_t n_queries, int64_t* ticket);
+/* Waits up to timeout_ms (< 0: forever) for a request; fills *out.
+ * Errors: EINVAL (unknown ticket), ETIMEDOUT. */
+int swgb_server_wait(swgb_server* server, int64_t ticket, int64_t timeout_ms,
+                     swgb_server_result* out);
+/* Frees a finished request's results.  Errors: EINVAL. */
+int swgb_server_release(swgb_server* server, int64_t ticket);
+/* Most batches seen in flight at once, requests waiting, bytes reserved. */
+int swgb_server_stats(swgb_server* server, int32_t* max_overlap, int64_t* pending,
+                      int64_t* inflight_bytes);
 
 /* ---- allocation-free variant ----
  * The paper has no counterpart of this call; it exists for callers that

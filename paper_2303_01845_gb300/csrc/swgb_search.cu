@@ -268,12 +268,14 @@ __global__ void __launch_bounds__(kScanT) scan_apply_kernel(const uint32_t* __re
 // 3. per-row partner bound and row class
 // ---------------------------------------------------------------------------
 struct JoinArgs {
-    SeqView s;
+    SeqView s;                 // the rows' set (offsets of their k-mer entries)
     const uint32_t* ent_kmer;
     const uint32_t* kcount;
-    const uint32_t* start;     // bucket starts [V + 1]
+    const uint32_t* start;     // bucket starts [V + 1] of the columns' set
     const int32_t* bseq;
-    uint32_t* need;            // [n] min(incidences with j > i, n - 1 - i)
+    int64_t n_cols;            // sequences of the columns' set
+    int self_pairs;            // rows and columns are one set: only j > i
+    uint32_t* need;            // [n] min(partner incidences, possible partners)
     uint32_t* ccount;          // [n] candidates of row i (counting pass)
     const uint64_t* coff;      // [n + 1] scan of ccount (writing pass)
     int32_t* out_pairs;        // caller's [capacity][2]
@@ -299,11 +301,15 @@ __global__ void row_need_kernel(JoinArgs a) {
         uint64_t inc = 0;
         for (uint32_t e = lane; e < c; e += 32) {
             const uint32_t x = a.ent_kmer[o + e];
-            for (uint32_t b = a.start[x]; b < a.start[x + 1]; ++b) inc += a.bseq[b] > i;
+            if (a.self_pairs) {
+                for (uint32_t b = a.start[x]; b < a.start[x + 1]; ++b) inc += a.bseq[b] > i;
+            } else {
+                inc += a.start[x + 1] - a.start[x];
+            }
         }
         for (int d = 16; d; d >>= 1) inc += __shfl_xor_sync(0xffffffffu, inc, d);
         if (lane == 0) {
-            const uint64_t lim = (uint64_t)(n - 1 - i);
+            const uint64_t lim = (uint64_t)(a.self_pairs ? a.n_cols - 1 - i : a.n_cols);
             const uint32_t need = (uint32_t)(inc < lim ? inc : lim);
             a.need[i] = inc < (uint64_t)a.min_shared ? 0u : need;
             if (inc >= (uint64_t)a.min_shared) {
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
             const uint32_t b1 = a.start[x + 1];
             for (uint32_t b = a.start[x]; b < b1; ++b) {
                 const int32_t j = a.bseq[b];
-                if (j <= i) continue;
+                if (a.self_pairs && j <= i) continue;
                 uint32_t h = slot_of((uint32_t)j, mask);
                 for (uint32_t probe = 0; probe < cap; ++probe) {
                     const uint32_t cur = atomicCAS(&keys[h], kEmpty, (uint32_t)j);
@@ -667,6 +673,198 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Pair features of the learned candidate filter
+// ---------------------------------------------------------------------------
+// For a pair (i of set A, j of set B), with K(s) the distinct k-mers of
+// standard letters of s and p_s(x) their first positions (kmer_sets), the
+// shared k-mers x give diagonals d = p_i(x) - p_j(x) and 24 bins
+// floor(24 (d + lj - k) / D), D = li + lj - 2k + 1.  The 32 features are
+// integer ratios num / den rounded through double to float (0 for den = 0):
+//   0 c/(c+16), 1 min(l)/max(l), 2..25 hist[t]/c,
+//   26 sum_y |nA(y) lj - nB(y) li| / (2 li lj), 27 li/(li+256), 28 lj/(lj+256),
+//   29 max_t hist[t]/c, 30 c/min(|K(i)|, |K(j)|), 31 (max d - min d)/D (c >= 2).
+constexpr int kFeat = 32;
+constexpr int kFeatBins = 24;
+constexpr int kFeatWarps = 8;
+constexpr int kFeatSlots = 4096;     // shared-memory table of K(i): up to 2048 k-mers
+constexpr int kFeatChunk = 64;       // consecutive pairs per task
+
+struct FeatArgs {
+    SeqView A, B;
+    int k;
+    const uint32_t *kmA, *posA, *cntA;     // kmer_sets of A
+    const uint32_t *kmB, *posB, *cntB;     // kmer_sets of B
+    const uint32_t *compA, *compB;         // [n][20] letter counts
+    const int32_t* pairs;
+    int64_t n_pairs;
+    float* out;                            // [n_pairs][32]
+    uint32_t* gtab;                        // per-block global tables (keys, positions)
+    uint32_t gslots;
+    unsigned long long* ctr;
+    int32_t* status;
+};
+
+__global__ void composition_kernel(SeqView s, uint32_t* comp) {
+    __shared__ uint32_t cnt[8][kStdLetters];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < s.n; i += warps) {
+        if (lane < kStdLetters) cnt[w][lane] = 0;
+        __syncwarp();
+        for (int64_t p = s.off[i] + lane; p < s.off[i + 1]; p += 32) {
+            const uint32_t c = s.res[p];
+            if (c < (uint32_t)kStdLetters) atomicAdd(&cnt[w][c], 1u);
+        }
+        __syncwarp();
+        if (lane < kStdLetters) comp[i * kStdLetters + lane] = cnt[w][lane];
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ float feat_ratio(int64_t num, int64_t den) {
+    return den == 0 ? 0.0f : __double2float_rn((double)num / (double)den);
+}
+
+__global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
+    __shared__ uint32_t s_keys[kFeatSlots];
+    __shared__ uint32_t s_pos[kFeatSlots];
+    __shared__ uint32_t s_hist[kFeatWarps][kFeatBins];
+    __shared__ int64_t s_task;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        const int64_t t0 = next_task(a.ctr, &s_task) * kFeatChunk;
+        if (t0 >= a.n_pairs) break;
+        const int64_t t1 = min(t0 + (int64_t)kFeatChunk, a.n_pairs);
+        int64_t p0 = t0;
+        while (p0 < t1) {
+            const int32_t i = a.pairs[2 * p0];
+            int64_t p1 = p0 + 1;
+            while (p1 < t1 && a.pairs[2 * p1] == i) ++p1;
+            const bool ok_i = i >= 0 && i < a.A.n;
+            const uint32_t ni = ok_i ? a.cntA[i] : 0u;
+            const uint32_t cap = pow2_at_least(2ull * ni);
+            uint32_t* keys = s_keys;
+            uint32_t* pos = s_pos;
+            bool table_ok = true;
+            if (cap > (uint32_t)kFeatSlots) {
+                if (cap > a.gslots) {
+                    table_ok = false;
+                } else {
+                    keys = a.gtab + (size_t)blockIdx.x * 2 * a.gslots;
+                    pos = keys + a.gslots;
+                }
+            }
+            const uint32_t mask = cap - 1;
+            if (table_ok) {
+                for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) keys[s] = kEmpty;
+                __syncthreads();
+                const int64_t oi = ok_i ? a.A.off[i] : 0;
+                for (uint32_t e = threadIdx.x; e < ni; e += blockDim.x) {
+                    const uint32_t x = a.kmA[oi + e];
+                    uint32_t h = slot_of(x, mask);
+                    for (uint32_t probe = 0; probe < cap; ++probe) {
+                        if (atomicCAS(&keys[h], kEmpty, x) == kEmpty) {
+                            pos[h] = a.posA[oi + e];
+                            break;
+                        }
+                        h = (h + 1) & mask;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int64_t p = p0 + w; p < p1; p += kFeatWarps) {
+                const int32_t j = a.pairs[2 * p + 1];
+                float* o = a.out + p * kFeat;
+                if (!ok_i || j < 0 || j >= a.B.n || !table_ok) {
+                    if (lane == 0) atomicMax(a.status, ok_i && j >= 0 && j < a.B.n ? 2 : 3);
+                    o[lane] = 0.0f;
+                    continue;
+                }
+                const int64_t li = a.A.off[i + 1] - a.A.off[i], lj = a.B.off[j + 1] - a.B.off[j];
+                const uint32_t nj = a.cntB[j];
+                const int64_t oj = a.B.off[j];
+                const int64_t D = li + lj - 2 * (int64_t)a.k + 1;
+                if (lane < kFeatBins) s_hist[w][lane] = 0;
+                __syncwarp();
+                int c = 0;
+                int64_t dmin = INT64_MAX, dmax = INT64_MIN;
+                for (uint32_t e = lane; e < nj; e += 32) {
+                    const uint32_t x = a.kmB[oj + e];
+                    uint32_t h = slot_of(x, mask);
+                    for (uint32_t probe = 0; probe < cap; ++probe) {
+                        const uint32_t key = keys[h];
+                        if (key == x) {
+                            const int64_t d = (int64_t)pos[h] - (int64_t)a.posB[oj + e];
+                            atomicAdd(&s_hist[w][(kFeatBins * (d + lj - a.k)) / D], 1u);
+                            ++c;
+                            dmin = min(dmin, d);
+                            dmax = max(dmax, d);
+                            break;
+                        }
+                        if (key == kEmpty) break;
+                        h = (h + 1) & mask;
+                    }
+                }
+                for (int s = 16; s; s >>= 1) {
+                    c += __shfl_xor_sync(0xffffffffu, c, s);
+                    dmin = min(dmin, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)dmin, s));
+                    dmax = max(dmax, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)dmax, s));
+                }
+                __syncwarp();
+                const uint32_t hmax =
+                    __reduce_max_sync(0xffffffffu, lane < kFeatBins ? s_hist[w][lane] : 0u);
+                // lanes 2..25 produce the histogram features
+                const uint32_t hv = (lane >= 2 && lane < 2 + kFeatBins) ? s_hist[w][lane - 2] : 0u;
+                int64_t cd = 0;
+                if (lane < kStdLetters) {
+                    const int64_t v = (int64_t)a.compA[(int64_t)i * kStdLetters + lane] * lj -
+                                      (int64_t)a.compB[(int64_t)j * kStdLetters + lane] * li;
+                    cd = v < 0 ? -v : v;
+                }
+                for (int s = 16; s; s >>= 1) cd += __shfl_xor_sync(0xffffffffu, (long long)cd, s);
+                float f;
+                if (lane == 0) f = feat_ratio(c, c + 16);
+                else if (lane == 1) f = feat_ratio(min(li, lj), max(li, lj));
+                else if (lane < 2 + kFeatBins) f = feat_ratio(hv, c);
+                else if (lane == 26) f = feat_ratio(cd, 2 * li * lj);
+                else if (lane == 27) f = feat_ratio(li, li + 256);
+                else if (lane == 28) f = feat_ratio(lj, lj + 256);
+                else if (lane == 29) f = feat_ratio(hmax, c);
+                else if (lane == 30) f = feat_ratio(c, min(ni, nj));
+                else f = c >= 2 ? feat_ratio(dmax - dmin, D) : 0.0f;
+                o[lane] = f;
+                __syncwarp();
+            }
+            __syncthreads();
+            p0 = p1;
+        }
+    }
+}
+
+// kept[p] = 1 when logit[p] >= threshold
+__global__ void select_flags_kernel(const float* __restrict__ logits, int64_t n, float threshold,
+                                    uint32_t* flags) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        flags[p] = logits[p] >= threshold ? 1u : 0u;
+}
+
+__global__ void select_scatter_kernel(const int32_t* __restrict__ pairs, const uint32_t* __restrict__ flags,
+                                      const uint64_t* __restrict__ pos, int64_t n, int32_t* out,
+                                      int64_t* index_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        if (flags[p]) {
+            const uint64_t d = pos[p];
+            out[2 * d] = pairs[2 * p];
+            out[2 * d + 1] = pairs[2 * p + 1];
+            if (index_out) index_out[d] = p;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace swgb
 
@@ -691,6 +889,13 @@ struct SearchStore {
     int2* bnd = nullptr;          int64_t bnd_cap = 0;
     int64_t* large = nullptr;     int64_t large_cap = 0;
     int32_t* large_rows = nullptr; int64_t large_rows_cap = 0;
+    // pair features: k-mer sets of a second set, letter counts of both
+    uint32_t* ent2_kmer = nullptr; int64_t ent2_cap = 0;
+    uint32_t* ent2_pos = nullptr;  int64_t ent2p_cap = 0;
+    uint32_t* kcount2 = nullptr;   int64_t kcount2_cap = 0;
+    uint32_t* comp = nullptr;      int64_t comp_cap = 0;
+    uint32_t* comp2 = nullptr;     int64_t comp2_cap = 0;
+    uint32_t* flags = nullptr;     int64_t flags_cap = 0;
     unsigned long long* ctr = nullptr;   // [8] work counters and statistics
     int32_t* status = nullptr;
 };
@@ -700,7 +905,8 @@ void search_store_free(SearchStore* s) {
     cudaSetDevice(s->device);
     void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq, s->bpos,
                     s->need, s->ccount, s->coff, s->part, s->gtab, s->dir, s->bnd, s->ctr,
-                    s->status, s->large, s->large_rows};
+                    s->status, s->large, s->large_rows, s->ent2_kmer, s->ent2_pos, s->kcount2,
+                    s->comp, s->comp2, s->flags};
     for (void* p : ptrs) cudaFree(p);
     delete s;
 }
@@ -750,71 +956,86 @@ int64_t warp_grid(swgb_ctx* ctx, int64_t items, int threads) {
 
 }  // namespace
 
-SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int min_shared,
-                              int32_t* pairs, int32_t* counts, int64_t capacity, int64_t* n_found,
-                              void* stream) {
-    if (!ctx) return SWGB_EINVAL;
-    if (!set || !n_found) return fail(ctx, SWGB_EINVAL, "discover: set or n_found is NULL");
-    *n_found = 0;
-    if (k < 1 || k > 6) return fail(ctx, SWGB_EINVAL, "discover: k must be 1..6");
-    if (min_shared < 1) return fail(ctx, SWGB_EINVAL, "discover: min_shared must be >= 1");
-    if (capacity < 0 || (capacity > 0 && !pairs))
-        return fail(ctx, SWGB_EINVAL, "discover: negative capacity or pairs is NULL");
-    if (set->device != ctx->device) return fail(ctx, SWGB_EINVAL, "discover: set on another device");
-    if (set->total >= (int64_t)UINT32_MAX)
-        return fail(ctx, SWGB_ETOOBIG, "discover: more than 2^32-1 residues in the set");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = set->n;
-    if (n < 2) return SWGB_OK;
-    SearchStore* S = nullptr;
-    int rc = search_store(ctx, &S);
-    if (rc) return rc;
+namespace {
+
+int64_t kmer_space(int k) {
     int64_t V = 1;
     for (int t = 0; t < k; ++t) V *= kStdLetters;
-    const int64_t total = std::max<int64_t>(set->total, 1);
-    CK(grow(&S->ent_kmer, &S->ent_cap, total), "discover scratch");
-    CK(grow(&S->ent_pos, &S->entp_cap, total), "discover scratch");
-    CK(grow(&S->bseq, &S->bseq_cap, total), "discover scratch");
-    CK(grow(&S->bpos, &S->bpos_cap, total), "discover scratch");
-    CK(grow(&S->kcount, &S->kcount_cap, n), "discover scratch");
-    CK(grow(&S->need, &S->need_cap, n), "discover scratch");
-    CK(grow(&S->ccount, &S->ccount_cap, n), "discover scratch");
-    CK(grow(&S->coff, &S->coff_cap, n + 1), "discover scratch");
-    CK(grow(&S->hist, &S->hist_cap, V), "discover scratch");
-    CK(grow(&S->start, &S->start_cap, V + 1), "discover scratch");
+    return V;
+}
 
-    const int set_blocks = ctx->sm_count * 4;
-    const uint32_t set_gslots = pow2_at_least((uint64_t)std::max<int64_t>(set->max_len, 1) * 2);
-    if (set_gslots > (uint32_t)kSetSmemSlots)
-        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)set_blocks * 2 * set_gslots), "discover scratch");
+// Global hash tables of sequences above the shared-memory class, for
+// kmer_sets launches over a set of longest length max_len (reserved before
+// any launch that may still run; grow() frees the old buffer).
+int reserve_set_tables(swgb_ctx* ctx, SearchStore* S, int64_t max_len, uint32_t* gslots) {
+    *gslots = pow2_at_least((uint64_t)std::max<int64_t>(max_len, 1) * 2);
+    if (*gslots > (uint32_t)kSetSmemSlots)
+        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)ctx->sm_count * 4 * 2 * *gslots), "k-mer table scratch");
+    return SWGB_OK;
+}
 
-    ctx->last_search_launches = 0;
-    int32_t launches = 0;
-    CK(cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * 8, st), "memset");
-    CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
-    SetArgs sa{view(set), k, S->ent_kmer, S->ent_pos, S->kcount, S->gtab, set_gslots, S->ctr + 0,
-               S->status};
-    kmer_sets_kernel<<<set_blocks, kSearchThreads, 0, st>>>(sa);
+// Distinct k-mers (with first positions) of every sequence of `set` into
+// kmer / pos at the set's offsets, their numbers into cnt.
+int build_sets(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set, int k, uint32_t* kmer,
+               uint32_t* pos, uint32_t* cnt, uint32_t gslots, int32_t* launches, cudaStream_t st) {
+    if (set->n == 0) return SWGB_OK;
+    CK(cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long), st), "memset");
+    SetArgs sa{view(set), k, kmer, pos, cnt, S->gtab, gslots, S->ctr, S->status};
+    kmer_sets_kernel<<<ctx->sm_count * 4, kSearchThreads, 0, st>>>(sa);
     CK(cudaGetLastError(), "kmer_sets kernel");
-    CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
-    const int64_t wg = warp_grid(ctx, n, 256);
-    kmer_hist_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), S->ent_kmer, S->kcount, S->hist);
-    CK(cudaGetLastError(), "kmer_hist kernel");
-    rc = device_scan<uint32_t>(ctx, S, S->hist, V, S->start, st);
-    if (rc) return rc;
-    CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
-    kmer_scatter_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), S->ent_kmer, S->ent_pos, S->kcount,
-                                                      S->start, S->hist, S->bseq, S->bpos);
-    CK(cudaGetLastError(), "kmer_scatter kernel");
-    launches += 3 + 3;   // sets, histogram, scatter + the scan
+    *launches += 1;
+    return SWGB_OK;
+}
 
+// Buckets of the distinct k-mers of `set` (the columns of the sequence x
+// k-mer matrix): start [V + 1], and per entry its sequence and position.
+int build_buckets(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set, const uint32_t* kmer,
+                  const uint32_t* pos, const uint32_t* cnt, int64_t V, uint32_t* start,
+                  int32_t* bseq, uint32_t* bpos, int32_t* launches, cudaStream_t st) {
+    CK(grow(&S->hist, &S->hist_cap, V), "bucket scratch");
+    CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
+    const int64_t wg = warp_grid(ctx, std::max<int64_t>(set->n, 1), 256);
+    if (set->n > 0) {
+        kmer_hist_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), kmer, cnt, S->hist);
+        CK(cudaGetLastError(), "kmer_hist kernel");
+        *launches += 1;
+    }
+    int rc = device_scan<uint32_t>(ctx, S, S->hist, V, start, st);
+    if (rc) return rc;
+    *launches += 3;
+    CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
+    if (set->n > 0) {
+        kmer_scatter_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), kmer, pos, cnt, start, S->hist,
+                                                          bseq, bpos);
+        CK(cudaGetLastError(), "kmer_scatter kernel");
+        *launches += 1;
+    }
+    return SWGB_OK;
+}
+
+// The join of the rows' k-mer sets with the columns' buckets: pairs (row i,
+// column j) with >= min_shared common k-mers (j > i for one set), ordered by
+// (i, j); *found receives their number, the first `capacity` are written.
+int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint32_t* kmer,
+              const uint32_t* cnt, const uint32_t* start, const int32_t* bseq, int64_t n_cols,
+              bool self_pairs, int min_shared, int32_t* pairs, int32_t* counts, int64_t capacity,
+              int64_t* found, int32_t* launches, cudaStream_t st) {
+    const int64_t n = rows->n;
+    *found = 0;
+    if (n == 0) return SWGB_OK;
+    CK(grow(&S->need, &S->need_cap, n), "join scratch");
+    CK(grow(&S->ccount, &S->ccount_cap, n), "join scratch");
+    CK(grow(&S->coff, &S->coff_cap, n + 1), "join scratch");
+    CK(grow(&S->large_rows, &S->large_rows_cap, n), "join scratch");
+    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 7, st), "memset");
     JoinArgs ja{};
-    ja.s = view(set);
-    ja.ent_kmer = S->ent_kmer;
-    ja.kcount = S->kcount;
-    ja.start = S->start;
-    ja.bseq = S->bseq;
+    ja.s = view(rows);
+    ja.ent_kmer = kmer;
+    ja.kcount = cnt;
+    ja.start = start;
+    ja.bseq = bseq;
+    ja.n_cols = n_cols;
+    ja.self_pairs = self_pairs ? 1 : 0;
     ja.need = S->need;
     ja.ccount = S->ccount;
     ja.coff = S->coff;
@@ -824,12 +1045,12 @@ SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int 
     ja.min_shared = min_shared;
     ja.stats = S->ctr + 4;
     ja.status = S->status;
-    CK(grow(&S->large_rows, &S->large_rows_cap, n), "discover scratch");
     ja.large_rows = S->large_rows;
     ja.n_tasks = n;
+    const int64_t wg = warp_grid(ctx, n, 256);
     row_need_kernel<<<(unsigned)wg, 256, 0, st>>>(ja);
     CK(cudaGetLastError(), "row_need kernel");
-    launches += 1;
+    *launches += 1;
     unsigned long long stats[2] = {0, 0};
     CK(cudaMemcpyAsync(stats, S->ctr + 4, sizeof(stats), cudaMemcpyDeviceToHost, st), "stats D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
@@ -842,47 +1063,232 @@ SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int 
         const int64_t budget = (int64_t)1 << 29;       // 2 GiB of words
         large_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(
             std::min<int64_t>((int64_t)n_large, (int64_t)ctx->sm_count * 2), budget / per_block));
-        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)large_blocks * per_block), "discover scratch");
+        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)large_blocks * per_block), "join scratch");
     }
     ja.gtab = S->gtab;
     ja.gslots = join_gslots;
     const int join_blocks = ctx->sm_count * 4;
     for (int pass = 0; pass < 2; ++pass) {
         ja.ctr = S->ctr + 1 + pass;
-        unsigned long long* lctr = S->ctr + 6 + pass;
+        JoinArgs jl = ja;
+        jl.ctr = S->ctr + 6 + pass;
+        jl.n_tasks = (int64_t)n_large;
         if (pass == 0) {
             join_kernel<false, false><<<join_blocks, kSearchThreads, kJoinSmemBytes, st>>>(ja);
-            if (large_blocks) {
-                JoinArgs jl = ja;
-                jl.ctr = lctr;
-                jl.n_tasks = (int64_t)n_large;
-                join_kernel<true, false><<<large_blocks, kSearchThreads, 0, st>>>(jl);
-            }
+            if (large_blocks) join_kernel<true, false><<<large_blocks, kSearchThreads, 0, st>>>(jl);
             CK(cudaGetLastError(), "join kernel (count)");
-            launches += (large_blocks ? 2 : 1) + 3;
-            rc = device_scan<uint64_t>(ctx, S, S->ccount, n, S->coff, st);
+            *launches += (large_blocks ? 2 : 1) + 3;
+            int rc = device_scan<uint64_t>(ctx, S, S->ccount, n, S->coff, st);
             if (rc) return rc;
         } else {
             join_kernel<false, true><<<join_blocks, kSearchThreads, kJoinSmemBytes, st>>>(ja);
-            if (large_blocks) {
-                JoinArgs jl = ja;
-                jl.ctr = lctr;
-                jl.n_tasks = (int64_t)n_large;
-                join_kernel<true, true><<<large_blocks, kSearchThreads, 0, st>>>(jl);
-            }
+            if (large_blocks) join_kernel<true, true><<<large_blocks, kSearchThreads, 0, st>>>(jl);
             CK(cudaGetLastError(), "join kernel (write)");
-            launches += large_blocks ? 2 : 1;
+            *launches += large_blocks ? 2 : 1;
         }
     }
-    uint64_t found = 0;
+    uint64_t total = 0;
     int32_t status = 0;
-    CK(cudaMemcpyAsync(&found, S->coff + n, sizeof(found), cudaMemcpyDeviceToHost, st), "count D2H");
+    CK(cudaMemcpyAsync(&total, S->coff + n, sizeof(total), cudaMemcpyDeviceToHost, st), "count D2H");
     CK(cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st), "status D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    ctx->last_search_launches = launches;
-    if (status) return fail(ctx, SWGB_EINTERNAL, "discover: a hash table was smaller than its bound");
-    *n_found = (int64_t)found;
+    if (status) return fail(ctx, SWGB_EINTERNAL, "join: a hash table was smaller than its bound");
+    *found = (int64_t)total;
     return SWGB_OK;
+}
+
+int check_discover_args(swgb_ctx* ctx, int k, int min_shared, int32_t* pairs, int64_t capacity,
+                        int64_t* n_found) {
+    if (!n_found) return fail(ctx, SWGB_EINVAL, "discover: n_found is NULL");
+    *n_found = 0;
+    if (k < 1 || k > 6) return fail(ctx, SWGB_EINVAL, "discover: k must be 1..6");
+    if (min_shared < 1) return fail(ctx, SWGB_EINVAL, "discover: min_shared must be >= 1");
+    if (capacity < 0 || (capacity > 0 && !pairs))
+        return fail(ctx, SWGB_EINVAL, "discover: negative capacity or pairs is NULL");
+    return SWGB_OK;
+}
+
+}  // namespace
+
+SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int min_shared,
+                              int32_t* pairs, int32_t* counts, int64_t capacity, int64_t* n_found,
+                              void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!set) return fail(ctx, SWGB_EINVAL, "discover: set is NULL");
+    int rc = check_discover_args(ctx, k, min_shared, pairs, capacity, n_found);
+    if (rc) return rc;
+    if (set->device != ctx->device) return fail(ctx, SWGB_EINVAL, "discover: set on another device");
+    if (set->total >= (int64_t)UINT32_MAX)
+        return fail(ctx, SWGB_ETOOBIG, "discover: more than 2^32-1 residues in the set");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->last_search_launches = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (set->n < 2) return SWGB_OK;
+    SearchStore* S = nullptr;
+    rc = search_store(ctx, &S);
+    if (rc) return rc;
+    const int64_t V = kmer_space(k);
+    const int64_t total = std::max<int64_t>(set->total, 1);
+    CK(grow(&S->ent_kmer, &S->ent_cap, total), "discover scratch");
+    CK(grow(&S->ent_pos, &S->entp_cap, total), "discover scratch");
+    CK(grow(&S->bseq, &S->bseq_cap, total), "discover scratch");
+    CK(grow(&S->bpos, &S->bpos_cap, total), "discover scratch");
+    CK(grow(&S->kcount, &S->kcount_cap, set->n), "discover scratch");
+    CK(grow(&S->start, &S->start_cap, V + 1), "discover scratch");
+    uint32_t gslots = 0;
+    rc = reserve_set_tables(ctx, S, set->max_len, &gslots);
+    if (rc) return rc;
+    int32_t launches = 0;
+    CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
+    rc = build_sets(ctx, S, set, k, S->ent_kmer, S->ent_pos, S->kcount, gslots, &launches, st);
+    if (!rc) rc = build_buckets(ctx, S, set, S->ent_kmer, S->ent_pos, S->kcount, V, S->start, S->bseq,
+                                S->bpos, &launches, st);
+    if (!rc) rc = join_rows(ctx, S, set, S->ent_kmer, S->kcount, S->start, S->bseq, set->n, true,
+                            min_shared, pairs, counts, capacity, n_found, &launches, st);
+    ctx->last_search_launches = launches;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Resident k-mer index of a reference set
+// ---------------------------------------------------------------------------
+struct swgb_index {
+    swgb_ctx* ctx = nullptr;
+    int device = 0;
+    const swgb_seqset* refs = nullptr;
+    int k = 6;
+    int64_t V = 0;
+    int64_t n = 0;
+    uint32_t* kmer = nullptr;   // k-mer sets of the references (at their offsets)
+    uint32_t* pos = nullptr;
+    uint32_t* cnt = nullptr;
+    uint32_t* comp = nullptr;   // [n][20] letter counts
+    uint32_t* start = nullptr;  // [V + 1]
+    int32_t* bseq = nullptr;
+    uint32_t* bpos = nullptr;
+    int64_t bytes = 0;
+};
+
+SWGB_EXPORT void swgb_index_destroy(swgb_index* ix) {
+    if (!ix) return;
+    cudaSetDevice(ix->device);
+    void* ptrs[] = {ix->kmer, ix->pos, ix->cnt, ix->comp, ix->start, ix->bseq, ix->bpos};
+    for (void* p : ptrs) cudaFree(p);
+    delete ix;
+}
+
+SWGB_EXPORT int swgb_index_create(swgb_ctx* ctx, const swgb_seqset* refs, int k, void* stream,
+                                  swgb_index** out) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!refs || !out) return fail(ctx, SWGB_EINVAL, "index: refs or out is NULL");
+    *out = nullptr;
+    if (k < 1 || k > 6) return fail(ctx, SWGB_EINVAL, "index: k must be 1..6");
+    if (refs->device != ctx->device) return fail(ctx, SWGB_EINVAL, "index: set on another device");
+    if (refs->total >= (int64_t)UINT32_MAX)
+        return fail(ctx, SWGB_ETOOBIG, "index: more than 2^32-1 residues in the set");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    SearchStore* S = nullptr;
+    int rc = search_store(ctx, &S);
+    if (rc) return rc;
+    swgb_index* ix = new (std::nothrow) swgb_index();
+    if (!ix) return fail(ctx, SWGB_ENOMEM, "index: host allocation");
+    ix->ctx = ctx;
+    ix->device = ctx->device;
+    ix->refs = refs;
+    ix->k = k;
+    ix->V = kmer_space(k);
+    ix->n = refs->n;
+    const int64_t total = std::max<int64_t>(refs->total, 1), n = std::max<int64_t>(refs->n, 1);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto** p, int64_t count) {
+        const size_t bytes = sizeof(**p) * (size_t)count;
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+        ix->bytes += (int64_t)bytes;
+    };
+    alloc(&ix->kmer, total);
+    alloc(&ix->pos, total);
+    alloc(&ix->bseq, total);
+    alloc(&ix->bpos, total);
+    alloc(&ix->cnt, n);
+    alloc(&ix->comp, n * kStdLetters);
+    alloc(&ix->start, ix->V + 1);
+    if (e != cudaSuccess) {
+        swgb_index_destroy(ix);
+        return cuda_fail(ctx, e, "index allocation");
+    }
+    uint32_t gslots = 0;
+    rc = reserve_set_tables(ctx, S, refs->max_len, &gslots);
+    int32_t launches = 0;
+    if (!rc) {
+        e = cudaMemsetAsync(S->status, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "memset");
+    }
+    if (!rc) rc = build_sets(ctx, S, refs, k, ix->kmer, ix->pos, ix->cnt, gslots, &launches, st);
+    if (!rc && refs->n > 0) {
+        composition_kernel<<<(unsigned)warp_grid(ctx, refs->n, 256), 256, 0, st>>>(view(refs), ix->comp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "composition kernel");
+        launches += 1;
+    }
+    if (!rc) rc = build_buckets(ctx, S, refs, ix->kmer, ix->pos, ix->cnt, ix->V, ix->start, ix->bseq,
+                                ix->bpos, &launches, st);
+    int32_t status = 0;
+    if (!rc) {
+        e = cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "index build");
+        else if (status) rc = fail(ctx, SWGB_EINTERNAL, "index: a k-mer table was smaller than its set");
+    }
+    ctx->last_search_launches = launches;
+    if (rc) {
+        swgb_index_destroy(ix);
+        return rc;
+    }
+    *out = ix;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_index_info(const swgb_index* ix, int64_t* n_refs, int* k, int64_t* bytes) {
+    if (!ix) return SWGB_EINVAL;
+    if (n_refs) *n_refs = ix->n;
+    if (k) *k = ix->k;
+    if (bytes) *bytes = ix->bytes;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_index_query(swgb_ctx* ctx, const swgb_index* ix, const swgb_seqset* queries,
+                                 int min_shared, int32_t* pairs, int32_t* counts, int64_t capacity,
+                                 int64_t* n_found, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!ix || !queries) return fail(ctx, SWGB_EINVAL, "index_query: index or queries is NULL");
+    int rc = check_discover_args(ctx, ix->k, min_shared, pairs, capacity, n_found);
+    if (rc) return rc;
+    if (queries->device != ctx->device || ix->device != ctx->device)
+        return fail(ctx, SWGB_EINVAL, "index_query: set or index on another device");
+    if (queries->total >= (int64_t)UINT32_MAX)
+        return fail(ctx, SWGB_ETOOBIG, "index_query: more than 2^32-1 query residues");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->last_search_launches = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (queries->n == 0 || ix->n == 0) return SWGB_OK;
+    SearchStore* S = nullptr;
+    rc = search_store(ctx, &S);
+    if (rc) return rc;
+    const int64_t total = std::max<int64_t>(queries->total, 1);
+    CK(grow(&S->ent_kmer, &S->ent_cap, total), "index_query scratch");
+    CK(grow(&S->ent_pos, &S->entp_cap, total), "index_query scratch");
+    CK(grow(&S->kcount, &S->kcount_cap, queries->n), "index_query scratch");
+    uint32_t gslots = 0;
+    rc = reserve_set_tables(ctx, S, queries->max_len, &gslots);
+    if (rc) return rc;
+    int32_t launches = 0;
+    CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
+    rc = build_sets(ctx, S, queries, ix->k, S->ent_kmer, S->ent_pos, S->kcount, gslots, &launches, st);
+    if (!rc) rc = join_rows(ctx, S, queries, S->ent_kmer, S->kcount, ix->start, ix->bseq, ix->n, false,
+                            min_shared, pairs, counts, capacity, n_found, &launches, st);
+    ctx->last_search_launches = launches;
+    return rc;
 }
 
 SWGB_EXPORT int swgb_search_launches(const swgb_ctx* ctx) {
@@ -984,5 +1390,151 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     ctx->last_search_launches = 2 + (large_blocks ? 1 : 0);
     if (status == 3) return fail(ctx, SWGB_ERANGE, "identity: a pair index or record outside its sequences");
     if (status) return fail(ctx, SWGB_EINTERNAL, "identity: a span's global optimum differs from its record's score");
+    return SWGB_OK;
+}
+
+namespace {
+
+// Features of pairs (i of A, j of B) from both sets' k-mer tables; the tables
+// of B come from the caller (another set's, or an index's).
+int run_features(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set_a, const swgb_seqset* set_b,
+                 const uint32_t* kmB, const uint32_t* posB, const uint32_t* cntB,
+                 const uint32_t* compB, bool b_is_a, int k, const int32_t* pairs, int64_t n_pairs,
+                 float* out, int32_t* launches, cudaStream_t st) {
+    // global hash tables: the k-mer sets of A (and B) and the feature
+    // kernel's table of K(i), reserved before any launch
+    const int blocks = ctx->sm_count * 2;
+    const int64_t longest = std::max<int64_t>(set_a->max_len, b_is_a ? 0 : set_b->max_len);
+    uint32_t gslots = 0;
+    int rc = reserve_set_tables(ctx, S, longest, &gslots);
+    if (rc) return rc;
+    if (gslots > (uint32_t)kFeatSlots)
+        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)blocks * 2 * gslots), "features scratch");
+    const int64_t total = std::max<int64_t>(set_a->total, 1), n = std::max<int64_t>(set_a->n, 1);
+    CK(grow(&S->ent_kmer, &S->ent_cap, total), "features scratch");
+    CK(grow(&S->ent_pos, &S->entp_cap, total), "features scratch");
+    CK(grow(&S->kcount, &S->kcount_cap, n), "features scratch");
+    CK(grow(&S->comp, &S->comp_cap, n * kStdLetters), "features scratch");
+    CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
+    rc = build_sets(ctx, S, set_a, k, S->ent_kmer, S->ent_pos, S->kcount, gslots, launches, st);
+    if (rc) return rc;
+    if (set_a->n > 0) {
+        composition_kernel<<<(unsigned)warp_grid(ctx, set_a->n, 256), 256, 0, st>>>(view(set_a), S->comp);
+        CK(cudaGetLastError(), "composition kernel");
+        *launches += 1;
+    }
+    if (b_is_a) {
+        kmB = S->ent_kmer;
+        posB = S->ent_pos;
+        cntB = S->kcount;
+        compB = S->comp;
+    } else if (!kmB) {
+        const int64_t tb = std::max<int64_t>(set_b->total, 1), nb = std::max<int64_t>(set_b->n, 1);
+        CK(grow(&S->ent2_kmer, &S->ent2_cap, tb), "features scratch");
+        CK(grow(&S->ent2_pos, &S->ent2p_cap, tb), "features scratch");
+        CK(grow(&S->kcount2, &S->kcount2_cap, nb), "features scratch");
+        CK(grow(&S->comp2, &S->comp2_cap, nb * kStdLetters), "features scratch");
+        rc = build_sets(ctx, S, set_b, k, S->ent2_kmer, S->ent2_pos, S->kcount2, gslots, launches, st);
+        if (rc) return rc;
+        if (set_b->n > 0) {
+            composition_kernel<<<(unsigned)warp_grid(ctx, set_b->n, 256), 256, 0, st>>>(view(set_b), S->comp2);
+            CK(cudaGetLastError(), "composition kernel");
+            *launches += 1;
+        }
+        kmB = S->ent2_kmer;
+        posB = S->ent2_pos;
+        cntB = S->kcount2;
+        compB = S->comp2;
+    }
+    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long), st), "memset");
+    FeatArgs fa{view(set_a), view(set_b), k, S->ent_kmer, S->ent_pos, S->kcount, kmB, posB, cntB,
+                S->comp, compB, pairs, n_pairs, out, S->gtab, gslots, S->ctr + 1, S->status};
+    features_kernel<<<blocks, kFeatWarps * 32, 0, st>>>(fa);
+    CK(cudaGetLastError(), "features kernel");
+    *launches += 1;
+    int32_t status = 0;
+    CK(cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st), "status D2H");
+    CK(cudaStreamSynchronize(st), "stream sync");
+    if (status == 3) return fail(ctx, SWGB_ERANGE, "features: a pair index outside its set");
+    if (status) return fail(ctx, SWGB_EINTERNAL, "features: a k-mer table was smaller than its set");
+    return SWGB_OK;
+}
+
+}  // namespace
+
+SWGB_EXPORT int swgb_pair_features(swgb_ctx* ctx, const swgb_seqset* set_a, const swgb_seqset* set_b,
+                                   const int32_t* pairs, int64_t n_pairs, int k, float* out,
+                                   void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!set_a || !set_b) return fail(ctx, SWGB_EINVAL, "features: set is NULL");
+    if (k < 1 || k > 6) return fail(ctx, SWGB_EINVAL, "features: k must be 1..6");
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !out)))
+        return fail(ctx, SWGB_EINVAL, "features: negative count or NULL buffer");
+    if (set_a->device != ctx->device || set_b->device != ctx->device)
+        return fail(ctx, SWGB_EINVAL, "features: set on another device");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->last_search_launches = 0;
+    if (n_pairs == 0) return SWGB_OK;
+    SearchStore* S = nullptr;
+    int rc = search_store(ctx, &S);
+    if (rc) return rc;
+    int32_t launches = 0;
+    rc = run_features(ctx, S, set_a, set_b, nullptr, nullptr, nullptr, nullptr, set_b == set_a, k,
+                      pairs, n_pairs, out, &launches, (cudaStream_t)stream);
+    ctx->last_search_launches = launches;
+    return rc;
+}
+
+SWGB_EXPORT int swgb_index_features(swgb_ctx* ctx, const swgb_index* ix, const swgb_seqset* queries,
+                                    const int32_t* pairs, int64_t n_pairs, float* out, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!ix || !queries) return fail(ctx, SWGB_EINVAL, "index_features: index or queries is NULL");
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !out)))
+        return fail(ctx, SWGB_EINVAL, "index_features: negative count or NULL buffer");
+    if (queries->device != ctx->device || ix->device != ctx->device)
+        return fail(ctx, SWGB_EINVAL, "index_features: set or index on another device");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->last_search_launches = 0;
+    if (n_pairs == 0) return SWGB_OK;
+    SearchStore* S = nullptr;
+    int rc = search_store(ctx, &S);
+    if (rc) return rc;
+    int32_t launches = 0;
+    rc = run_features(ctx, S, queries, ix->refs, ix->kmer, ix->pos, ix->cnt, ix->comp, false, ix->k,
+                      pairs, n_pairs, out, &launches, (cudaStream_t)stream);
+    ctx->last_search_launches = launches;
+    return rc;
+}
+
+SWGB_EXPORT int swgb_select_pairs(swgb_ctx* ctx, const int32_t* pairs, const float* logits,
+                                  int64_t n_pairs, float threshold, int32_t* kept,
+                                  int64_t* kept_index, int64_t* n_kept, void* stream) {
+    if (!ctx) return SWGB_EINVAL;
+    if (!n_kept) return fail(ctx, SWGB_EINVAL, "select: n_kept is NULL");
+    *n_kept = 0;
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !logits || !kept)))
+        return fail(ctx, SWGB_EINVAL, "select: negative count or NULL buffer");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->last_search_launches = 0;
+    if (n_pairs == 0) return SWGB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SearchStore* S = nullptr;
+    int rc = search_store(ctx, &S);
+    if (rc) return rc;
+    CK(grow(&S->flags, &S->flags_cap, n_pairs), "select scratch");
+    CK(grow(&S->coff, &S->coff_cap, n_pairs + 1), "select scratch");
+    const int64_t g = std::min<int64_t>((n_pairs + 255) / 256, (int64_t)ctx->sm_count * 16);
+    select_flags_kernel<<<(unsigned)g, 256, 0, st>>>(logits, n_pairs, threshold, S->flags);
+    CK(cudaGetLastError(), "select kernel");
+    rc = device_scan<uint64_t>(ctx, S, S->flags, n_pairs, S->coff, st);
+    if (rc) return rc;
+    select_scatter_kernel<<<(unsigned)g, 256, 0, st>>>(pairs, S->flags, S->coff, n_pairs, kept,
+                                                       kept_index);
+    CK(cudaGetLastError(), "select kernel");
+    uint64_t found = 0;
+    CK(cudaMemcpyAsync(&found, S->coff + n_pairs, sizeof(found), cudaMemcpyDeviceToHost, st), "count D2H");
+    CK(cudaStreamSynchronize(st), "stream sync");
+    ctx->last_search_launches = 5;
+    *n_kept = (int64_t)found;
     return SWGB_OK;
 }

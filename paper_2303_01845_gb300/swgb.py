@@ -33,6 +33,8 @@ SWGB_TIMING = 0x2
 SWGB_NOALLOC_SCRATCH_BYTES = 32 << 20
 SWGB_NOALLOC_MAX_PAIRS = 1 << 19
 SWGB_NOALLOC_MAX_QUERY_LENGTH = 4096
+SWGB_MLP_PARAMS = 10561
+SWGB_FEATURES = 32
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 
@@ -111,6 +113,25 @@ _SIGS = [
                                      ctypes.POINTER(swgb_params), ctypes.POINTER(swgb_thresholds),
                                      _VP, _VP]),
     ("swgb_search_launches", ctypes.c_int, [_VP]),
+    ("swgb_index_create", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    ("swgb_index_destroy", None, [_VP]),
+    ("swgb_index_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    ("swgb_index_query", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), _VP]),
+    ("swgb_index_features", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("swgb_pair_features", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, _VP]),
+    ("swgb_mlp_create", ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
+    ("swgb_mlp_destroy", None, [_VP]),
+    ("swgb_mlp_set", ctypes.c_int, [_VP, _VP]),
+    ("swgb_mlp_get", ctypes.c_int, [_VP, _VP]),
+    ("swgb_mlp_forward", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("swgb_mlp_grad", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP, _VP]),
+    ("swgb_mlp_train", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                      _VP]),
+    ("swgb_select_pairs", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP,
+                                         ctypes.POINTER(ctypes.c_int64), _VP]),
     ("swgb_align_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                           _VP, ctypes.c_int64, ctypes.POINTER(swgb_params), _VP,
                                           _VP]),
@@ -378,6 +399,173 @@ def swgb_identity(ctx, queries, refs, pairs, records, params, thresholds=None, o
     return out
 
 
+def _cuda(t_, dtype, what):
+    import torch
+    if not t_.is_cuda or t_.dtype != dtype or not t_.is_contiguous():
+        raise TypeError("%s must be a contiguous CUDA %s tensor" % (what, dtype))
+
+
+def swgb_pair_features(ctx, set_a, set_b, pairs, k=6, out=None, stream=None):
+    """Features of the learned filter for CUDA int32 pairs [P, 2] (index into
+    set_a, index into set_b): CUDA float32 [P, 32].  Synchronous."""
+    import torch
+    _cuda(pairs, torch.int32, "pairs")
+    n = pairs.shape[0]
+    if out is None:
+        out = torch.empty((n, SWGB_FEATURES), dtype=torch.float32, device=pairs.device)
+    _cuda(out, torch.float32, "out")
+    rc = load().swgb_pair_features(ctx, set_a, set_b, _ptr(pairs), n, int(k), _ptr(out),
+                                   _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
+def swgb_select_pairs(ctx, pairs, logits, threshold, stream=None):
+    """(kept pairs CUDA int32 [K, 2], their positions CUDA int64 [K]) of the
+    pairs whose logit is >= threshold, in order.  Synchronous."""
+    import torch
+    _cuda(pairs, torch.int32, "pairs")
+    _cuda(logits, torch.float32, "logits")
+    n = pairs.shape[0]
+    kept = torch.empty((max(n, 1), 2), dtype=torch.int32, device=pairs.device)
+    index = torch.empty((max(n, 1),), dtype=torch.int64, device=pairs.device)
+    nk = ctypes.c_int64()
+    rc = load().swgb_select_pairs(ctx, _ptr(pairs), _ptr(logits), n, float(threshold), _ptr(kept),
+                                  _ptr(index), ctypes.byref(nk), _stream_handle(stream))
+    _check(ctx, rc)
+    return kept[:nk.value], index[:nk.value]
+
+
+class Index:
+    """A resident k-mer index of a reference SeqSet (swgb_index_*)."""
+
+    def __init__(self, aligner, refs, k=6, stream=None):
+        self.aligner = aligner
+        self.refs = refs          # kept alive: the index reads the set
+        h = _VP()
+        _check(aligner.ctx, load().swgb_index_create(aligner.ctx, refs.handle, int(k),
+                                                     _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def info(self):
+        n = ctypes.c_int64()
+        k = ctypes.c_int()
+        b = ctypes.c_int64()
+        load().swgb_index_info(self.handle, ctypes.byref(n), ctypes.byref(k), ctypes.byref(b))
+        return {"n_refs": n.value, "k": k.value, "bytes": b.value}
+
+    def query(self, queries, min_shared=2, capacity=None, stream=None, ctx=None):
+        """(pairs CUDA int32 [P, 2] = (query, reference), counts CUDA int32 [P])."""
+        import torch
+        ctx = ctx or self.aligner.ctx
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cap = 1 << 16 if capacity is None else int(capacity)
+        while True:
+            pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
+            counts = torch.empty((max(cap, 1),), dtype=torch.int32, device=dev)
+            found = ctypes.c_int64()
+            _check(ctx, load().swgb_index_query(ctx, self.handle, queries.handle, int(min_shared),
+                                                _ptr(pairs), _ptr(counts), cap, ctypes.byref(found),
+                                                _stream_handle(stream)))
+            if found.value <= cap or capacity is not None:
+                m = min(found.value, cap)
+                return pairs[:m], counts[:m]
+            cap = found.value
+
+    def features(self, queries, pairs, out=None, stream=None, ctx=None):
+        import torch
+        ctx = ctx or self.aligner.ctx
+        _cuda(pairs, torch.int32, "pairs")
+        n = pairs.shape[0]
+        if out is None:
+            out = torch.empty((n, SWGB_FEATURES), dtype=torch.float32, device=pairs.device)
+        _check(ctx, load().swgb_index_features(ctx, self.handle, queries.handle, _ptr(pairs), n,
+                                               _ptr(out), _stream_handle(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            load().swgb_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned filter's network (swgb_mlp_*), parameters on the device."""
+
+    def __init__(self, ctx, init):
+        init = np.ascontiguousarray(init, dtype=np.float32).reshape(-1)
+        if init.size != SWGB_MLP_PARAMS:
+            raise ValueError("expected %d parameters" % SWGB_MLP_PARAMS)
+        self.ctx = ctx
+        h = _VP()
+        _check(ctx, load().swgb_mlp_create(ctx, init.ctypes.data, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().swgb_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        _check(self.ctx, load().swgb_mlp_set(self.handle, params.ctypes.data))
+
+    def get(self):
+        out = np.zeros(SWGB_MLP_PARAMS, np.float32)
+        _check(self.ctx, load().swgb_mlp_get(self.handle, out.ctypes.data))
+        return out
+
+    def forward(self, features, out=None, stream=None):
+        import torch
+        _cuda(features, torch.float32, "features")
+        n = features.shape[0]
+        if out is None:
+            out = torch.empty((n,), dtype=torch.float32, device=features.device)
+        _check(self.ctx, load().swgb_mlp_forward(self.handle, _ptr(features), n, _ptr(out),
+                                                 _stream_handle(stream)))
+        return out
+
+    def grad(self, features, labels, pos_weight=1.0, stream=None):
+        """(gradient CUDA float32 [SWGB_MLP_PARAMS], loss CUDA float32 [1])."""
+        import torch
+        _cuda(features, torch.float32, "features")
+        _cuda(labels, torch.float32, "labels")
+        g = torch.empty((SWGB_MLP_PARAMS,), dtype=torch.float32, device=features.device)
+        loss = torch.empty((1,), dtype=torch.float32, device=features.device)
+        _check(self.ctx, load().swgb_mlp_grad(self.handle, _ptr(features), _ptr(labels),
+                                              features.shape[0], float(pos_weight), _ptr(g),
+                                              _ptr(loss), _stream_handle(stream)))
+        return g, loss
+
+    def train(self, features, labels, order=None, batch=8192, lr=1e-3, pos_weight=1.0,
+              stream=None):
+        """One pass in minibatches (order: CUDA int32 permutation or None);
+        returns the mean minibatch loss."""
+        import torch
+        _cuda(features, torch.float32, "features")
+        _cuda(labels, torch.float32, "labels")
+        if order is not None:
+            _cuda(order, torch.int32, "order")
+        ml = ctypes.c_float()
+        _check(self.ctx, load().swgb_mlp_train(self.handle, _ptr(features), _ptr(labels),
+                                               _ptr(order), features.shape[0], int(batch),
+                                               float(lr), float(pos_weight), ctypes.byref(ml),
+                                               _stream_handle(stream)))
+        return ml.value
+
+
 def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, out, stream=None):
     """Allocation-free alignment for callers that cannot allocate device memory
     while they align (a pool or arena owns the device, or the footprint must
@@ -442,6 +630,9 @@ class Aligner:
 
     def discover(self, seqset, k=6, min_shared=2, capacity=None, stream=None):
         return swgb_discover(self.ctx, seqset.handle, k, min_shared, capacity, stream)
+
+    def features(self, set_a, set_b, pairs, k=6, out=None, stream=None):
+        return swgb_pair_features(self.ctx, set_a.handle, set_b.handle, pairs, k, out, stream)
 
     def identity(self, queries, refs, pairs, records, params=None, thresholds=None, out=None,
                  stream=None):

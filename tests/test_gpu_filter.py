@@ -1,0 +1,257 @@
+"""GPU checks of the learned candidate filter through the C ABI: pair
+features bit-exact against the oracle; the network's logits, gradient and
+Adam step against the float64 oracle network within tolerances derived from
+bfloat16; selection exact; and a trained filter's gain over the common-k-mer
+threshold on a held-out family block.
+
+Tolerances.  Products are of bfloat16 operands (exact in float32) summed in
+float32 over at most 128 terms; the oracle sums the same bfloat16 values in
+float64.  What differs is (a) float32 accumulation, relative error about
+128 * 2^-24, and (b) a bfloat16 rounding of an activation or a gradient
+operand that falls on the other side of a rounding boundary because its
+float32 value differs in the last bits from the float64 one: one such flip
+moves that element by one bfloat16 step (2^-8 relative) and a logit or a
+gradient entry by that step times one weight.  Logits: |dz| <= 2e-3 (1 + |z|);
+gradients and Adam steps: max error <= 2 % of the largest entry, and the
+relative 2-norm error <= 1 %.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_01845_gb300 import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def aligner(torch_mod):
+    from paper_2303_01845_gb300 import swgb
+    al = swgb.Aligner(0)
+    yield al
+    al.close()
+
+
+@pytest.fixture(scope="module")
+def mat():
+    from paper_2303_01845_gb300 import swgb
+    return swgb.swgb_blosum62()
+
+
+@pytest.fixture(scope="module")
+def family2k(aligner, torch_mod, oracle_mod, mat):
+    fs = workload.generate_families("families_2k", mat)
+    s = aligner.seqset(torch_mod.from_numpy(fs.res).cuda(), torch_mod.from_numpy(fs.off).cuda())
+    cand, _ = aligner.discover(s, 6, 2)
+    yield fs, s, cand
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def mlp_mod():
+    from oracle import mlp_oracle
+    return mlp_oracle
+
+
+def pack(seqs):
+    lens = np.array([len(x) for x in seqs], dtype=np.int64)
+    off = np.zeros(len(seqs) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    res = (np.concatenate([np.asarray(x, np.uint8) for x in seqs]) if off[-1] > 0
+           else np.zeros(0, np.uint8))
+    return res, off
+
+
+# ---------------------------------------------------------------------------
+# features
+# ---------------------------------------------------------------------------
+def test_features_of_family_candidates_match_oracle(aligner, torch_mod, oracle_mod, family2k):
+    from paper_2303_01845_gb300 import swgb
+    fs, s, cand = family2k
+    got = swgb.swgb_pair_features(aligner.ctx, s.handle, s.handle, cand).cpu().numpy()
+    want = oracle_mod.pair_features_batch(fs.res, fs.off, fs.res, fs.off, cand.cpu().numpy())
+    np.testing.assert_array_equal(got, want)
+
+
+def test_features_across_two_sets_and_edge_cases(aligner, torch_mod, oracle_mod):
+    """Random pairs between two different sets, in no particular order, with
+    non-standard letters, sequences shorter than k, empty ones, repeats, and
+    sequences of more than 2048 k-mers (global-memory tables)."""
+    from paper_2303_01845_gb300 import swgb
+    rng = np.random.default_rng(8)
+    base = rng.integers(0, 20, 3000)
+    A = [base[:2600], base[100:2900], [], [0] * 30, rng.integers(0, 24, 40), base[5:9]]
+    B = [base[50:3000], [0] * 12, rng.integers(0, 20, 300), [], base[:700], [22] * 10]
+    for _ in range(60):
+        L = int(rng.integers(0, 200))
+        A.append(rng.integers(0, 20 if rng.random() < 0.7 else 24, L))
+        B.append(np.concatenate([rng.integers(0, 20, 5), A[-1][3:]]) if rng.random() < 0.5
+                 else rng.integers(0, 20, L))
+    ra, oa = pack(A)
+    rb, ob = pack(B)
+    pairs = np.stack([rng.integers(0, len(A), 500), rng.integers(0, len(B), 500)], 1).astype(np.int32)
+    pairs[:6] = [[0, 0], [1, 0], [0, 4], [2, 3], [3, 1], [5, 5]]
+    sa = aligner.seqset(torch_mod.from_numpy(ra).cuda(), torch_mod.from_numpy(oa).cuda())
+    sb = aligner.seqset(torch_mod.from_numpy(rb).cuda(), torch_mod.from_numpy(ob).cuda())
+    got = swgb.swgb_pair_features(aligner.ctx, sa.handle, sb.handle,
+                                  torch_mod.from_numpy(pairs).cuda()).cpu().numpy()
+    want = oracle_mod.pair_features_batch(ra, oa, rb, ob, pairs)
+    np.testing.assert_array_equal(got, want)
+    with pytest.raises(swgb.SwgbError) as e:
+        bad = torch_mod.tensor([[0, len(B)]], dtype=torch_mod.int32, device="cuda")
+        swgb.swgb_pair_features(aligner.ctx, sa.handle, sb.handle, bad)
+    assert e.value.code == swgb.SWGB_ERANGE
+    sa.close()
+    sb.close()
+
+
+# ---------------------------------------------------------------------------
+# network
+# ---------------------------------------------------------------------------
+def real_features(aligner, torch_mod, family2k):
+    from paper_2303_01845_gb300 import swgb
+    fs, s, cand = family2k
+    return swgb.swgb_pair_features(aligner.ctx, s.handle, s.handle, cand)
+
+
+def test_forward_matches_oracle(aligner, torch_mod, mlp_mod, family2k):
+    from paper_2303_01845_gb300 import swgb
+    from paper_2303_01845_gb300 import filter as F
+    X = real_features(aligner, torch_mod, family2k)
+    rng = np.random.default_rng(3)
+    Xr = torch_mod.from_numpy(rng.uniform(-1, 2, (777, 32)).astype(np.float32)).cuda()
+    for seed in (1, 2):
+        init = F.init_params(seed)
+        init[10560] = 0.3      # b3
+        init[2048:2112] = rng.uniform(-0.2, 0.2, 64).astype(np.float32)   # b1
+        net = swgb.MLP(aligner.ctx, init)
+        for feats in (X, Xr):
+            z = net.forward(feats).cpu().numpy()
+            want, _ = mlp_mod.forward(init.astype(np.float64), feats.cpu().numpy().astype(np.float64))
+            err = np.abs(z - want)
+            assert (err <= 2e-3 * (1 + np.abs(want))).all(), err.max()
+        net.close()
+
+
+def grad_close(got, want):
+    err = np.abs(got - want)
+    assert err.max() <= 0.02 * np.abs(want).max() + 1e-9, (err.max(), np.abs(want).max())
+    assert np.linalg.norm(got - want) <= 0.01 * np.linalg.norm(want) + 1e-9
+
+
+def test_gradient_matches_oracle(aligner, torch_mod, oracle_mod, mlp_mod, family2k):
+    from paper_2303_01845_gb300 import swgb
+    from paper_2303_01845_gb300 import filter as F
+    X = real_features(aligner, torch_mod, family2k)
+    n = X.shape[0]
+    rng = np.random.default_rng(4)
+    y = (rng.uniform(size=n) < 0.3).astype(np.float32)
+    init = F.init_params(5)
+    net = swgb.MLP(aligner.ctx, init)
+    for pw, rows in ((1.0, n), (6.5, n), (2.0, 37)):
+        Xs = X[:rows].contiguous()
+        ys = torch_mod.from_numpy(y[:rows]).cuda()
+        g, loss = net.grad(Xs, ys, pw)
+        wl, wg = mlp_mod.loss_and_grad(init.astype(np.float64), Xs.cpu().numpy().astype(np.float64),
+                                       y[:rows], pw)
+        assert abs(loss.item() - wl) <= 1e-3 * (1 + abs(wl))
+        grad_close(g.cpu().numpy(), wg)
+    net.close()
+
+
+def test_training_step_matches_oracle_adam(aligner, torch_mod, mlp_mod, family2k):
+    """A full-batch Adam step on the device against the oracle's Adam step on
+    the device's own gradient of that batch.  Entries whose gradient is within
+    1e-3 of the largest are compared (their step is sign-stable: a gradient
+    summed in another order flips no sign there); every step is at most lr."""
+    from paper_2303_01845_gb300 import swgb
+    from paper_2303_01845_gb300 import filter as F
+    X = real_features(aligner, torch_mod, family2k)
+    n = X.shape[0]
+    y = (np.random.default_rng(6).uniform(size=n) < 0.3).astype(np.float32)
+    init = F.init_params(7)
+    net = swgb.MLP(aligner.ctx, init)
+    yd = torch_mod.from_numpy(y).cuda()
+    lr = 1e-3
+    g, _ = net.grad(X, yd, 3.0)
+    gg = g.cpu().numpy().astype(np.float64)
+    net.train(X, yd, None, n, lr, 3.0)
+    p = init.astype(np.float64)
+    p1, _, _ = mlp_mod.adam_step(p, gg, np.zeros_like(p), np.zeros_like(p), 1, lr)
+    d_got = net.get().astype(np.float64) - p
+    d_want = p1 - p
+    stable = np.abs(gg) > 1e-3 * np.abs(gg).max()
+    assert stable.sum() > 1000
+    assert np.abs(d_got - d_want)[stable].max() <= 1e-3 * lr
+    assert np.abs(d_got).max() <= 1.001 * lr
+    net.close()
+
+
+def test_select_pairs_is_exact(aligner, torch_mod):
+    from paper_2303_01845_gb300 import swgb
+    rng = np.random.default_rng(9)
+    for n in (0, 1, 1000, 70000):
+        pairs = rng.integers(0, 1 << 20, (n, 2)).astype(np.int32)
+        logits = rng.normal(size=n).astype(np.float32)
+        kept, idx = swgb.swgb_select_pairs(aligner.ctx, torch_mod.from_numpy(pairs).cuda(),
+                                           torch_mod.from_numpy(logits).cuda(), 0.25)
+        sel = np.nonzero(logits >= 0.25)[0]
+        np.testing.assert_array_equal(idx.cpu().numpy(), sel)
+        np.testing.assert_array_equal(kept.cpu().numpy(), pairs[sel])
+
+
+# ---------------------------------------------------------------------------
+# what the trained network gains
+# ---------------------------------------------------------------------------
+def block(aligner, torch_mod, mat, seed, n_fam=1000):
+    from paper_2303_01845_gb300 import filter as F
+    from paper_2303_01845_gb300 import swgb
+    spec = workload.FamilySpec("filter_block", n_fam, 10, "lognormal", 20, 5000, median=250.0,
+                               sigma=0.7, seed=seed)
+    fs = workload.generate_families(spec, mat)
+    s = aligner.seqset(torch_mod.from_numpy(fs.res).cuda(), torch_mod.from_numpy(fs.off).cuda())
+    cand, counts = aligner.discover(s, 6, 2)
+    feats = swgb.swgb_pair_features(aligner.ctx, s.handle, s.handle, cand)
+    _, ident = F.exact_labels(aligner, s, cand, swgb.make_params(mat, 11, 1))
+    return fs, s, cand, counts, feats, ident[:, 2].to(torch_mod.float32).contiguous()
+
+
+def test_trained_filter_beats_the_kmer_threshold(aligner, torch_mod, mat):
+    """Trained on one seeded family block, tested on another: at a threshold
+    set for 99.5 % recall of the training positives, the network keeps at
+    least 97 % of the held-out passing pairs while aligning at most a third of
+    the candidates; the next common-k-mer threshold (3 instead of 2) loses
+    far more of the passing pairs."""
+    from paper_2303_01845_gb300 import filter as F
+    _, s_tr, _, _, X_tr, y_tr = block(aligner, torch_mod, mat, 4)
+    _, s_te, cand_te, cnt_te, X_te, y_te = block(aligner, torch_mod, mat, 3)
+    net, losses = F.train(aligner, X_tr, y_tr, epochs=20, batch=1024, lr=3e-3, seed=1)
+    assert losses[-1] < losses[0]
+    thr = F.calibrate(net, X_tr, y_tr, 0.995)
+    z = net.forward(X_te).cpu().numpy()
+    y = y_te.cpu().numpy() > 0.5
+    keep = z >= thr
+    recall = keep[y].mean()
+    kept_frac = keep.mean()
+    c = cnt_te.cpu().numpy()
+    recall_k3 = (c[y] >= 3).mean()
+    assert y.sum() > 500
+    assert recall >= 0.97, recall
+    assert kept_frac <= 1 / 3, kept_frac
+    assert recall_k3 < 0.8, recall_k3
+    # the filtered search returns exactly the kept candidates' exact results
+    from paper_2303_01845_gb300 import swgb
+    res = F.filtered_search(aligner, s_te, net, thr, swgb.make_params(mat, 11, 1))
+    np.testing.assert_array_equal(res["kept_index"].cpu().numpy(), np.nonzero(keep)[0])
+    ident_all = F.exact_labels(aligner, s_te, cand_te, swgb.make_params(mat, 11, 1))[1].cpu().numpy()
+    np.testing.assert_array_equal(res["identity"].cpu().numpy(), ident_all[keep])
+    net.close()
+    s_tr.close()
+    s_te.close()
