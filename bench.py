@@ -55,6 +55,10 @@ def parse():
                     help="family blocks: training epochs of the learned filter")
     ap.add_argument("--filter-recall", type=float, default=0.995,
                     help="family blocks: recall of the training positives the threshold keeps")
+    ap.add_argument("--serve-refs", type=int, default=1_000_000, help="serving: resident references")
+    ap.add_argument("--serve-requests", type=int, default=400, help="serving: timed requests")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
+    ap.add_argument("--serve-slots", type=int, default=3, help="serving: batches in flight")
     return ap.parse_args()
 
 
@@ -647,12 +651,139 @@ def run_search(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """The query server over 1,000,000 resident references: requests of 1 to
+    1,000 queries arrive as a Poisson process; each goes through shared-6-mer
+    candidates from the resident index, the learned filter (trained
+    beforehand on a family block of another seed), exact alignment and
+    identity.  Latency = submission to completion of a request."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_2303_01845_gb300 import filter as F
+    from paper_2303_01845_gb300 import swgb, workload
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mat = swgb.swgb_blosum62()
+    params = swgb.make_params(mat, 11, 1)
+    al = swgb.Aligner(local)
+    # ---- the filter, trained on an all-vs-all family block (untimed)
+    t_train = time.perf_counter()
+    fs_tr = workload.generate_families(dataclasses.replace(workload.FAMILY_SPECS["families_200k"],
+                                                           seed=4), mat)
+    s_tr = al.seqset(torch.from_numpy(fs_tr.res).to(dev), torch.from_numpy(fs_tr.off).to(dev))
+    cand_tr, _ = al.discover(s_tr, 6, 2)
+    _, ident_tr = F.exact_labels(al, s_tr, cand_tr, params)
+    X_tr = swgb.swgb_pair_features(al.ctx, s_tr.handle, s_tr.handle, cand_tr)
+    y_tr = ident_tr[:, 2].to(torch.float32).contiguous()
+    net, _ = F.train(al, X_tr, y_tr, epochs=args.filter_epochs, batch=8192, lr=3e-3, seed=1)
+    threshold = F.calibrate(net, X_tr, y_tr, args.filter_recall)
+    mlp_params = net.get()
+    net.close()
+    del cand_tr, ident_tr, X_tr, y_tr
+    s_tr.close()
+    t_train = time.perf_counter() - t_train
+    # ---- resident references: 100,000 families x 10 copies; queries: an
+    # 11th copy of random families (or an unrelated draw)
+    n_fam = args.serve_refs // 10
+    spec = workload.FamilySpec("serving_refs", n_fam, 11, "lognormal", 20, 5000, median=250.0,
+                               sigma=0.7, seed=5)
+    fs = workload.generate_families(spec, mat)
+    n = len(fs)
+    is_q = np.zeros(n, bool)
+    is_q[np.arange(10, n, 11)] = True
+
+    def pack(idx):
+        lens = (fs.off[idx + 1] - fs.off[idx]).astype(np.int64)
+        off = np.zeros(len(idx) + 1, np.int64)
+        np.cumsum(lens, out=off[1:])
+        starts = fs.off[idx]
+        res = np.concatenate([fs.res[s:s + l] for s, l in zip(starts, lens)]).astype(np.uint8)
+        return res, off
+    rr, ro = pack(np.nonzero(~is_q)[0])
+    qr, qo = pack(np.nonzero(is_q)[0])
+    t_index = time.perf_counter()
+    refs = al.seqset(torch.from_numpy(rr).to(dev), torch.from_numpy(ro).to(dev))
+    index = swgb.Index(al, refs, 6)
+    torch.cuda.synchronize()
+    t_index = time.perf_counter() - t_index
+    srv = swgb.Server(refs, index, params, mlp_params, device=local, slots=args.serve_slots,
+                      threshold=threshold, max_batch_queries=4096, max_batch_residues=1 << 21,
+                      max_inflight_bytes=8 << 30, candidates_per_query=1024)
+    rng = np.random.default_rng(17)
+    nq_pool = len(qo) - 1
+
+    def make_request():
+        size = int(rng.integers(1, 1001))
+        q0 = int(rng.integers(0, nq_pool - size))
+        off = qo[q0:q0 + size + 1] - qo[q0]
+        return qr[qo[q0]:qo[q0 + size]], off
+
+    for _ in range(args.warmup):
+        srv.wait(srv.submit(*make_request()))
+    reqs = [make_request() for _ in range(args.serve_requests)]
+    gaps = rng.exponential(1.0 / args.serve_rate, len(reqs))
+    tickets = []
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        next_t = t0
+        for (c, o), g in zip(reqs, gaps):
+            next_t += g
+            delay = next_t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(c, o))
+        results = [srv.wait(tk) for tk in tickets]
+        wall = time.perf_counter() - t0
+    clock = clocks.summary()
+    lat = np.array([r["latency_ms"] for r in results])
+    queue = np.array([r["queue_ms"] for r in results])
+    aligned = sum(len(r["records"]) for r in results)
+    cands = sum(r["candidates"] for r in results)
+    queries = sum(len(o) - 1 for _, o in reqs)
+    passing = sum(int(r["identity"][:, 2].sum()) for r in results if len(r["identity"]))
+    stats = srv.stats()
+    info = index.info()
+    srv.close()
+    line = {
+        "metric": METRIC, "value": aligned / wall, "unit": "alignments/s", "n_gpus": 1,
+        "steps": len(reqs), "warmup": args.warmup, "ms_per_step": 1000 * wall / len(reqs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i16x2+i32 align, bf16 net", "data": "synthetic",
+        "config": {"workload": "serving_%dk" % (args.serve_refs // 1000),
+                   "references": int(len(ro) - 1), "reference_residues": int(ro[-1]),
+                   "requests": len(reqs), "queries_per_request": "uniform 1..1000",
+                   "arrivals": "Poisson, %.1f requests/s" % args.serve_rate,
+                   "slots": args.serve_slots, "index_bytes": info["bytes"],
+                   "index_build_s": t_index, "filter_training_s": t_train,
+                   "filter_threshold": threshold,
+                   "step": "one request (submission to completion)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "queue_ms": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+        "throughput": {"alignments_per_s": aligned / wall, "candidates_per_s": cands / wall,
+                       "queries_per_s": queries / wall, "requests_per_s": len(reqs) / wall,
+                       "passing_pairs": passing, "aligned_pairs": aligned, "candidates": cands,
+                       "wall_s": wall},
+        "max_batches_in_flight": stats["max_overlap"],
+        "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
+                   "reasons": clock["reasons"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("families"):
         run_search(args)
+    elif args.workload.startswith("serving"):
+        run_serving(args)
     else:
         run_ours(args)
 

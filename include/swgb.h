@@ -37,7 +37,9 @@
  *
  * Threading: a context owns device scratch reused by every call, so calls on
  * one context must be ordered (one stream, or caller-serialised).  Different
- * contexts are independent.
+ * contexts are independent.  A sequence set (or index) may be read by the
+ * calls of any context of its device at once; it must not be reloaded or
+ * destroyed while such calls are in flight.
  */
 #ifndef SWGB_H
 #define SWGB_H
@@ -415,7 +417,7 @@ int swgb_select_pairs(swgb_ctx* ctx, const int32_t* pairs, const float* logits, 
  * stream.  A free worker admits the longest FIFO prefix of the waiting
  * requests that fits one batch (max_batch_queries, max_batch_residues) and
  * the device-memory budget (the reservations of the requests in flight,
- * reservation = 24 bytes per residue + candidates_per_query x 172 bytes per
+ * reservation = 24 bytes per residue + candidates_per_query x 192 bytes per
  * query, stay within max_inflight_bytes; the blocked formation of the
  * overlap matrix bounds memory the same way, Sec. "Blocked 2D Sparse
  * SUMMA"), and runs it; the batches of different workers overlap on the
@@ -446,6 +448,7 @@ typedef struct {
     double latency_ms;             /* submission to completion */
     int64_t batch_id;              /* the batch the request ran in */
     int32_t slot;                  /* the worker that ran it */
+    const char* error;             /* message of a failed request ("" if none) */
 } swgb_server_result;
 
 /* Defaults: 3 slots, 4096 queries / 2^20 residues per batch, 4 GiB budget,

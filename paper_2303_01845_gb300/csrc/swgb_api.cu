@@ -448,7 +448,8 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
 
 int check_sets(swgb_ctx* ctx, const swgb_seqset* q, const swgb_seqset* r) {
     if (!q || !r) return fail(ctx, SWGB_EINVAL, "sequence set is NULL");
-    if (q->ctx != ctx || r->ctx != ctx) return fail(ctx, SWGB_EINVAL, "sequence set of another context");
+    if (q->device != ctx->device || r->device != ctx->device)
+        return fail(ctx, SWGB_EINVAL, "sequence set on another device");
     return SWGB_OK;
 }
 

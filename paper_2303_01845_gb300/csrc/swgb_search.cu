@@ -443,17 +443,33 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
 // ---------------------------------------------------------------------------
 // Identity of alignment records
 // ---------------------------------------------------------------------------
-// Decision bits of one cell (a, b) of the span's global DP, 4 per cell:
-//   bits 0-1: source of H -- 0 diagonal, 1 F (query residue against a gap),
-//             2 E (gap against a reference residue), by the preference order;
-//   bit 2:    F(a, b) opens its gap (F = H(a-1, b) - o - e);
-//   bit 3:    E(a, b) opens its gap (E = H(a, b-1) - o - e).
-// Layout per pair: rows a = 1..n of words; a row holds nch * 32 words, lane k
-// of chunk c writing word c * 32 + k for columns c*256 + k*8 + 1 .. +8.
+// The traceback of the span's global DP (diagonal first, then F, then E;
+// inside a gap its opening first) makes only local choices, so the
+// statistics (identical columns, diagonal steps) of the path it follows from
+// any cell and state are those of the cell it steps to plus its own step:
+//   SF(a,b) = F opens ? SH(a-1,b) : SF(a-1,b)
+//   SE(a,b) = E opens ? SH(a,b-1) : SE(a,b-1)
+//   SH(a,b) = H = H(a-1,b-1) + s ? SH(a-1,b-1) + ([q_a = r_b], 1)
+//           : H = F(a,b) ? SF(a,b) : SE(a,b)
+// with zero at the borders (gaps only); the answer is SH(n, m), and a path
+// from (0, 0) to (n, m) with D diagonal steps has n + m - D columns.  The wavefront below computes H, E, F and these pairs
+// forward, one warp per pair: lane k holds kIdR columns of a chunk of 32 kIdR
+// columns and streams the span's query rows (row t - k + 1 at step t), the
+// left inputs of its first column arriving from lane k - 1 by shuffle and,
+// for lane 0 of a later chunk, from the boundary column the previous chunk
+// left in global memory.
 constexpr int kIdR = 8;                        // columns per lane
-constexpr int kIdChunk = 32 * kIdR;            // columns per chunk
 constexpr int kIdWarps = 4;                    // warps per block
+constexpr int kIdSmallCols = 64;               // spans of up to 64 columns: 8-lane groups
+constexpr int kIdMidCols = 128;                // up to 128 columns: 16-lane groups
+constexpr int kIdClasses = 4;
 constexpr int32_t kNegInf = -(1 << 28);
+
+// A chunk's last column at one row: H, E and the (matches, columns) of H and E.
+struct IdBnd {
+    int32_t h, e;
+    uint64_t sh, se;
+};
 
 struct IdentArgs {
     SeqView q, r;
@@ -464,215 +480,258 @@ struct IdentArgs {
     int32_t go, ge;
     int32_t id_num, id_den, cov_num, cov_den;
     int32_t* out;              // [n_pairs][3]: matches, columns, pass
-    uint32_t* dir;             // per-warp regions of region_words words
-    int64_t region_words;
-    int64_t min_words, max_words;   // this launch takes pairs with min < need <= max
-    int2* bnd;                 // per-warp chunk-boundary rows, bnd_stride entries each
+    IdBnd* bnd;                // per-warp boundary columns, one entry per row
     int64_t bnd_stride;
-    unsigned long long* ctr;
-    unsigned long long* stats; // [0] max need (words), [1] pairs above the small class
+    const int64_t* list;       // the pairs of this launch's class
+    int64_t n_list;
+    int64_t* lists;            // classification: kIdClasses lists of n_pairs entries
+    unsigned long long* ctr;   // [0] task counter, [1..kIdClasses] list sizes
     int32_t* status;
-    int64_t* large;            // [n_pairs] the pairs above the small class
-    int64_t n_tasks;           // large launch: tasks are large[0, n_tasks); else all pairs
 };
 
-// words of decision bits of a record's span (0 when there is nothing to trace)
-__device__ __forceinline__ int64_t ident_need(const swgb_record& rc) {
-    if (rc.score <= 0) return 0;
-    const int64_t n = (int64_t)rc.q_end - rc.q_start + 1, m = (int64_t)rc.r_end - rc.r_start + 1;
-    if (n <= 0 || m <= 0) return 0;
-    return n * ((m + kIdChunk - 1) / kIdChunk) * 32;
+// prmt.b32 in its default mode: a selector nibble with bit 3 set replicates
+// the sign of the byte it selects (the C intrinsic __byte_perm ignores that bit)
+__device__ __forceinline__ uint32_t prmt_sext(uint32_t a, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(a), "r"(sel));
+    return d;
 }
 
-// Largest need, and the pairs above the small class appended to a.large
-// (their count in stats[1]).
-__global__ void ident_need_kernel(IdentArgs a, int64_t small_words) {
+// (matches, diagonal steps): packed 16 / 16 bits in a uint32_t when the span
+// has fewer than 65536 rows + columns, else 32 / 32 bits in a uint64_t.
+template <class St>
+struct Stat;
+template <>
+struct Stat<uint32_t> {
+    __device__ static uint32_t make(uint32_t m, uint32_t c) { return (m << 16) | c; }
+    __device__ static uint32_t inc(bool match) { return match ? 0x10001u : 1u; }
+    __device__ static uint32_t matches(uint32_t s) { return s >> 16; }
+    __device__ static uint32_t columns(uint32_t s) { return s & 0xffffu; }
+    __device__ static uint64_t wide(uint32_t s) { return ((uint64_t)(s >> 16) << 32) | (s & 0xffffu); }
+    __device__ static uint32_t narrow(uint64_t w) { return ((uint32_t)(w >> 32) << 16) | (uint32_t)(w & 0xffffu); }
+};
+template <>
+struct Stat<uint64_t> {
+    __device__ static uint64_t make(uint32_t m, uint32_t c) { return ((uint64_t)m << 32) | c; }
+    __device__ static uint64_t inc(bool match) { return match ? 0x100000001ull : 1ull; }
+    __device__ static uint32_t matches(uint64_t s) { return (uint32_t)(s >> 32); }
+    __device__ static uint32_t columns(uint64_t s) { return (uint32_t)s; }
+    __device__ static uint64_t wide(uint64_t s) { return s; }
+    __device__ static uint64_t narrow(uint64_t w) { return w; }
+};
+
+__device__ __forceinline__ void ident_write(const IdentArgs& a, int64_t p, int32_t mt, int32_t cols,
+                                            int32_t pass) {
+    a.out[3 * p] = mt;
+    a.out[3 * p + 1] = cols;
+    a.out[3 * p + 2] = pass;
+}
+
+// Classes (rows + columns < 65536): 0 = at most kIdSmallCols columns, 1 = at
+// most kIdMidCols, 2 = more; 3 = rows + columns >= 65536.  Zero scores and
+// records outside their sequences are answered here.
+__global__ void ident_classify_kernel(IdentArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_pairs; p += stride) {
-        const int64_t w = ident_need(a.rec[p]);
-        if (w > 0) {
-            atomicMax(&a.stats[0], (unsigned long long)w);
-            if (w > small_words) a.large[atomicAdd(&a.stats[1], 1ull)] = p;
+        const swgb_record rc = a.rec[p];
+        if (rc.score <= 0) {
+            ident_write(a, p, 0, 0, 0);
+            continue;
         }
+        const int32_t qi = a.pairs[2 * p], ri = a.pairs[2 * p + 1];
+        const bool ok_idx = qi >= 0 && qi < a.q.n && ri >= 0 && ri < a.r.n;
+        const int64_t lq = ok_idx ? a.q.off[qi + 1] - a.q.off[qi] : 0;
+        const int64_t lr = ok_idx ? a.r.off[ri + 1] - a.r.off[ri] : 0;
+        const int64_t n = (int64_t)rc.q_end - rc.q_start + 1, m = (int64_t)rc.r_end - rc.r_start + 1;
+        if (!ok_idx || rc.q_start < 0 || rc.q_end >= lq || rc.r_start < 0 || rc.r_end >= lr ||
+            n <= 0 || m <= 0 || n >= a.bnd_stride) {
+            atomicMax(a.status, 3);
+            ident_write(a, p, -1, -1, 0);
+            continue;
+        }
+        const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
+        a.lists[cls * a.n_pairs + (int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
     }
 }
 
+// The wavefront of groups of G lanes, one pair per group (G = 8: four pairs
+// per warp, one chunk of 64 columns; G = 32: one pair per warp, chunks of 256
+// columns).  PROF: lane-private substitution profile in shared memory
+// (prof[letter] = the 8 scores of the lane's columns) instead of one lookup
+// per cell.
+template <int G, class St, bool PROF>
 __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
+    constexpr int GROUPS = 32 / G;
+    constexpr int CHUNK = G * kIdR;
     __shared__ int8_t s_mat[kAlpha * kAlpha];
+    __shared__ __align__(8) uint2 s_prof[PROF ? kIdWarps * 32 * kAlpha : 1];
     for (int t = threadIdx.x; t < kAlpha * kAlpha; t += blockDim.x) s_mat[t] = a.mat[t];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * kIdWarps + (threadIdx.x >> 5);
-    uint32_t* dir = a.dir + gw * a.region_words;
-    int2* bnd = a.bnd + gw * a.bnd_stride;
-    const int32_t go = a.go, ge = a.ge, oe = go + ge;
+    using S = Stat<St>;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    const int64_t gw = (int64_t)blockIdx.x * kIdWarps + w;
+    IdBnd* bnd = a.bnd + gw * a.bnd_stride;
+    uint2* prof = s_prof + (PROF ? (w * 32 + lane) * kAlpha : 0);
+    const int32_t ge = a.ge, oe = a.go + a.ge;
     for (;;) {
-        int64_t p = 0;
-        if (lane == 0) p = (int64_t)atomicAdd(a.ctr, 1ull);
-        p = __shfl_sync(0xffffffffu, p, 0);
-        if (p >= a.n_tasks) break;
-        if (a.min_words > 0) p = a.large[p];
-        const swgb_record rc = a.rec[p];
-        const int64_t need = ident_need(rc);
-        const bool mine = need > a.min_words && need <= a.max_words;
-        if (need == 0) {
-            // nothing to trace: the smallest class writes the zero result
-            if (a.min_words == 0 && lane == 0) {
-                a.out[3 * p] = 0;
-                a.out[3 * p + 1] = 0;
-                a.out[3 * p + 2] = 0;
-            }
-            continue;
+        int64_t task = 0;
+        if (lane == 0) task = (int64_t)atomicAdd(a.ctr, 1ull);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        const int64_t first = task * GROUPS;
+        if (first >= a.n_list) break;
+        // this group's pair (groups past the list compute nothing)
+        const int64_t li = first + grp;
+        const bool live = li < a.n_list;
+        const int64_t p = live ? a.list[li] : 0;
+        swgb_record rc{0, 0, 0, 0, 0};
+        int n = 0, m = 0, lq = 0, lr = 0;
+        const uint8_t *qs = nullptr, *rs = nullptr;
+        if (live) {
+            rc = a.rec[p];
+            const int32_t qi = a.pairs[2 * p], ri = a.pairs[2 * p + 1];
+            lq = (int)(a.q.off[qi + 1] - a.q.off[qi]);
+            lr = (int)(a.r.off[ri + 1] - a.r.off[ri]);
+            n = rc.q_end - rc.q_start + 1;
+            m = rc.r_end - rc.r_start + 1;
+            qs = a.q.res + a.q.off[qi] + rc.q_start;
+            rs = a.r.res + a.r.off[ri] + rc.r_start;
         }
-        if (!mine) continue;
-        const int32_t qi = a.pairs[2 * p], ri = a.pairs[2 * p + 1];
-        // a record must lie inside its pair's sequences
-        const bool ok_idx = qi >= 0 && qi < a.q.n && ri >= 0 && ri < a.r.n;
-        const int lq = ok_idx ? (int)(a.q.off[qi + 1] - a.q.off[qi]) : 0;
-        const int lr = ok_idx ? (int)(a.r.off[ri + 1] - a.r.off[ri]) : 0;
-        if (!ok_idx || rc.q_start < 0 || rc.q_end >= lq || rc.r_start < 0 || rc.r_end >= lr) {
-            if (lane == 0) {
-                atomicMax(a.status, 3);
-                a.out[3 * p] = -1;
-                a.out[3 * p + 1] = -1;
-                a.out[3 * p + 2] = 0;
-            }
-            continue;
+        // warp-uniform extents
+        int n_w = n, nch_w = (m + CHUNK - 1) / CHUNK;
+        for (int d = 16; d; d >>= 1) {
+            n_w = max(n_w, __shfl_xor_sync(0xffffffffu, n_w, d));
+            nch_w = max(nch_w, __shfl_xor_sync(0xffffffffu, nch_w, d));
         }
-        const uint8_t* qs = a.q.res + a.q.off[qi] + rc.q_start;
-        const uint8_t* rs = a.r.res + a.r.off[ri] + rc.r_start;
-        const int n = rc.q_end - rc.q_start + 1, m = rc.r_end - rc.r_start + 1;
-        const int nch = (m + kIdChunk - 1) / kIdChunk;
-        const int64_t row_words = (int64_t)nch * 32;
-        int32_t hnm = kNegInf;   // H(n, m), held by the lane owning column m
-        for (int c = 0; c < nch; ++c) {
-            // this lane's columns b = c0 + 1 .. c0 + kIdR (1-based)
-            const int c0 = c * kIdChunk + lane * kIdR;
+        int32_t hnm = kNegInf;
+        St snm = 0;
+        for (int c = 0; c < nch_w; ++c) {
+            const int c0 = c * CHUNK + gl * kIdR;
             int rcode[kIdR];
             int32_t H[kIdR], F[kIdR];
+            St SH[kIdR], SF[kIdR];
 #pragma unroll
             for (int x = 0; x < kIdR; ++x) {
                 const int b = c0 + x + 1;
                 rcode[x] = b <= m ? rs[b - 1] : 0;
-                H[x] = -(oe + ge * (b - 1));     // H(0, b)
-                F[x] = kNegInf;                  // F(0, b)
+                H[x] = -(oe + ge * (b - 1));
+                F[x] = kNegInf;
+                SH[x] = 0;
+                SF[x] = 0;
             }
-            // This lane's outputs of the previous step (its last column's H and
-            // E), before its first row: H(0, c0 + kIdR), the diagonal of lane
-            // k+1's first row.
+            if (PROF) {
+                __syncwarp();
+                for (int l = 0; l < kAlpha; ++l) {
+                    uint32_t lo = 0, hi = 0;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        lo |= (uint32_t)(uint8_t)s_mat[l * kAlpha + rcode[x]] << (8 * x);
+                        hi |= (uint32_t)(uint8_t)s_mat[l * kAlpha + rcode[x + 4]] << (8 * x);
+                    }
+                    prof[l] = make_uint2(lo, hi);
+                }
+                __syncwarp();
+            }
             int32_t h_out = -(oe + ge * (c0 + kIdR - 1)), e_out = kNegInf;
-            // lanes > 0: what lane-1 sent one step ago (the next diagonal);
-            // lane 0: H(a - 1, c * kIdChunk), from the border or the boundary row
+            St sh_out = 0, se_out = 0;
             int32_t hd_next = c0 == 0 ? 0 : -(oe + ge * (c0 - 1));
-            for (int t = 0; t < n + 31; ++t) {
-                const int arow = t - lane + 1;   // row of this lane at step t
-                // lane-1's last column of its row at step t-1, which is row arow
-                const int32_t up_h = __shfl_up_sync(0xffffffffu, h_out, 1);
-                const int32_t up_e = __shfl_up_sync(0xffffffffu, e_out, 1);
+            St sd_next = 0;
+            const bool read_b = G == 32 && c > 0 && gl == 0;
+            for (int t = 0; t < n_w + G - 1; ++t) {
+                const int arow = t - gl + 1;
+                const int32_t up_h = __shfl_up_sync(0xffffffffu, h_out, 1, G);
+                const int32_t up_e = __shfl_up_sync(0xffffffffu, e_out, 1, G);
+                const St up_sh = __shfl_up_sync(0xffffffffu, sh_out, 1, G);
+                const St up_se = __shfl_up_sync(0xffffffffu, se_out, 1, G);
                 int32_t hl = up_h, el = up_e;
+                St shl = up_sh, sel = up_se;
                 const int32_t hd = hd_next;
-                if (lane == 0) {
-                    if (c == 0) {
+                const St sd = sd_next;
+                if (gl == 0) {
+                    if (!read_b) {
                         hl = -(oe + ge * (arow - 1));   // H(a, 0)
-                        el = kNegInf;                   // E(a, 0)
+                        el = kNegInf;
+                        shl = 0;
+                        sel = 0;
                     } else if (arow >= 1 && arow <= n) {
-                        const int2 v = bnd[arow];
-                        hl = v.x;
-                        el = v.y;
+                        const IdBnd v = bnd[arow];
+                        hl = v.h;
+                        el = v.e;
+                        shl = S::narrow(v.sh);
+                        sel = S::narrow(v.se);
                     }
                 }
-                if (arow >= 1 && arow <= n) {
+                if (arow >= 1 && arow <= n && c0 < m) {
                     const int qc = qs[arow - 1];
-                    const int8_t* srow = s_mat + qc * kAlpha;
-                    uint32_t word = 0;
+                    uint2 pw = make_uint2(0u, 0u);
+                    if (PROF) pw = prof[qc];
                     int32_t hleft = hl, eleft = el, hdiag = hd;
+                    St shleft = shl, seleft = sel, sdiag = sd;
 #pragma unroll
                     for (int x = 0; x < kIdR; ++x) {
-                        const int32_t eo_v = hleft - oe, ee_v = eleft - ge;
-                        const int32_t e = max(eo_v, ee_v);
-                        const uint32_t eopen = eo_v >= ee_v;
-                        const int32_t fo_v = H[x] - oe, fe_v = F[x] - ge;
-                        const int32_t f = max(fo_v, fe_v);
-                        const uint32_t fopen = fo_v >= fe_v;
-                        const int32_t d = hdiag + srow[rcode[x]];
-                        const int32_t h = max(d, max(e, f));
-                        const uint32_t src = h == d ? 0u : (h == f ? 1u : 2u);
-                        word |= (src | (fopen << 2) | (eopen << 3)) << (4 * x);
+                        const int32_t eo = hleft - oe;
+                        const int32_t e = __viaddmax_s32(eleft, -ge, eo);
+                        const St se = e == eo ? shleft : seleft;
+                        const int32_t fo = H[x] - oe;
+                        const int32_t f = __viaddmax_s32(F[x], -ge, fo);
+                        const St sf = f == fo ? SH[x] : SF[x];
+                        // byte x % 4 of the profile word, sign-extended (one byte permute)
+                        const uint32_t xb = (uint32_t)(x & 3);   // a constant once unrolled
+                        const uint32_t sel8 = xb | ((xb | 8u) << 4) | ((xb | 8u) << 8) | ((xb | 8u) << 12);
+                        const int32_t s = PROF ? (int32_t)prmt_sext(x < 4 ? pw.x : pw.y, sel8)
+                                               : (int32_t)s_mat[qc * kAlpha + rcode[x]];
+                        const int32_t d = hdiag + s;
+                        const int32_t h = __vimax3_s32(d, e, f);
+                        const St salt = h == f ? sf : se;
+                        const St sh = h == d ? sdiag + S::inc(qc == rcode[x]) : salt;
                         hdiag = H[x];
+                        sdiag = SH[x];
                         H[x] = h;
                         F[x] = f;
+                        SH[x] = sh;
+                        SF[x] = sf;
                         hleft = h;
                         eleft = e;
+                        shleft = sh;
+                        seleft = se;
                     }
-                    dir[(int64_t)(arow - 1) * row_words + c * 32 + lane] = word;
                     h_out = hleft;
                     e_out = eleft;
-                    if (lane == 31 && c + 1 < nch) bnd[arow] = make_int2(hleft, eleft);
+                    sh_out = shleft;
+                    se_out = seleft;
+                    if (G == 32 && gl == 31 && c + 1 < nch_w)
+                        bnd[arow] = IdBnd{hleft, eleft, S::wide(shleft), S::wide(seleft)};
                     if (arow == n && m > c0 && m <= c0 + kIdR) {
 #pragma unroll
                         for (int x = 0; x < kIdR; ++x)
-                            if (c0 + x + 1 == m) hnm = H[x];
+                            if (c0 + x + 1 == m) {
+                                hnm = H[x];
+                                snm = SH[x];
+                            }
                     }
                 }
-                // the next row's diagonal: lane-1's value received now (row
-                // arow), or for lane 0 this row's left input
-                hd_next = lane == 0 ? hl : up_h;
+                hd_next = gl == 0 ? hl : up_h;
+                sd_next = gl == 0 ? shl : up_sh;
             }
-            // chunk c's boundary row must be complete before chunk c + 1 reads it
             __syncwarp();
         }
-        // H(n, m) must equal the record's score
-        const int32_t hv = __reduce_max_sync(0xffffffffu, hnm);
-        if (hv != rc.score) {
-            if (lane == 0) {
+        // the lane owning (n, m) answers for its group
+        if (live && hnm != kNegInf) {
+            if (hnm != rc.score) {
                 atomicMax(a.status, 2);
-                a.out[3 * p] = -1;
-                a.out[3 * p + 1] = -1;
-                a.out[3 * p + 2] = 0;
+                ident_write(a, p, -1, -1, 0);
+            } else {
+                const int32_t mt = (int32_t)S::matches(snm);
+                const int32_t cols = n + m - (int32_t)S::columns(snm);   // minus diagonal steps
+                const bool pass = cols > 0 && (int64_t)mt * a.id_den >= (int64_t)a.id_num * cols &&
+                                  (int64_t)n * a.cov_den >= (int64_t)a.cov_num * lq &&
+                                  (int64_t)m * a.cov_den >= (int64_t)a.cov_num * lr;
+                ident_write(a, p, mt, cols, pass ? 1 : 0);
             }
-            continue;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            int ai = n, bi = m, state = 0;
-            int32_t mt = 0, cols = 0;
-            for (int guard = 0; guard < 2 * (n + m) + 2 && (ai > 0 || bi > 0); ++guard) {
-                if (ai == 0) { cols += bi; bi = 0; break; }
-                if (bi == 0) { cols += ai; ai = 0; break; }
-                const uint32_t w = dir[(int64_t)(ai - 1) * row_words + (bi - 1) / kIdR];
-                const uint32_t bits = (w >> (4 * ((bi - 1) % kIdR))) & 15u;
-                if (state == 0) {
-                    const uint32_t src = bits & 3u;
-                    if (src == 0) {
-                        mt += qs[ai - 1] == rs[bi - 1];
-                        ++cols;
-                        --ai;
-                        --bi;
-                    } else {
-                        state = src == 1 ? 1 : 2;
-                    }
-                } else if (state == 1) {
-                    ++cols;
-                    state = (bits & 4u) ? 0 : 1;
-                    --ai;
-                } else {
-                    ++cols;
-                    state = (bits & 8u) ? 0 : 2;
-                    --bi;
-                }
-            }
-            const int64_t sq = n, sr = m;
-            const bool pass = cols > 0 && (int64_t)mt * a.id_den >= (int64_t)a.id_num * cols &&
-                              sq * a.cov_den >= (int64_t)a.cov_num * lq &&
-                              sr * a.cov_den >= (int64_t)a.cov_num * lr;
-            a.out[3 * p] = mt;
-            a.out[3 * p + 1] = cols;
-            a.out[3 * p + 2] = pass ? 1 : 0;
         }
         __syncwarp();
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // Pair features of the learned candidate filter
@@ -688,8 +747,9 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
 constexpr int kFeat = 32;
 constexpr int kFeatBins = 24;
 constexpr int kFeatWarps = 8;
-constexpr int kFeatSlots = 4096;     // shared-memory table of K(i): up to 2048 k-mers
-constexpr int kFeatChunk = 64;       // consecutive pairs per task
+constexpr int kFeatWarpSlots = 1024;  // warp-private shared table of K(i): up to 512 k-mers
+constexpr int kFeatSmemBytes = kFeatWarps * kFeatWarpSlots * 8;
+constexpr int kFeatChunk = 32;        // consecutive pairs per warp task
 
 struct FeatArgs {
     SeqView A, B;
@@ -700,7 +760,7 @@ struct FeatArgs {
     const int32_t* pairs;
     int64_t n_pairs;
     float* out;                            // [n_pairs][32]
-    uint32_t* gtab;                        // per-block global tables (keys, positions)
+    uint32_t* gtab;                        // per-warp global tables (keys, positions)
     uint32_t gslots;
     unsigned long long* ctr;
     int32_t* status;
@@ -727,14 +787,20 @@ __device__ __forceinline__ float feat_ratio(int64_t num, int64_t den) {
     return den == 0 ? 0.0f : __double2float_rn((double)num / (double)den);
 }
 
+// One warp per task of kFeatChunk consecutive pairs; for each run of pairs
+// with the same first index i it builds K(i) (k-mer -> first position) in a
+// warp-private hash table and probes every partner's k-mers against it.
 __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
-    __shared__ uint32_t s_keys[kFeatSlots];
-    __shared__ uint32_t s_pos[kFeatSlots];
+    extern __shared__ __align__(16) uint32_t s_tab[];
     __shared__ uint32_t s_hist[kFeatWarps][kFeatBins];
-    __shared__ int64_t s_task;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* const s_keys = s_tab + w * 2 * kFeatWarpSlots;
+    uint32_t* const g_keys = a.gtab ? a.gtab + ((size_t)blockIdx.x * kFeatWarps + w) * 2 * a.gslots
+                                    : nullptr;
     for (;;) {
-        const int64_t t0 = next_task(a.ctr, &s_task) * kFeatChunk;
+        int64_t task = 0;
+        if (lane == 0) task = (int64_t)atomicAdd(a.ctr, 1ull);
+        const int64_t t0 = __shfl_sync(0xffffffffu, task, 0) * kFeatChunk;
         if (t0 >= a.n_pairs) break;
         const int64_t t1 = min(t0 + (int64_t)kFeatChunk, a.n_pairs);
         int64_t p0 = t0;
@@ -746,22 +812,21 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
             const uint32_t ni = ok_i ? a.cntA[i] : 0u;
             const uint32_t cap = pow2_at_least(2ull * ni);
             uint32_t* keys = s_keys;
-            uint32_t* pos = s_pos;
-            bool table_ok = true;
-            if (cap > (uint32_t)kFeatSlots) {
-                if (cap > a.gslots) {
-                    table_ok = false;
-                } else {
-                    keys = a.gtab + (size_t)blockIdx.x * 2 * a.gslots;
-                    pos = keys + a.gslots;
-                }
+            uint32_t* pos;
+            uint32_t tcap = kFeatWarpSlots;
+            if (cap > (uint32_t)kFeatWarpSlots) {
+                keys = g_keys;
+                tcap = a.gslots;
             }
+            const bool table_ok = cap <= tcap && keys != nullptr;
+            pos = keys + tcap;
             const uint32_t mask = cap - 1;
+            __syncwarp();
             if (table_ok) {
-                for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) keys[s] = kEmpty;
-                __syncthreads();
-                const int64_t oi = ok_i ? a.A.off[i] : 0;
-                for (uint32_t e = threadIdx.x; e < ni; e += blockDim.x) {
+                for (uint32_t s = lane; s < cap; s += 32) keys[s] = kEmpty;
+                __syncwarp();
+                const int64_t oi = a.A.off[i];
+                for (uint32_t e = lane; e < ni; e += 32) {
                     const uint32_t x = a.kmA[oi + e];
                     uint32_t h = slot_of(x, mask);
                     for (uint32_t probe = 0; probe < cap; ++probe) {
@@ -772,9 +837,9 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                         h = (h + 1) & mask;
                     }
                 }
+                __syncwarp();
             }
-            __syncthreads();
-            for (int64_t p = p0 + w; p < p1; p += kFeatWarps) {
+            for (int64_t p = p0; p < p1; ++p) {
                 const int32_t j = a.pairs[2 * p + 1];
                 float* o = a.out + p * kFeat;
                 if (!ok_i || j < 0 || j >= a.B.n || !table_ok) {
@@ -790,21 +855,29 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 __syncwarp();
                 int c = 0;
                 int64_t dmin = INT64_MAX, dmax = INT64_MIN;
-                for (uint32_t e = lane; e < nj; e += 32) {
-                    const uint32_t x = a.kmB[oj + e];
-                    uint32_t h = slot_of(x, mask);
-                    for (uint32_t probe = 0; probe < cap; ++probe) {
-                        const uint32_t key = keys[h];
-                        if (key == x) {
-                            const int64_t d = (int64_t)pos[h] - (int64_t)a.posB[oj + e];
-                            atomicAdd(&s_hist[w][(kFeatBins * (d + lj - a.k)) / D], 1u);
-                            ++c;
-                            dmin = min(dmin, d);
-                            dmax = max(dmax, d);
-                            break;
+                // two probes in flight per lane
+                for (uint32_t e0 = lane; e0 < nj; e0 += 64) {
+                    uint32_t xs[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) xs[u] = e0 + 32 * u < nj ? a.kmB[oj + e0 + 32 * u] : kEmpty;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const uint32_t x = xs[u];
+                        if (x == kEmpty) continue;
+                        uint32_t h = slot_of(x, mask);
+                        for (uint32_t probe = 0; probe < cap; ++probe) {
+                            const uint32_t key = keys[h];
+                            if (key == x) {
+                                const int64_t d = (int64_t)pos[h] - (int64_t)a.posB[oj + e0 + 32 * u];
+                                atomicAdd(&s_hist[w][(kFeatBins * (d + lj - a.k)) / D], 1u);
+                                ++c;
+                                dmin = min(dmin, d);
+                                dmax = max(dmax, d);
+                                break;
+                            }
+                            if (key == kEmpty) break;
+                            h = (h + 1) & mask;
                         }
-                        if (key == kEmpty) break;
-                        h = (h + 1) & mask;
                     }
                 }
                 for (int s = 16; s; s >>= 1) {
@@ -837,7 +910,6 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 o[lane] = f;
                 __syncwarp();
             }
-            __syncthreads();
             p0 = p1;
         }
     }
@@ -885,9 +957,8 @@ struct SearchStore {
     uint64_t* coff = nullptr;     int64_t coff_cap = 0;
     uint64_t* part = nullptr;     int64_t part_cap = 0;
     uint32_t* gtab = nullptr;     int64_t gtab_cap = 0;
-    uint32_t* dir = nullptr;      int64_t dir_cap = 0;
-    int2* bnd = nullptr;          int64_t bnd_cap = 0;
-    int64_t* large = nullptr;     int64_t large_cap = 0;
+    IdBnd* bnd = nullptr;         int64_t bnd_cap = 0;
+    int64_t* lists = nullptr;     int64_t lists_cap = 0;
     int32_t* large_rows = nullptr; int64_t large_rows_cap = 0;
     // pair features: k-mer sets of a second set, letter counts of both
     uint32_t* ent2_kmer = nullptr; int64_t ent2_cap = 0;
@@ -904,8 +975,8 @@ void search_store_free(SearchStore* s) {
     if (!s) return;
     cudaSetDevice(s->device);
     void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq, s->bpos,
-                    s->need, s->ccount, s->coff, s->part, s->gtab, s->dir, s->bnd, s->ctr,
-                    s->status, s->large, s->large_rows, s->ent2_kmer, s->ent2_pos, s->kcount2,
+                    s->need, s->ccount, s->coff, s->part, s->gtab, s->bnd, s->ctr,
+                    s->status, s->large_rows, s->lists, s->ent2_kmer, s->ent2_pos, s->kcount2,
                     s->comp, s->comp2, s->flags};
     for (void* p : ptrs) cudaFree(p);
     delete s;
@@ -926,6 +997,9 @@ int search_store(swgb_ctx* ctx, SearchStore** out) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(join_kernel<false, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kJoinSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kFeatSmemBytes);
         if (e != cudaSuccess) {
             search_store_free(s);
             return cuda_fail(ctx, e, "search scratch");
@@ -1333,61 +1407,54 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     a.cov_den = th->cov_den;
     a.out = reinterpret_cast<int32_t*>(out);
     a.status = S->status;
-    a.stats = S->ctr + 4;
-    // small class: spans of up to kSmallWords words per warp
-    constexpr int64_t kSmallWords = 1 << 16;   // e.g. 512 x 1024 cells
-    CK(grow(&S->large, &S->large_cap, n_pairs), "identity scratch");
-    a.large = S->large;
-    a.n_tasks = n_pairs;
+    // one boundary column per resident warp of the large classes (rows of the
+    // longest query + 1)
+    const int64_t max_rows = queries->max_len + 1;
+    a.bnd_stride = max_rows;
+    CK(grow(&S->lists, &S->lists_cap, (int64_t)kIdClasses * n_pairs), "identity scratch");
+    a.lists = S->lists;
+    a.ctr = S->ctr;
     CK(cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * 8, st), "memset");
     CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
     const int64_t g = std::min<int64_t>((n_pairs + 255) / 256, (int64_t)ctx->sm_count * 16);
-    ident_need_kernel<<<(unsigned)g, 256, 0, st>>>(a, kSmallWords);
-    CK(cudaGetLastError(), "ident_need kernel");
-    unsigned long long stats[2] = {0, 0};
-    CK(cudaMemcpyAsync(stats, S->ctr + 4, sizeof(stats), cudaMemcpyDeviceToHost, st), "stats D2H");
+    ident_classify_kernel<<<(unsigned)g, 256, 0, st>>>(a);
+    CK(cudaGetLastError(), "ident_classify kernel");
+    unsigned long long sizes[kIdClasses] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(sizes, S->ctr + 1, sizeof(sizes), cudaMemcpyDeviceToHost, st), "sizes D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    const int64_t max_need = (int64_t)stats[0], n_large = (int64_t)stats[1];
-    const int64_t max_rows = std::max(queries->max_len, refs->max_len) + 1;
-    const int small_blocks = ctx->sm_count * 8;
-    int large_blocks = 0;
-    int64_t large_words = 0;
-    if (n_large > 0) {
-        large_words = max_need;
-        const int64_t budget = (int64_t)1 << 31;   // 8 GiB of words
-        const int64_t warps = std::max<int64_t>(1, std::min<int64_t>(
-            std::min<int64_t>(n_large, (int64_t)ctx->sm_count * kIdWarps), budget / large_words));
-        large_blocks = (int)((warps + kIdWarps - 1) / kIdWarps);
+    int32_t launches = 1;
+    const int64_t resident_blocks = (int64_t)ctx->sm_count * 8;
+    const int pairs_per_warp[kIdClasses] = {4, 2, 1, 1};
+    int blocks_of[kIdClasses] = {0, 0, 0, 0};
+    int64_t bnd_warps = 0;
+    for (int cls = 0; cls < kIdClasses; ++cls) {
+        const int64_t tasks = ((int64_t)sizes[cls] + pairs_per_warp[cls] - 1) / pairs_per_warp[cls];
+        blocks_of[cls] = (int)std::min<int64_t>((tasks + kIdWarps - 1) / kIdWarps, resident_blocks);
+        // every warp of a chunked (32-lane) launch owns a boundary column
+        if (cls >= 2) bnd_warps = std::max<int64_t>(bnd_warps, (int64_t)blocks_of[cls] * kIdWarps);
     }
-    const int64_t small_warps = (int64_t)small_blocks * kIdWarps;
-    const int64_t large_warps = (int64_t)large_blocks * kIdWarps;
-    CK(grow(&S->dir, &S->dir_cap, small_warps * kSmallWords + large_warps * large_words), "identity scratch");
-    CK(grow(&S->bnd, &S->bnd_cap, (small_warps + large_warps) * max_rows), "identity scratch");
-    a.bnd_stride = max_rows;
-    a.dir = S->dir;
+    if (bnd_warps > 0) CK(grow(&S->bnd, &S->bnd_cap, bnd_warps * max_rows), "identity scratch");
     a.bnd = S->bnd;
-    a.region_words = kSmallWords;
-    a.min_words = 0;
-    a.max_words = kSmallWords;
-    a.ctr = S->ctr + 0;
-    ident_kernel<<<small_blocks, kIdWarps * 32, 0, st>>>(a);
-    CK(cudaGetLastError(), "ident kernel");
-    if (large_blocks) {
+    for (int cls = 0; cls < kIdClasses; ++cls) {
+        if (sizes[cls] == 0) continue;
         IdentArgs b = a;
-        b.dir = S->dir + small_warps * kSmallWords;
-        b.bnd = S->bnd + small_warps * max_rows;
-        b.region_words = large_words;
-        b.min_words = kSmallWords;
-        b.max_words = large_words;
-        b.n_tasks = n_large;
-        b.ctr = S->ctr + 1;
-        ident_kernel<<<large_blocks, kIdWarps * 32, 0, st>>>(b);
-        CK(cudaGetLastError(), "ident kernel (large spans)");
+        b.list = S->lists + cls * n_pairs;
+        b.n_list = (int64_t)sizes[cls];
+        const int blocks = blocks_of[cls];
+        // the launches of the classes run in stream order and share one work counter
+        CK(cudaMemsetAsync(S->ctr + 7, 0, sizeof(unsigned long long), st), "memset");
+        b.ctr = S->ctr + 7;
+        if (cls == 0) ident_kernel<8, uint32_t, false><<<blocks, kIdWarps * 32, 0, st>>>(b);
+        else if (cls == 1) ident_kernel<16, uint32_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
+        else if (cls == 2) ident_kernel<32, uint32_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
+        else ident_kernel<32, uint64_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
+        CK(cudaGetLastError(), "ident kernel");
+        launches += 1;
     }
     int32_t status = 0;
     CK(cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st), "status D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    ctx->last_search_launches = 2 + (large_blocks ? 1 : 0);
+    ctx->last_search_launches = launches;
     if (status == 3) return fail(ctx, SWGB_ERANGE, "identity: a pair index or record outside its sequences");
     if (status) return fail(ctx, SWGB_EINTERNAL, "identity: a span's global optimum differs from its record's score");
     return SWGB_OK;
@@ -1403,13 +1470,17 @@ int run_features(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set_a, const 
                  float* out, int32_t* launches, cudaStream_t st) {
     // global hash tables: the k-mer sets of A (and B) and the feature
     // kernel's table of K(i), reserved before any launch
-    const int blocks = ctx->sm_count * 2;
+    const int blocks = ctx->sm_count * 3;
     const int64_t longest = std::max<int64_t>(set_a->max_len, b_is_a ? 0 : set_b->max_len);
     uint32_t gslots = 0;
     int rc = reserve_set_tables(ctx, S, longest, &gslots);
     if (rc) return rc;
-    if (gslots > (uint32_t)kFeatSlots)
-        CK(grow(&S->gtab, &S->gtab_cap, (int64_t)blocks * 2 * gslots), "features scratch");
+    // per-warp global tables of rows above the shared-memory class
+    const uint32_t fslots = pow2_at_least((uint64_t)std::max<int64_t>(set_a->max_len, 1) * 2);
+    if (fslots > (uint32_t)kFeatWarpSlots)
+        CK(grow(&S->gtab, &S->gtab_cap,
+                std::max<int64_t>((int64_t)blocks * kFeatWarps * 2 * fslots,
+                                  (int64_t)ctx->sm_count * 4 * 2 * gslots)), "features scratch");
     const int64_t total = std::max<int64_t>(set_a->total, 1), n = std::max<int64_t>(set_a->n, 1);
     CK(grow(&S->ent_kmer, &S->ent_cap, total), "features scratch");
     CK(grow(&S->ent_pos, &S->entp_cap, total), "features scratch");
@@ -1448,8 +1519,9 @@ int run_features(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set_a, const 
     }
     CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long), st), "memset");
     FeatArgs fa{view(set_a), view(set_b), k, S->ent_kmer, S->ent_pos, S->kcount, kmB, posB, cntB,
-                S->comp, compB, pairs, n_pairs, out, S->gtab, gslots, S->ctr + 1, S->status};
-    features_kernel<<<blocks, kFeatWarps * 32, 0, st>>>(fa);
+                S->comp, compB, pairs, n_pairs, out,
+                fslots > (uint32_t)kFeatWarpSlots ? S->gtab : nullptr, fslots, S->ctr + 1, S->status};
+    features_kernel<<<blocks, kFeatWarps * 32, kFeatSmemBytes, st>>>(fa);
     CK(cudaGetLastError(), "features kernel");
     *launches += 1;
     int32_t status = 0;

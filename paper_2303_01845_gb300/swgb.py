@@ -23,6 +23,7 @@ SWGB_ENOMEM = -4
 SWGB_ECUDA = -5
 SWGB_EINTERNAL = -6
 SWGB_ETOOBIG = -7
+SWGB_ETIMEDOUT = -8
 
 SWGB_ALPHABET_SIZE = 24
 SWGB_MAX_LENGTH = 65536
@@ -40,7 +41,7 @@ ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 
 _NAMES = {SWGB_EINVAL: "EINVAL", SWGB_ERANGE: "ERANGE", SWGB_EBADRES: "EBADRES",
           SWGB_ENOMEM: "ENOMEM", SWGB_ECUDA: "ECUDA", SWGB_EINTERNAL: "EINTERNAL",
-          SWGB_ETOOBIG: "ETOOBIG"}
+          SWGB_ETOOBIG: "ETOOBIG", SWGB_ETIMEDOUT: "ETIMEDOUT"}
 
 
 class SwgbError(RuntimeError):
@@ -75,6 +76,22 @@ class swgb_thresholds(ctypes.Structure):
 
 class swgb_identity_record(ctypes.Structure):
     _fields_ = [("matches", ctypes.c_int32), ("columns", ctypes.c_int32), ("pass_", ctypes.c_int32)]
+
+
+class swgb_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch_queries", ctypes.c_int32),
+                ("max_batch_residues", ctypes.c_int64), ("max_inflight_bytes", ctypes.c_int64),
+                ("candidates_per_query", ctypes.c_int32), ("min_shared", ctypes.c_int32),
+                ("threshold", ctypes.c_float), ("identity", swgb_thresholds)]
+
+
+class swgb_server_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_pairs", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("pairs", ctypes.POINTER(ctypes.c_int32)),
+                ("counts", ctypes.POINTER(ctypes.c_int32)), ("records", ctypes.POINTER(ctypes.c_int32)),
+                ("identity", ctypes.POINTER(ctypes.c_int32)), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("batch_id", ctypes.c_int64), ("slot", ctypes.c_int32),
+                ("error", ctypes.c_char_p)]
 
 
 # (name, restype, argtypes) of every exported function
@@ -132,6 +149,16 @@ _SIGS = [
                                       _VP]),
     ("swgb_select_pairs", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP,
                                          ctypes.POINTER(ctypes.c_int64), _VP]),
+    ("swgb_server_default_config", None, [ctypes.POINTER(swgb_server_config)]),
+    ("swgb_server_create", ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(swgb_params),
+                                          ctypes.POINTER(swgb_server_config), ctypes.POINTER(_VP)]),
+    ("swgb_server_destroy", None, [_VP]),
+    ("swgb_server_submit", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    ("swgb_server_wait", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.POINTER(swgb_server_result)]),
+    ("swgb_server_release", ctypes.c_int, [_VP, ctypes.c_int64]),
+    ("swgb_server_stats", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("swgb_align_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int64,
                                           _VP, ctypes.c_int64, ctypes.POINTER(swgb_params), _VP,
                                           _VP]),
@@ -564,6 +591,90 @@ class MLP:
                                                float(lr), float(pos_weight), ctypes.byref(ml),
                                                _stream_handle(stream)))
         return ml.value
+
+
+def server_config(**kw):
+    """swgb_server_config with the library's defaults, overridden by kw
+    (identity=(num, den, num, den))."""
+    cfg = swgb_server_config()
+    load().swgb_server_default_config(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if k == "identity":
+            cfg.identity = swgb_thresholds(*[int(x) for x in v])
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Server:
+    """A query server over a resident reference set (swgb_server_*)."""
+
+    def __init__(self, refs, index, params, mlp_params=None, device=0, **cfg):
+        self.refs, self.index, self.params = refs, index, params   # kept alive
+        self.cfg = server_config(**cfg)
+        mp = None
+        if mlp_params is not None:
+            self._mlp = np.ascontiguousarray(mlp_params, dtype=np.float32).reshape(-1)
+            mp = self._mlp.ctypes.data
+        h = _VP()
+        rc = load().swgb_server_create(int(device), refs.handle, index.handle, mp, ctypes.byref(params),
+                                       ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc != SWGB_OK:
+            raise SwgbError(rc, "swgb_server_create failed")
+        self.handle = h
+
+    def submit(self, codes, offsets):
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        t = ctypes.c_int64()
+        rc = load().swgb_server_submit(self.handle, codes.ctypes.data if codes.size else None,
+                                       offsets.ctypes.data, len(offsets) - 1, ctypes.byref(t))
+        if rc != SWGB_OK:
+            raise SwgbError(rc, "swgb_server_submit failed")
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1, release=True):
+        """Results of a request as numpy copies: pairs [P, 2], counts [P],
+        records [P, 5], identity [P, 3], plus candidates, latency_ms,
+        queue_ms, batch_id, slot."""
+        r = swgb_server_result()
+        rc = load().swgb_server_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r))
+        if rc != SWGB_OK:
+            raise SwgbError(rc, "swgb_server_wait failed")
+        if r.status != SWGB_OK:
+            msg = r.error.decode(errors="replace") if r.error else ""
+            raise SwgbError(r.status, "request %d failed: %s" % (ticket, msg))
+        n = r.n_pairs
+
+        def arr(ptr, shape):
+            if n == 0:
+                return np.zeros(shape, np.int32)
+            return np.ctypeslib.as_array(ptr, shape=shape).copy()
+        out = {"pairs": arr(r.pairs, (n, 2)), "counts": arr(r.counts, (n,)),
+               "records": arr(r.records, (n, 5)), "identity": arr(r.identity, (n, 3)),
+               "candidates": r.n_candidates, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms,
+               "batch_id": r.batch_id, "slot": r.slot}
+        if release:
+            load().swgb_server_release(self.handle, int(ticket))
+        return out
+
+    def stats(self):
+        mo = ctypes.c_int32()
+        pend = ctypes.c_int64()
+        b = ctypes.c_int64()
+        load().swgb_server_stats(self.handle, ctypes.byref(mo), ctypes.byref(pend), ctypes.byref(b))
+        return {"max_overlap": mo.value, "pending": pend.value, "inflight_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().swgb_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, out, stream=None):

@@ -270,3 +270,21 @@ def test_identity_thresholds(aligner, torch_mod, oracle_mod, mat):
     for th in (((1, 2), (1, 2)), ((0, 1), (0, 1)), ((9, 10), (9, 10))):
         identity_case(aligner, torch_mod, oracle_mod, mat, wl.q_res, wl.q_off, wl.r_res, wl.r_off,
                       wl.pairs, th=th)
+
+
+def test_identity_few_large_spans_among_small_ones(aligner, torch_mod, oracle_mod, mat):
+    """Five long homologous pairs among many short ones: the large-span launch
+    starts more warps than it has pairs, every warp with its own boundary
+    column."""
+    long_wl = workload.generate(workload.Spec("idfew", 5, "uniform", 600, 900, seed=31,
+                                              homologous_fraction=1.0), mat)
+    short_wl = workload.generate(workload.Spec("idmany", 300, "uniform", 20, 60, seed=32), mat)
+    qs = [long_wl.q_res[long_wl.q_off[i]:long_wl.q_off[i + 1]] for i in range(5)] + \
+         [short_wl.q_res[short_wl.q_off[i]:short_wl.q_off[i + 1]] for i in range(300)]
+    rs = [long_wl.r_res[long_wl.r_off[i]:long_wl.r_off[i + 1]] for i in range(5)] + \
+         [short_wl.r_res[short_wl.r_off[i]:short_wl.r_off[i + 1]] for i in range(300)]
+    rq, oq = pack(qs)
+    rr, orr = pack(rs)
+    pairs = np.array([[k, k] for k in range(len(qs))], np.int32)
+    ident, rec = identity_case(aligner, torch_mod, oracle_mod, mat, rq, oq, rr, orr, pairs)
+    assert ((rec[:5, 4] - rec[:5, 3] + 1) > 256).all()
