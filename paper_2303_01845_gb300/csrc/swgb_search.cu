@@ -275,6 +275,7 @@ struct JoinArgs {
     const int32_t* bseq;
     int64_t n_cols;            // sequences of the columns' set
     int self_pairs;            // rows and columns are one set: only j > i
+    uint2* range;              // per row entry: its bucket [begin, end), set by row_need
     uint32_t* need;            // [n] min(partner incidences, possible partners)
     uint32_t* ccount;          // [n] candidates of row i (counting pass)
     const uint64_t* coff;      // [n + 1] scan of ccount (writing pass)
@@ -301,10 +302,14 @@ __global__ void row_need_kernel(JoinArgs a) {
         uint64_t inc = 0;
         for (uint32_t e = lane; e < c; e += 32) {
             const uint32_t x = a.ent_kmer[o + e];
+            const uint32_t b0 = a.start[x], b1 = a.start[x + 1];
+            a.range[o + e] = make_uint2(b0, b1);
             if (a.self_pairs) {
-                for (uint32_t b = a.start[x]; b < a.start[x + 1]; ++b) inc += a.bseq[b] > i;
+                // a bucket of one holds only row i itself
+                if (b1 - b0 > 1)
+                    for (uint32_t b = b0; b < b1; ++b) inc += a.bseq[b] > i;
             } else {
-                inc += a.start[x + 1] - a.start[x];
+                inc += b1 - b0;
             }
         }
         for (int d = 16; d; d >>= 1) inc += __shfl_xor_sync(0xffffffffu, inc, d);
@@ -376,9 +381,9 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
         const int64_t o = a.s.off[i];
         const uint32_t c = a.kcount[i];
         for (uint32_t e = threadIdx.x; e < c; e += blockDim.x) {
-            const uint32_t x = a.ent_kmer[o + e];
-            const uint32_t b1 = a.start[x + 1];
-            for (uint32_t b = a.start[x]; b < b1; ++b) {
+            const uint2 rg = a.range[o + e];
+            if (a.self_pairs && rg.y - rg.x <= 1) continue;   // only row i itself
+            for (uint32_t b = rg.x; b < rg.y; ++b) {
                 const int32_t j = a.bseq[b];
                 if (a.self_pairs && j <= i) continue;
                 uint32_t h = slot_of((uint32_t)j, mask);
@@ -463,6 +468,7 @@ constexpr int kIdWarps = 4;                    // warps per block
 constexpr int kIdSmallCols = 64;               // spans of up to 64 columns: 8-lane groups
 constexpr int kIdMidCols = 128;                // up to 128 columns: 16-lane groups
 constexpr int kIdClasses = 4;
+constexpr int64_t kIdLongCells = 1 << 20;      // chunked spans started first
 constexpr int32_t kNegInf = -(1 << 28);
 
 // A chunk's last column at one row: H, E and the (matches, columns) of H and E.
@@ -484,6 +490,8 @@ struct IdentArgs {
     int64_t bnd_stride;
     const int64_t* list;       // the pairs of this launch's class
     int64_t n_list;
+    int64_t n_front;           // tasks < n_front read list[task], later ones
+    int64_t back_base;         // list[back_base - (task - n_front)]
     int64_t* lists;            // classification: kIdClasses lists of n_pairs entries
     unsigned long long* ctr;   // [0] task counter, [1..kIdClasses] list sizes
     int32_t* status;
@@ -550,7 +558,16 @@ __global__ void ident_classify_kernel(IdentArgs a) {
             continue;
         }
         const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
-        a.lists[cls * a.n_pairs + (int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
+        int64_t* list = a.lists + cls * a.n_pairs;
+        if (cls >= 2 && n * m >= kIdLongCells) {
+            // long spans from the front of the list, the rest from its back, so
+            // that the launch starts them first
+            list[(int64_t)atomicAdd(&a.ctr[5 + (cls - 2)], 1ull)] = p;
+        } else if (cls >= 2) {
+            list[a.n_pairs - 1 - (int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
+        } else {
+            list[(int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
+        }
     }
 }
 
@@ -583,7 +600,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
         // this group's pair (groups past the list compute nothing)
         const int64_t li = first + grp;
         const bool live = li < a.n_list;
-        const int64_t p = live ? a.list[li] : 0;
+        const int64_t p = !live ? 0 : li < a.n_front ? a.list[li] : a.list[a.back_base - (li - a.n_front)];
         swgb_record rc{0, 0, 0, 0, 0};
         int n = 0, m = 0, lq = 0, lr = 0;
         const uint8_t *qs = nullptr, *rs = nullptr;
@@ -855,13 +872,13 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 __syncwarp();
                 int c = 0;
                 int64_t dmin = INT64_MAX, dmax = INT64_MIN;
-                // two probes in flight per lane
-                for (uint32_t e0 = lane; e0 < nj; e0 += 64) {
-                    uint32_t xs[2];
+                // four probes in flight per lane
+                for (uint32_t e0 = lane; e0 < nj; e0 += 128) {
+                    uint32_t xs[4];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) xs[u] = e0 + 32 * u < nj ? a.kmB[oj + e0 + 32 * u] : kEmpty;
+                    for (int u = 0; u < 4; ++u) xs[u] = e0 + 32 * u < nj ? a.kmB[oj + e0 + 32 * u] : kEmpty;
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < 4; ++u) {
                         const uint32_t x = xs[u];
                         if (x == kEmpty) continue;
                         uint32_t h = slot_of(x, mask);
@@ -897,17 +914,18 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                     cd = v < 0 ? -v : v;
                 }
                 for (int s = 16; s; s >>= 1) cd += __shfl_xor_sync(0xffffffffu, (long long)cd, s);
-                float f;
-                if (lane == 0) f = feat_ratio(c, c + 16);
-                else if (lane == 1) f = feat_ratio(min(li, lj), max(li, lj));
-                else if (lane < 2 + kFeatBins) f = feat_ratio(hv, c);
-                else if (lane == 26) f = feat_ratio(cd, 2 * li * lj);
-                else if (lane == 27) f = feat_ratio(li, li + 256);
-                else if (lane == 28) f = feat_ratio(lj, lj + 256);
-                else if (lane == 29) f = feat_ratio(hmax, c);
-                else if (lane == 30) f = feat_ratio(c, min(ni, nj));
-                else f = c >= 2 ? feat_ratio(dmax - dmin, D) : 0.0f;
-                o[lane] = f;
+                // lane f's numerator and denominator, then one division for all lanes
+                int64_t num, den;
+                if (lane == 0) { num = c; den = c + 16; }
+                else if (lane == 1) { num = min(li, lj); den = max(li, lj); }
+                else if (lane < 2 + kFeatBins) { num = hv; den = c; }
+                else if (lane == 26) { num = cd; den = 2 * li * lj; }
+                else if (lane == 27) { num = li; den = li + 256; }
+                else if (lane == 28) { num = lj; den = lj + 256; }
+                else if (lane == 29) { num = hmax; den = c; }
+                else if (lane == 30) { num = c; den = min(ni, nj); }
+                else { num = dmax - dmin; den = c >= 2 ? D : 0; }
+                o[lane] = feat_ratio(num, den);
                 __syncwarp();
             }
             p0 = p1;
@@ -959,6 +977,7 @@ struct SearchStore {
     uint32_t* gtab = nullptr;     int64_t gtab_cap = 0;
     IdBnd* bnd = nullptr;         int64_t bnd_cap = 0;
     int64_t* lists = nullptr;     int64_t lists_cap = 0;
+    uint2* range = nullptr;       int64_t range_cap = 0;
     int32_t* large_rows = nullptr; int64_t large_rows_cap = 0;
     // pair features: k-mer sets of a second set, letter counts of both
     uint32_t* ent2_kmer = nullptr; int64_t ent2_cap = 0;
@@ -976,7 +995,7 @@ void search_store_free(SearchStore* s) {
     cudaSetDevice(s->device);
     void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq, s->bpos,
                     s->need, s->ccount, s->coff, s->part, s->gtab, s->bnd, s->ctr,
-                    s->status, s->large_rows, s->lists, s->ent2_kmer, s->ent2_pos, s->kcount2,
+                    s->status, s->large_rows, s->lists, s->range, s->ent2_kmer, s->ent2_pos, s->kcount2,
                     s->comp, s->comp2, s->flags};
     for (void* p : ptrs) cudaFree(p);
     delete s;
@@ -1101,6 +1120,7 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     CK(grow(&S->ccount, &S->ccount_cap, n), "join scratch");
     CK(grow(&S->coff, &S->coff_cap, n + 1), "join scratch");
     CK(grow(&S->large_rows, &S->large_rows_cap, n), "join scratch");
+    CK(grow(&S->range, &S->range_cap, std::max<int64_t>(rows->total, 1)), "join scratch");
     CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 7, st), "memset");
     JoinArgs ja{};
     ja.s = view(rows);
@@ -1121,6 +1141,7 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     ja.status = S->status;
     ja.large_rows = S->large_rows;
     ja.n_tasks = n;
+    ja.range = S->range;
     const int64_t wg = warp_grid(ctx, n, 256);
     row_need_kernel<<<(unsigned)wg, 256, 0, st>>>(ja);
     CK(cudaGetLastError(), "row_need kernel");
@@ -1419,9 +1440,10 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     const int64_t g = std::min<int64_t>((n_pairs + 255) / 256, (int64_t)ctx->sm_count * 16);
     ident_classify_kernel<<<(unsigned)g, 256, 0, st>>>(a);
     CK(cudaGetLastError(), "ident_classify kernel");
-    unsigned long long sizes[kIdClasses] = {0, 0, 0, 0};
-    CK(cudaMemcpyAsync(sizes, S->ctr + 1, sizeof(sizes), cudaMemcpyDeviceToHost, st), "sizes D2H");
+    unsigned long long cnt[6] = {0, 0, 0, 0, 0, 0};   // class sizes (long spans of 2, 3 apart)
+    CK(cudaMemcpyAsync(cnt, S->ctr + 1, sizeof(cnt), cudaMemcpyDeviceToHost, st), "sizes D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
+    const unsigned long long sizes[kIdClasses] = {cnt[0], cnt[1], cnt[2] + cnt[4], cnt[3] + cnt[5]};
     int32_t launches = 1;
     const int64_t resident_blocks = (int64_t)ctx->sm_count * 8;
     const int pairs_per_warp[kIdClasses] = {4, 2, 1, 1};
@@ -1440,6 +1462,8 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         IdentArgs b = a;
         b.list = S->lists + cls * n_pairs;
         b.n_list = (int64_t)sizes[cls];
+        b.n_front = cls >= 2 ? (int64_t)cnt[4 + (cls - 2)] : b.n_list;
+        b.back_base = n_pairs - 1;
         const int blocks = blocks_of[cls];
         // the launches of the classes run in stream order and share one work counter
         CK(cudaMemsetAsync(S->ctr + 7, 0, sizeof(unsigned long long), st), "memset");
