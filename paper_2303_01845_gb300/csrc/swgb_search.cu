@@ -1008,7 +1008,7 @@ int search_store(swgb_ctx* ctx, SearchStore** out) {
         SearchStore* s = new (std::nothrow) SearchStore();
         if (!s) return fail(ctx, SWGB_ENOMEM, "search scratch: host allocation");
         s->device = ctx->device;
-        cudaError_t e = cudaMalloc(&s->ctr, sizeof(unsigned long long) * 8);
+        cudaError_t e = cudaMalloc(&s->ctr, sizeof(unsigned long long) * 16);
         if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(int32_t));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(join_kernel<false, false>,
@@ -1457,24 +1457,35 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     }
     if (bnd_warps > 0) CK(grow(&S->bnd, &S->bnd_cap, bnd_warps * max_rows), "identity scratch");
     a.bnd = S->bnd;
-    for (int cls = 0; cls < kIdClasses; ++cls) {
+    // The chunked classes (2, then 3: they share the boundary columns) run on
+    // the caller's stream, longest spans first; the short-span classes (0, 1)
+    // run beside them on a side stream and fill the SMs their tail leaves idle.
+    // Each class has its own work counter.
+    CK(cudaMemsetAsync(S->ctr + 8, 0, sizeof(unsigned long long) * kIdClasses, st), "memset");
+    CK(cudaEventRecord(ctx->fork_ev, st), "event record");
+    cudaStream_t side = ctx->side[0];
+    CK(cudaStreamWaitEvent(side, ctx->fork_ev, 0), "stream wait");
+    const int order[kIdClasses] = {2, 3, 0, 1};
+    for (int k = 0; k < kIdClasses; ++k) {
+        const int cls = order[k];
         if (sizes[cls] == 0) continue;
         IdentArgs b = a;
         b.list = S->lists + cls * n_pairs;
         b.n_list = (int64_t)sizes[cls];
         b.n_front = cls >= 2 ? (int64_t)cnt[4 + (cls - 2)] : b.n_list;
         b.back_base = n_pairs - 1;
+        b.ctr = S->ctr + 8 + cls;
         const int blocks = blocks_of[cls];
-        // the launches of the classes run in stream order and share one work counter
-        CK(cudaMemsetAsync(S->ctr + 7, 0, sizeof(unsigned long long), st), "memset");
-        b.ctr = S->ctr + 7;
-        if (cls == 0) ident_kernel<8, uint32_t, false><<<blocks, kIdWarps * 32, 0, st>>>(b);
-        else if (cls == 1) ident_kernel<16, uint32_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
-        else if (cls == 2) ident_kernel<32, uint32_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
-        else ident_kernel<32, uint64_t, true><<<blocks, kIdWarps * 32, 0, st>>>(b);
+        cudaStream_t s = cls >= 2 ? st : side;
+        if (cls == 0) ident_kernel<8, uint32_t, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        else if (cls == 1) ident_kernel<16, uint32_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        else if (cls == 2) ident_kernel<32, uint32_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        else ident_kernel<32, uint64_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
         CK(cudaGetLastError(), "ident kernel");
         launches += 1;
     }
+    CK(cudaEventRecord(ctx->join_ev[0], side), "event record");
+    CK(cudaStreamWaitEvent(st, ctx->join_ev[0], 0), "stream wait");
     int32_t status = 0;
     CK(cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st), "status D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
