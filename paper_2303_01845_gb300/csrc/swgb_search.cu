@@ -468,7 +468,8 @@ constexpr int kIdWarps = 4;                    // warps per block
 constexpr int kIdSmallCols = 64;               // spans of up to 64 columns: 8-lane groups
 constexpr int kIdMidCols = 128;                // up to 128 columns: 16-lane groups
 constexpr int kIdClasses = 4;
-constexpr int64_t kIdLongCells = 1 << 20;      // chunked spans started first
+constexpr int kIdCoopCols = 2048;              // spans of >= 8 chunks: one block per span
+constexpr int kIdSpinLimit = 1 << 25;          // bounded wait on the previous chunk's progress
 constexpr int32_t kNegInf = -(1 << 28);
 
 // A chunk's last column at one row: H, E and the (matches, columns) of H and E.
@@ -559,9 +560,9 @@ __global__ void ident_classify_kernel(IdentArgs a) {
         }
         const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
         int64_t* list = a.lists + cls * a.n_pairs;
-        if (cls >= 2 && n * m >= kIdLongCells) {
-            // long spans from the front of the list, the rest from its back, so
-            // that the launch starts them first
+        if (cls >= 2 && m >= kIdCoopCols) {
+            // spans of many chunks at the front of the list (the cooperative
+            // launch takes them), the rest from its back
             list[(int64_t)atomicAdd(&a.ctr[5 + (cls - 2)], 1ull)] = p;
         } else if (cls >= 2) {
             list[a.n_pairs - 1 - (int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
@@ -576,25 +577,46 @@ __global__ void ident_classify_kernel(IdentArgs a) {
 // columns).  PROF: lane-private substitution profile in shared memory
 // (prof[letter] = the 8 scores of the lane's columns) instead of one lookup
 // per cell.
-template <int G, class St, bool PROF>
+// COOP (G = 32): the kIdWarps warps of a block share one span, warp w taking
+// chunks w, w + kIdWarps, ...; a chunk's boundary column goes to its warp's
+// buffer, and the next chunk's lane 0 waits (bounded) until the producing
+// warp's progress counter in shared memory passes the row it needs.  Chunk
+// c's progress is published as c (n + 1) + row, so the counters only grow.
+template <int G, class St, bool PROF, bool COOP = false>
 __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
+    static_assert(!COOP || G == 32, "cooperative spans use 32-lane chunks");
     constexpr int GROUPS = 32 / G;
     constexpr int CHUNK = G * kIdR;
     __shared__ int8_t s_mat[kAlpha * kAlpha];
     __shared__ __align__(8) uint2 s_prof[PROF ? kIdWarps * 32 * kAlpha : 1];
+    __shared__ long long s_prog[COOP ? kIdWarps : 1];
+    __shared__ int s_abort;    // COOP: a wait ran out; later waits return at once
+    __shared__ int64_t s_task;
     for (int t = threadIdx.x; t < kAlpha * kAlpha; t += blockDim.x) s_mat[t] = a.mat[t];
     __syncthreads();
     using S = Stat<St>;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
     const int64_t gw = (int64_t)blockIdx.x * kIdWarps + w;
-    IdBnd* bnd = a.bnd + gw * a.bnd_stride;
+    // boundary columns: one per warp (COOP: the block's kIdWarps, one per chunk residue)
+    IdBnd* const bnd_base = a.bnd + (COOP ? (int64_t)blockIdx.x * kIdWarps : gw) * a.bnd_stride;
     uint2* prof = s_prof + (PROF ? (w * 32 + lane) * kAlpha : 0);
     const int32_t ge = a.ge, oe = a.go + a.ge;
     for (;;) {
         int64_t task = 0;
-        if (lane == 0) task = (int64_t)atomicAdd(a.ctr, 1ull);
-        task = __shfl_sync(0xffffffffu, task, 0);
+        if (COOP) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_task = (int64_t)atomicAdd(a.ctr, 1ull);
+                for (int k = 0; k < kIdWarps; ++k) s_prog[k] = -1;
+                s_abort = 0;
+            }
+            __syncthreads();
+            task = s_task;
+        } else {
+            if (lane == 0) task = (int64_t)atomicAdd(a.ctr, 1ull);
+            task = __shfl_sync(0xffffffffu, task, 0);
+        }
         const int64_t first = task * GROUPS;
         if (first >= a.n_list) break;
         // this group's pair (groups past the list compute nothing)
@@ -622,8 +644,10 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
         }
         int32_t hnm = kNegInf;
         St snm = 0;
-        for (int c = 0; c < nch_w; ++c) {
+        for (int c = COOP ? w : 0; c < nch_w; c += COOP ? kIdWarps : 1) {
             const int c0 = c * CHUNK + gl * kIdR;
+            IdBnd* const wbuf = bnd_base + (COOP ? (c % kIdWarps) * a.bnd_stride : 0);
+            IdBnd* const rbuf = bnd_base + (COOP ? ((c + kIdWarps - 1) % kIdWarps) * a.bnd_stride : 0);
             int rcode[kIdR];
             int32_t H[kIdR], F[kIdR];
             St SH[kIdR], SF[kIdR];
@@ -671,7 +695,21 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                         shl = 0;
                         sel = 0;
                     } else if (arow >= 1 && arow <= n) {
-                        const IdBnd v = bnd[arow];
+                        if (COOP) {
+                            // the previous chunk's warp must have finished this row
+                            const long long want = (long long)(c - 1) * (n + 1) + arow;
+                            volatile long long* prog = s_prog + (c - 1) % kIdWarps;
+                            volatile int* abort_flag = &s_abort;
+                            int spins = 0;
+                            while (*prog < want && !*abort_flag && ++spins < kIdSpinLimit) {
+                            }
+                            if (spins >= kIdSpinLimit) {
+                                *abort_flag = 1;
+                                atomicMax(a.status, 4);
+                            }
+                            __threadfence_block();
+                        }
+                        const IdBnd v = rbuf[arow];
                         hl = v.h;
                         el = v.e;
                         shl = S::narrow(v.sh);
@@ -716,8 +754,13 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                     e_out = eleft;
                     sh_out = shleft;
                     se_out = seleft;
-                    if (G == 32 && gl == 31 && c + 1 < nch_w)
-                        bnd[arow] = IdBnd{hleft, eleft, S::wide(shleft), S::wide(seleft)};
+                    if (G == 32 && gl == 31 && c + 1 < nch_w) {
+                        wbuf[arow] = IdBnd{hleft, eleft, S::wide(shleft), S::wide(seleft)};
+                        if (COOP) {
+                            __threadfence_block();
+                            *(volatile long long*)(s_prog + c % kIdWarps) = (long long)c * (n + 1) + arow;
+                        }
+                    }
                     if (arow == n && m > c0 && m <= c0 + kIdR) {
 #pragma unroll
                         for (int x = 0; x < kIdR; ++x)
@@ -1443,36 +1486,62 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     unsigned long long cnt[6] = {0, 0, 0, 0, 0, 0};   // class sizes (long spans of 2, 3 apart)
     CK(cudaMemcpyAsync(cnt, S->ctr + 1, sizeof(cnt), cudaMemcpyDeviceToHost, st), "sizes D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    const unsigned long long sizes[kIdClasses] = {cnt[0], cnt[1], cnt[2] + cnt[4], cnt[3] + cnt[5]};
     int32_t launches = 1;
     const int64_t resident_blocks = (int64_t)ctx->sm_count * 8;
+    // classes 2 and 3 split: spans of >= kIdCoopCols columns at the front of
+    // their lists go to the cooperative launches, the rest to the regular ones
+    const int64_t coop_n[2] = {(int64_t)cnt[4], (int64_t)cnt[5]};
+    const int64_t reg_n[kIdClasses] = {(int64_t)cnt[0], (int64_t)cnt[1], (int64_t)cnt[2], (int64_t)cnt[3]};
     const int pairs_per_warp[kIdClasses] = {4, 2, 1, 1};
     int blocks_of[kIdClasses] = {0, 0, 0, 0};
     int64_t bnd_warps = 0;
     for (int cls = 0; cls < kIdClasses; ++cls) {
-        const int64_t tasks = ((int64_t)sizes[cls] + pairs_per_warp[cls] - 1) / pairs_per_warp[cls];
+        const int64_t tasks = (reg_n[cls] + pairs_per_warp[cls] - 1) / pairs_per_warp[cls];
         blocks_of[cls] = (int)std::min<int64_t>((tasks + kIdWarps - 1) / kIdWarps, resident_blocks);
         // every warp of a chunked (32-lane) launch owns a boundary column
         if (cls >= 2) bnd_warps = std::max<int64_t>(bnd_warps, (int64_t)blocks_of[cls] * kIdWarps);
     }
-    if (bnd_warps > 0) CK(grow(&S->bnd, &S->bnd_cap, bnd_warps * max_rows), "identity scratch");
+    int coop_blocks[2] = {0, 0};
+    for (int k = 0; k < 2; ++k)
+        coop_blocks[k] = (int)std::min<int64_t>(coop_n[k], (int64_t)ctx->sm_count * 2);
+    const int64_t coop_warps = (int64_t)std::max(coop_blocks[0], coop_blocks[1]) * kIdWarps;
+    if (bnd_warps + coop_warps > 0)
+        CK(grow(&S->bnd, &S->bnd_cap, (bnd_warps + coop_warps) * max_rows), "identity scratch");
     a.bnd = S->bnd;
-    // The chunked classes (2, then 3: they share the boundary columns) run on
-    // the caller's stream, longest spans first; the short-span classes (0, 1)
-    // run beside them on a side stream and fill the SMs their tail leaves idle.
-    // Each class has its own work counter.
-    CK(cudaMemsetAsync(S->ctr + 8, 0, sizeof(unsigned long long) * kIdClasses, st), "memset");
+    // The regular chunked classes (2, then 3: they share their boundary
+    // columns) run on the caller's stream; the cooperative launches (the
+    // longest spans, their own boundary region) on one side stream and the
+    // short-span classes (0, 1) on another, all at once, so that the short
+    // spans fill the SMs the long spans' tail leaves idle.  Each launch has
+    // its own work counter.
+    CK(cudaMemsetAsync(S->ctr + 8, 0, sizeof(unsigned long long) * 8, st), "memset");
     CK(cudaEventRecord(ctx->fork_ev, st), "event record");
-    cudaStream_t side = ctx->side[0];
+    cudaStream_t side = ctx->side[0], side_coop = ctx->side[1];
     CK(cudaStreamWaitEvent(side, ctx->fork_ev, 0), "stream wait");
+    CK(cudaStreamWaitEvent(side_coop, ctx->fork_ev, 0), "stream wait");
+    for (int k = 0; k < 2; ++k) {
+        if (coop_n[k] == 0) continue;
+        IdentArgs b = a;
+        b.list = S->lists + (2 + k) * n_pairs;
+        b.n_list = coop_n[k];
+        b.n_front = coop_n[k];
+        b.back_base = n_pairs - 1;
+        b.bnd = S->bnd + bnd_warps * max_rows;
+        b.ctr = S->ctr + 12 + k;
+        if (k == 0) ident_kernel<32, uint32_t, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
+        else ident_kernel<32, uint64_t, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
+        CK(cudaGetLastError(), "ident kernel (cooperative)");
+        launches += 1;
+    }
     const int order[kIdClasses] = {2, 3, 0, 1};
     for (int k = 0; k < kIdClasses; ++k) {
         const int cls = order[k];
-        if (sizes[cls] == 0) continue;
+        if (reg_n[cls] == 0) continue;
         IdentArgs b = a;
+        // classes 2 and 3: the back of the list (the front went cooperative)
         b.list = S->lists + cls * n_pairs;
-        b.n_list = (int64_t)sizes[cls];
-        b.n_front = cls >= 2 ? (int64_t)cnt[4 + (cls - 2)] : b.n_list;
+        b.n_list = reg_n[cls];
+        b.n_front = cls >= 2 ? 0 : reg_n[cls];
         b.back_base = n_pairs - 1;
         b.ctr = S->ctr + 8 + cls;
         const int blocks = blocks_of[cls];
@@ -1484,6 +1553,8 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         CK(cudaGetLastError(), "ident kernel");
         launches += 1;
     }
+    CK(cudaEventRecord(ctx->join_ev[1], side_coop), "event record");
+    CK(cudaStreamWaitEvent(st, ctx->join_ev[1], 0), "stream wait");
     CK(cudaEventRecord(ctx->join_ev[0], side), "event record");
     CK(cudaStreamWaitEvent(st, ctx->join_ev[0], 0), "stream wait");
     int32_t status = 0;
@@ -1491,6 +1562,7 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     CK(cudaStreamSynchronize(st), "stream sync");
     ctx->last_search_launches = launches;
     if (status == 3) return fail(ctx, SWGB_ERANGE, "identity: a pair index or record outside its sequences");
+    if (status == 4) return fail(ctx, SWGB_EINTERNAL, "identity: a chunk waited too long for the previous one");
     if (status) return fail(ctx, SWGB_EINTERNAL, "identity: a span's global optimum differs from its record's score");
     return SWGB_OK;
 }

@@ -288,3 +288,36 @@ def test_identity_few_large_spans_among_small_ones(aligner, torch_mod, oracle_mo
     pairs = np.array([[k, k] for k in range(len(qs))], np.int32)
     ident, rec = identity_case(aligner, torch_mod, oracle_mod, mat, rq, oq, rr, orr, pairs)
     assert ((rec[:5, 4] - rec[:5, 3] + 1) > 256).all()
+
+
+def test_identity_cooperative_spans_match_oracle(aligner, torch_mod, oracle_mod, mat):
+    """Spans of more than 2,048 columns run on one block of four warps that
+    pipeline the span's chunks."""
+    wl = workload.generate(workload.Spec("idcoop", 6, "uniform", 2600, 4200, seed=41,
+                                         homologous_fraction=1.0), mat)
+    ident, rec = identity_case(aligner, torch_mod, oracle_mod, mat, wl.q_res, wl.q_off, wl.r_res,
+                               wl.r_off, wl.pairs)
+    assert ((rec[:, 4] - rec[:, 3] + 1) >= 2048).sum() >= 3
+
+
+def test_identity_of_very_long_self_alignments(aligner, torch_mod, mat):
+    """Closed form where the oracle's traceback matrix would not fit: a
+    sequence of standard letters aligned with itself scores the sum of its
+    diagonal over the whole length (every off-diagonal BLOSUM62 entry is below
+    both diagonal ones), so its identity record is (n, n, pass).  Lengths
+    33,000 (rows + columns >= 65,536: 64-bit statistics) and 6,000."""
+    from paper_2303_01845_gb300 import swgb
+    rng = np.random.default_rng(43)
+    seqs = [rng.integers(0, 20, 33000).astype(np.uint8), rng.integers(0, 20, 6000).astype(np.uint8)]
+    res, off = pack(seqs)
+    s = aligner.seqset(torch_mod.from_numpy(res).cuda(), torch_mod.from_numpy(off).cuda())
+    pairs = torch_mod.tensor([[0, 0], [1, 1]], dtype=torch_mod.int32, device="cuda")
+    params = swgb.make_params(mat, 11, 1)
+    rec = aligner.align(s, s, pairs, params)
+    ident = aligner.identity(s, s, pairs, rec, params).cpu().numpy()
+    rec = rec.cpu().numpy()
+    for k, q in enumerate(seqs):
+        n = len(q)
+        assert rec[k].tolist() == [int(mat[q, q].astype(np.int64).sum()), 0, n - 1, 0, n - 1]
+        assert ident[k].tolist() == [n, n, 1]
+    s.close()
