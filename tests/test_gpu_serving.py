@@ -203,3 +203,28 @@ def test_admission_by_memory(setup, torch_mod, mat):
         srv.submit(*big_q)
     assert e.value.code == swgb.SWGB_ETOOBIG
     srv.close()
+
+
+def test_server_rejects_bad_requests(setup, torch_mod, mat):
+    """Host-side failures reach the caller as status codes, and the server
+    keeps serving good requests after them."""
+    from paper_2303_01845_gb300 import swgb
+    al, refs, index, _, (qr, qo) = setup
+    srv = swgb.Server(refs, index, swgb.make_params(mat, 11, 1), None, slots=2)
+    codes, offs = requests_of(qr, qo, [3])[0]
+    bad_code = codes.copy()
+    bad_code[5] = 30
+    with pytest.raises(swgb.SwgbError) as e:
+        srv.submit(bad_code, offs)
+    assert e.value.code == swgb.SWGB_EBADRES
+    bad_off = offs.copy()
+    bad_off[2] = bad_off[1] - 1
+    with pytest.raises(swgb.SwgbError) as e:
+        srv.submit(codes, bad_off)
+    assert e.value.code == swgb.SWGB_ERANGE
+    with pytest.raises(swgb.SwgbError) as e:
+        srv.wait(123456789)
+    assert e.value.code == swgb.SWGB_EINVAL
+    res = srv.wait(srv.submit(codes, offs))
+    assert res["candidates"] >= len(res["records"])
+    srv.close()
