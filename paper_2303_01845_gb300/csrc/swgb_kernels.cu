@@ -35,6 +35,15 @@ namespace swgb {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// SMs of the current device: caps the grids of the grid-stride kernels.
+static int64_t sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+        return 1;
+    return n;
+}
+
 // ---------------------------------------------------------------------------
 // Residue encoding (ASCII letters or codes -> codes 0..23)
 // ---------------------------------------------------------------------------
@@ -81,7 +90,7 @@ cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii
                           int32_t* flags, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > sm_count() * 32) blocks = sm_count() * 32;
     encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, n, ascii ? 1 : 0, flags);
     return cudaGetLastError();
 }
@@ -176,7 +185,7 @@ cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs
                         const Workspace& ws, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     int64_t blocks = (n_pairs + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, reverse ? 1 : 0, ca, ws);
     return cudaGetLastError();
 }
@@ -232,7 +241,7 @@ __global__ void scatter_kernel(int64_t n_pairs, Workspace ws) {
 cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     int64_t blocks = (n_pairs + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_pairs, ws);
     return cudaGetLastError();
 }

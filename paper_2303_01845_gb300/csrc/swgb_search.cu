@@ -46,6 +46,11 @@ constexpr int kSearchThreads = 256;
 constexpr int kSetSmemSlots = 4096;
 constexpr int kJoinSmemSlots = 4096;
 constexpr int kJoinSmemBytes = kJoinSmemSlots * 12;
+// rows of at most kWarpJoinNeed partners: one warp each (join_warp_kernel)
+constexpr int kWarpJoinSlots = 512;
+constexpr int kWarpJoinNeed = kWarpJoinSlots / 2;
+constexpr int kWarpJoinWarps = 8;
+constexpr int kWarpJoinSmemBytes = kWarpJoinWarps * kWarpJoinSlots * 12;
 
 __host__ __device__ inline uint32_t pow2_at_least(uint64_t v) {
     uint32_t p = 64;
@@ -168,18 +173,27 @@ __global__ void kmer_hist_kernel(SeqView s, const uint32_t* __restrict__ ent_kme
 __global__ void kmer_scatter_kernel(SeqView s, const uint32_t* __restrict__ ent_kmer,
                                     const uint32_t* __restrict__ ent_pos,
                                     const uint32_t* __restrict__ kcount,
-                                    const uint32_t* __restrict__ start, uint32_t* fill,
-                                    int32_t* bseq, uint32_t* bpos) {
+                                    const uint32_t* __restrict__ start, uint32_t* __restrict__ fill,
+                                    int32_t* __restrict__ bseq, uint32_t* __restrict__ bpos) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < s.n; i += warps) {
         const int64_t o = s.off[i];
         const uint32_t c = kcount[i];
-        for (uint32_t e = lane; e < c; e += 32) {
-            const uint32_t x = ent_kmer[o + e];
-            const uint32_t slot = start[x] + atomicAdd(&fill[x], 1u);
-            bseq[slot] = (int32_t)i;
-            bpos[slot] = ent_pos[o + e];
+        // four entries per lane at a time: their atomics are in flight together
+        for (uint32_t e0 = lane; e0 < c; e0 += 128) {
+            uint32_t x[4], slot[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = e0 + 32 * u < c ? ent_kmer[o + e0 + 32 * u] : kEmpty;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (x[u] != kEmpty) slot[u] = start[x[u]] + atomicAdd(&fill[x[u]], 1u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (x[u] != kEmpty) {
+                    bseq[slot[u]] = (int32_t)i;
+                    bpos[slot[u]] = ent_pos[o + e0 + 32 * u];
+                }
         }
     }
 }
@@ -349,7 +363,8 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
         if (LARGE) i = a.large_rows[i];
         const uint32_t need = a.need[i];
         const bool large = 2ull * need > (unsigned long long)kJoinSmemSlots;
-        if (need == 0 || large != LARGE) {
+        // rows of at most kWarpJoinNeed partners belong to join_warp_kernel
+        if (need == 0 || large != LARGE || need <= (uint32_t)kWarpJoinNeed) {
             if (!WRITE && need == 0 && threadIdx.x == 0) a.ccount[i] = 0;
             continue;
         }
@@ -442,6 +457,106 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
                 if (a.out_counts) a.out_counts[d] = (int32_t)(v & 0xffffffffu);
             }
         }
+    }
+}
+
+// The join of rows with at most kWarpJoinNeed possible partners: one warp
+// per row, its hash table and candidate list in the warp's share of shared
+// memory, warp-level synchronisation only.  Same results as join_kernel.
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kWarpJoinWarps * 32) join_warp_kernel(JoinArgs a) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ uint32_t s_n[kWarpJoinWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t* const list = reinterpret_cast<uint64_t*>(s_dyn) + w * (kWarpJoinSlots / 2);
+    uint32_t* const keys = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(s_dyn) +
+                                                       kWarpJoinWarps * (kWarpJoinSlots / 2)) +
+                           w * 2 * kWarpJoinSlots;
+    uint32_t* const cnts = keys + kWarpJoinSlots;
+    const int64_t n = a.s.n;
+    for (;;) {
+        int64_t i = 0;
+        if (lane == 0) i = (int64_t)atomicAdd(a.ctr, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n) break;
+        const uint32_t need = a.need[i];
+        if (need == 0 || need > (uint32_t)kWarpJoinNeed) {
+            if (!WRITE && need == 0 && lane == 0) a.ccount[i] = 0;
+            continue;
+        }
+        const uint32_t cap = pow2_at_least(2ull * need);
+        const uint32_t mask = cap - 1;
+        for (uint32_t t = lane; t < cap; t += 32) {
+            keys[t] = kEmpty;
+            cnts[t] = 0;
+        }
+        if (lane == 0) s_n[w] = 0;
+        __syncwarp();
+        const int64_t o = a.s.off[i];
+        const uint32_t c = a.kcount[i];
+        for (uint32_t e = lane; e < c; e += 32) {
+            const uint2 rg = a.range[o + e];
+            if (a.self_pairs && rg.y - rg.x <= 1) continue;   // only row i itself
+            for (uint32_t b = rg.x; b < rg.y; ++b) {
+                const int32_t j = a.bseq[b];
+                if (a.self_pairs && j <= i) continue;
+                uint32_t h = slot_of((uint32_t)j, mask);
+                for (uint32_t probe = 0; probe < cap; ++probe) {
+                    const uint32_t cur = atomicCAS(&keys[h], kEmpty, (uint32_t)j);
+                    if (cur == kEmpty || cur == (uint32_t)j) {
+                        atomicAdd(&cnts[h], 1u);
+                        break;
+                    }
+                    h = (h + 1) & mask;
+                }
+            }
+        }
+        __syncwarp();
+        for (uint32_t t = lane; t < cap; t += 32) {
+            const uint32_t j = keys[t];
+            if (j != kEmpty && cnts[t] >= (uint32_t)a.min_shared) {
+                const uint32_t e = atomicAdd(&s_n[w], 1u);
+                if (WRITE) list[e] = ((uint64_t)j << 32) | cnts[t];
+            }
+        }
+        __syncwarp();
+        const uint32_t m = s_n[w];
+        if (!WRITE) {
+            if (lane == 0) a.ccount[i] = m;
+            continue;
+        }
+        if (m == 0) continue;
+        // bitonic sort of list[0, P) by j (padding sorts last); P <= cap / 2
+        const uint32_t P = m <= 1 ? 1 : 1u << (32 - __clz(m - 1));
+        for (uint32_t t = m + lane; t < P; t += 32) list[t] = ~0ull;
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t t = lane; t < P; t += 32) {
+                    const uint32_t u = t ^ jj;
+                    if (u > t) {
+                        const uint64_t x = list[t], y = list[u];
+                        if ((x > y) == ((t & k) == 0)) {
+                            list[t] = y;
+                            list[u] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        const int64_t base = (int64_t)a.coff[i];
+        for (uint32_t t = lane; t < m; t += 32) {
+            const int64_t d = base + t;
+            if (d < a.capacity) {
+                const uint64_t v = list[t];
+                a.out_pairs[2 * d] = (int32_t)i;
+                a.out_pairs[2 * d + 1] = (int32_t)(v >> 32);
+                if (a.out_counts) a.out_counts[d] = (int32_t)(v & 0xffffffffu);
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1062,6 +1177,12 @@ int search_store(swgb_ctx* ctx, SearchStore** out) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kFeatSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(join_warp_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpJoinSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(join_warp_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpJoinSmemBytes);
         if (e != cudaSuccess) {
             search_store_free(s);
             return cuda_fail(ctx, e, "search scratch");
@@ -1164,7 +1285,7 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     CK(grow(&S->coff, &S->coff_cap, n + 1), "join scratch");
     CK(grow(&S->large_rows, &S->large_rows_cap, n), "join scratch");
     CK(grow(&S->range, &S->range_cap, std::max<int64_t>(rows->total, 1)), "join scratch");
-    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 7, st), "memset");
+    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 9, st), "memset");
     JoinArgs ja{};
     ja.s = view(rows);
     ja.ent_kmer = kmer;
@@ -1206,23 +1327,28 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     ja.gtab = S->gtab;
     ja.gslots = join_gslots;
     const int join_blocks = ctx->sm_count * 4;
+    const int warp_blocks = ctx->sm_count * 4;
     for (int pass = 0; pass < 2; ++pass) {
         ja.ctr = S->ctr + 1 + pass;
         JoinArgs jl = ja;
         jl.ctr = S->ctr + 6 + pass;
         jl.n_tasks = (int64_t)n_large;
+        JoinArgs jw = ja;
+        jw.ctr = S->ctr + 8 + pass;
         if (pass == 0) {
+            join_warp_kernel<false><<<warp_blocks, kWarpJoinWarps * 32, kWarpJoinSmemBytes, st>>>(jw);
             join_kernel<false, false><<<join_blocks, kSearchThreads, kJoinSmemBytes, st>>>(ja);
             if (large_blocks) join_kernel<true, false><<<large_blocks, kSearchThreads, 0, st>>>(jl);
             CK(cudaGetLastError(), "join kernel (count)");
-            *launches += (large_blocks ? 2 : 1) + 3;
+            *launches += (large_blocks ? 3 : 2) + 3;
             int rc = device_scan<uint64_t>(ctx, S, S->ccount, n, S->coff, st);
             if (rc) return rc;
         } else {
+            join_warp_kernel<true><<<warp_blocks, kWarpJoinWarps * 32, kWarpJoinSmemBytes, st>>>(jw);
             join_kernel<false, true><<<join_blocks, kSearchThreads, kJoinSmemBytes, st>>>(ja);
             if (large_blocks) join_kernel<true, true><<<large_blocks, kSearchThreads, 0, st>>>(jl);
             CK(cudaGetLastError(), "join kernel (write)");
-            *launches += large_blocks ? 2 : 1;
+            *launches += large_blocks ? 3 : 2;
         }
     }
     uint64_t total = 0;
