@@ -312,7 +312,7 @@ int swgb_search_launches(const swgb_ctx* ctx);
 typedef struct swgb_index swgb_index;
 
 /* Builds the index of `refs` (which must outlive it) on ctx's device with k
- * in 1..6; about 17 bytes per reference residue + 4 (20^k + 1) bytes.
+ * in 1..6; about 12 bytes per reference residue + 4 (20^k + 1) bytes.
  * Synchronous on `stream`.  Errors: EINVAL, ETOOBIG, ENOMEM, ECUDA. */
 int swgb_index_create(swgb_ctx* ctx, const swgb_seqset* refs, int k, void* stream,
                       swgb_index** out);

@@ -170,30 +170,26 @@ __global__ void kmer_hist_kernel(SeqView s, const uint32_t* __restrict__ ent_kme
     }
 }
 
+// Bucket members: each entry takes the next slot of its k-mer's bucket from
+// a cursor array (a copy of the bucket starts), four atomics in flight per lane.
 __global__ void kmer_scatter_kernel(SeqView s, const uint32_t* __restrict__ ent_kmer,
-                                    const uint32_t* __restrict__ ent_pos,
                                     const uint32_t* __restrict__ kcount,
-                                    const uint32_t* __restrict__ start, uint32_t* __restrict__ fill,
-                                    int32_t* __restrict__ bseq, uint32_t* __restrict__ bpos) {
+                                    uint32_t* __restrict__ cursor, int32_t* __restrict__ bseq) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < s.n; i += warps) {
         const int64_t o = s.off[i];
         const uint32_t c = kcount[i];
-        // four entries per lane at a time: their atomics are in flight together
         for (uint32_t e0 = lane; e0 < c; e0 += 128) {
             uint32_t x[4], slot[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) x[u] = e0 + 32 * u < c ? ent_kmer[o + e0 + 32 * u] : kEmpty;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (x[u] != kEmpty) slot[u] = start[x[u]] + atomicAdd(&fill[x[u]], 1u);
+                if (x[u] != kEmpty) slot[u] = atomicAdd(&cursor[x[u]], 1u);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (x[u] != kEmpty) {
-                    bseq[slot[u]] = (int32_t)i;
-                    bpos[slot[u]] = ent_pos[o + e0 + 32 * u];
-                }
+                if (x[u] != kEmpty) bseq[slot[u]] = (int32_t)i;
         }
     }
 }
@@ -1127,7 +1123,6 @@ struct SearchStore {
     uint32_t* hist = nullptr;     int64_t hist_cap = 0;
     uint32_t* start = nullptr;    int64_t start_cap = 0;
     int32_t* bseq = nullptr;      int64_t bseq_cap = 0;
-    uint32_t* bpos = nullptr;     int64_t bpos_cap = 0;
     uint32_t* need = nullptr;     int64_t need_cap = 0;
     uint32_t* ccount = nullptr;   int64_t ccount_cap = 0;
     uint64_t* coff = nullptr;     int64_t coff_cap = 0;
@@ -1151,7 +1146,7 @@ struct SearchStore {
 void search_store_free(SearchStore* s) {
     if (!s) return;
     cudaSetDevice(s->device);
-    void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq, s->bpos,
+    void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq,
                     s->need, s->ccount, s->coff, s->part, s->gtab, s->bnd, s->ctr,
                     s->status, s->large_rows, s->lists, s->range, s->ent2_kmer, s->ent2_pos, s->kcount2,
                     s->comp, s->comp2, s->flags};
@@ -1247,8 +1242,8 @@ int build_sets(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set, int k, uin
 // Buckets of the distinct k-mers of `set` (the columns of the sequence x
 // k-mer matrix): start [V + 1], and per entry its sequence and position.
 int build_buckets(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set, const uint32_t* kmer,
-                  const uint32_t* pos, const uint32_t* cnt, int64_t V, uint32_t* start,
-                  int32_t* bseq, uint32_t* bpos, int32_t* launches, cudaStream_t st) {
+                  const uint32_t* cnt, int64_t V, uint32_t* start, int32_t* bseq,
+                  int32_t* launches, cudaStream_t st) {
     CK(grow(&S->hist, &S->hist_cap, V), "bucket scratch");
     CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
     const int64_t wg = warp_grid(ctx, std::max<int64_t>(set->n, 1), 256);
@@ -1260,10 +1255,10 @@ int build_buckets(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* set, const u
     int rc = device_scan<uint32_t>(ctx, S, S->hist, V, start, st);
     if (rc) return rc;
     *launches += 3;
-    CK(cudaMemsetAsync(S->hist, 0, sizeof(uint32_t) * V, st), "memset");
+    // the histogram's array becomes the scatter's cursors: a copy of the starts
+    CK(cudaMemcpyAsync(S->hist, start, sizeof(uint32_t) * V, cudaMemcpyDeviceToDevice, st), "cursor copy");
     if (set->n > 0) {
-        kmer_scatter_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), kmer, pos, cnt, start, S->hist,
-                                                          bseq, bpos);
+        kmer_scatter_kernel<<<(unsigned)wg, 256, 0, st>>>(view(set), kmer, cnt, S->hist, bseq);
         CK(cudaGetLastError(), "kmer_scatter kernel");
         *launches += 1;
     }
@@ -1396,7 +1391,6 @@ SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int 
     CK(grow(&S->ent_kmer, &S->ent_cap, total), "discover scratch");
     CK(grow(&S->ent_pos, &S->entp_cap, total), "discover scratch");
     CK(grow(&S->bseq, &S->bseq_cap, total), "discover scratch");
-    CK(grow(&S->bpos, &S->bpos_cap, total), "discover scratch");
     CK(grow(&S->kcount, &S->kcount_cap, set->n), "discover scratch");
     CK(grow(&S->start, &S->start_cap, V + 1), "discover scratch");
     uint32_t gslots = 0;
@@ -1405,8 +1399,7 @@ SWGB_EXPORT int swgb_discover(swgb_ctx* ctx, const swgb_seqset* set, int k, int 
     int32_t launches = 0;
     CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
     rc = build_sets(ctx, S, set, k, S->ent_kmer, S->ent_pos, S->kcount, gslots, &launches, st);
-    if (!rc) rc = build_buckets(ctx, S, set, S->ent_kmer, S->ent_pos, S->kcount, V, S->start, S->bseq,
-                                S->bpos, &launches, st);
+    if (!rc) rc = build_buckets(ctx, S, set, S->ent_kmer, S->kcount, V, S->start, S->bseq, &launches, st);
     if (!rc) rc = join_rows(ctx, S, set, S->ent_kmer, S->kcount, S->start, S->bseq, set->n, true,
                             min_shared, pairs, counts, capacity, n_found, &launches, st);
     ctx->last_search_launches = launches;
@@ -1429,14 +1422,13 @@ struct swgb_index {
     uint32_t* comp = nullptr;   // [n][20] letter counts
     uint32_t* start = nullptr;  // [V + 1]
     int32_t* bseq = nullptr;
-    uint32_t* bpos = nullptr;
     int64_t bytes = 0;
 };
 
 SWGB_EXPORT void swgb_index_destroy(swgb_index* ix) {
     if (!ix) return;
     cudaSetDevice(ix->device);
-    void* ptrs[] = {ix->kmer, ix->pos, ix->cnt, ix->comp, ix->start, ix->bseq, ix->bpos};
+    void* ptrs[] = {ix->kmer, ix->pos, ix->cnt, ix->comp, ix->start, ix->bseq};
     for (void* p : ptrs) cudaFree(p);
     delete ix;
 }
@@ -1473,7 +1465,6 @@ SWGB_EXPORT int swgb_index_create(swgb_ctx* ctx, const swgb_seqset* refs, int k,
     alloc(&ix->kmer, total);
     alloc(&ix->pos, total);
     alloc(&ix->bseq, total);
-    alloc(&ix->bpos, total);
     alloc(&ix->cnt, n);
     alloc(&ix->comp, n * kStdLetters);
     alloc(&ix->start, ix->V + 1);
@@ -1495,8 +1486,7 @@ SWGB_EXPORT int swgb_index_create(swgb_ctx* ctx, const swgb_seqset* refs, int k,
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "composition kernel");
         launches += 1;
     }
-    if (!rc) rc = build_buckets(ctx, S, refs, ix->kmer, ix->pos, ix->cnt, ix->V, ix->start, ix->bseq,
-                                ix->bpos, &launches, st);
+    if (!rc) rc = build_buckets(ctx, S, refs, ix->kmer, ix->cnt, ix->V, ix->start, ix->bseq, &launches, st);
     int32_t status = 0;
     if (!rc) {
         e = cudaMemcpyAsync(&status, S->status, sizeof(status), cudaMemcpyDeviceToHost, st);
