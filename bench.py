@@ -765,6 +765,9 @@ def run_serving(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "queue_ms": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+        "batch_stage_ms_p50": dict(zip(["load", "candidates", "filter", "align_identity", "results"],
+                                       [float(v) for v in np.median(
+                                           np.array([r["stage_ms"] for r in results]), axis=0)])),
         "throughput": {"alignments_per_s": aligned / wall, "candidates_per_s": cands / wall,
                        "queries_per_s": queries / wall, "requests_per_s": len(reqs) / wall,
                        "passing_pairs": passing, "aligned_pairs": aligned, "candidates": cands,

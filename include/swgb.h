@@ -435,6 +435,8 @@ typedef struct {
     swgb_thresholds identity;      /* pass / fail thresholds */
 } swgb_server_config;
 
+#define SWGB_SERVER_STAGES 5
+
 /* The results of one request (valid until swgb_server_release). */
 typedef struct {
     int32_t status;                /* SWGB_OK or the failing call's code */
@@ -449,6 +451,9 @@ typedef struct {
     int64_t batch_id;              /* the batch the request ran in */
     int32_t slot;                  /* the worker that ran it */
     const char* error;             /* message of a failed request ("" if none) */
+    double stage_ms[SWGB_SERVER_STAGES];   /* host wall time of its batch's stages: loading the
+                                              queries, candidates, filter, alignment + identity,
+                                              results back */
 } swgb_server_result;
 
 /* Defaults: 3 slots, 4096 queries / 2^20 residues per batch, 4 GiB budget,

@@ -54,6 +54,7 @@ struct Request {
     int64_t candidates = 0;
     int64_t batch_id = -1;
     int32_t slot = -1;
+    double stage_ms[SWGB_SERVER_STAGES] = {};   // of the batch it ran in
 };
 
 // Device buffers of a slot, grown on demand.
@@ -212,6 +213,13 @@ void worker(swgb_server* s, int slot_id) {
             fail_batch(setup_err, SWGB_ECUDA);
             continue;
         }
+        double stage[SWGB_SERVER_STAGES] = {};
+        auto t_mark = Clock::now();
+        auto lap = [&](int k) {
+            const auto now = Clock::now();
+            stage[k] += std::chrono::duration<double, std::milli>(now - t_mark).count();
+            t_mark = now;
+        };
         auto run = [&]() -> int {
             // the batch's queries, concatenated
             std::vector<uint8_t> res;
@@ -228,6 +236,7 @@ void worker(swgb_server* s, int slot_id) {
                                 : swgb_seqset_create(sl.ctx, res.data(), off.data(), nq, 0, sl.stream,
                                                      &sl.queries);
             if (rc) return fail_batch(std::string("queries: ") + swgb_last_error(sl.ctx), rc);
+            lap(0);
             // candidates from the resident index
             int64_t found = 0;
             SCK(sl.cand.need(2 * std::max<int64_t>(sl.cand.cap / 2, 1024)));
@@ -244,6 +253,7 @@ void worker(swgb_server* s, int slot_id) {
                                       sl.counts.p, cap, &found, sl.stream);
                 if (rc) return fail_batch(std::string("index_query: ") + swgb_last_error(sl.ctx), rc);
             }
+            lap(1);
             const int32_t* align_pairs = sl.cand.p;
             int64_t n_align = found;
             if (sl.mlp && found > 0) {
@@ -259,6 +269,7 @@ void worker(swgb_server* s, int slot_id) {
                 if (rc) return fail_batch(std::string("filter: ") + swgb_last_error(sl.ctx), rc);
                 align_pairs = sl.kept.p;
             }
+            lap(2);
             SCK(sl.rec.need(std::max<int64_t>(n_align, 1)));
             SCK(sl.ident.need(std::max<int64_t>(n_align, 1)));
             if (n_align > 0) {
@@ -269,6 +280,7 @@ void worker(swgb_server* s, int slot_id) {
                 if (!rc) rc = swgb_sync(sl.ctx, sl.stream);
                 if (rc) return fail_batch(std::string("align: ") + swgb_last_error(sl.ctx), rc);
             }
+            lap(3);
             // results back, split per request (pairs are ordered by query)
             std::vector<int32_t> hp((size_t)(2 * n_align)), hc((size_t)found);
             std::vector<swgb_record> hr((size_t)n_align);
@@ -315,6 +327,9 @@ void worker(swgb_server* s, int slot_id) {
                     ++p;
                 }
             }
+            lap(4);
+            for (auto& r : batch)
+                for (int k = 0; k < SWGB_SERVER_STAGES; ++k) r->stage_ms[k] = stage[k];
             finish(s, batch, SWGB_OK, "");
             return 0;
         };
@@ -441,6 +456,7 @@ SWGB_EXPORT int swgb_server_wait(swgb_server* s, int64_t ticket, int64_t timeout
     out->batch_id = r->batch_id;
     out->slot = r->slot;
     out->error = r->error.c_str();
+    for (int k = 0; k < SWGB_SERVER_STAGES; ++k) out->stage_ms[k] = r->stage_ms[k];
     return SWGB_OK;
 }
 

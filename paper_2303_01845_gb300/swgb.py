@@ -91,7 +91,7 @@ class swgb_server_result(ctypes.Structure):
                 ("counts", ctypes.POINTER(ctypes.c_int32)), ("records", ctypes.POINTER(ctypes.c_int32)),
                 ("identity", ctypes.POINTER(ctypes.c_int32)), ("queue_ms", ctypes.c_double),
                 ("latency_ms", ctypes.c_double), ("batch_id", ctypes.c_int64), ("slot", ctypes.c_int32),
-                ("error", ctypes.c_char_p)]
+                ("error", ctypes.c_char_p), ("stage_ms", ctypes.c_double * 5)]
 
 
 # (name, restype, argtypes) of every exported function
@@ -636,7 +636,9 @@ class Server:
     def wait(self, ticket, timeout_ms=-1, release=True):
         """Results of a request as numpy copies: pairs [P, 2], counts [P],
         records [P, 5], identity [P, 3], plus candidates, latency_ms,
-        queue_ms, batch_id, slot."""
+        queue_ms, batch_id, slot and stage_ms (host wall time of the batch's
+        stages: queries loaded, candidates, filter, alignment + identity,
+        results back)."""
         r = swgb_server_result()
         rc = load().swgb_server_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r))
         if rc != SWGB_OK:
@@ -653,7 +655,7 @@ class Server:
         out = {"pairs": arr(r.pairs, (n, 2)), "counts": arr(r.counts, (n,)),
                "records": arr(r.records, (n, 5)), "identity": arr(r.identity, (n, 3)),
                "candidates": r.n_candidates, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms,
-               "batch_id": r.batch_id, "slot": r.slot}
+               "batch_id": r.batch_id, "slot": r.slot, "stage_ms": list(r.stage_ms)}
         if release:
             load().swgb_server_release(self.handle, int(ticket))
         return out

@@ -227,4 +227,7 @@ def test_server_rejects_bad_requests(setup, torch_mod, mat):
     assert e.value.code == swgb.SWGB_EINVAL
     res = srv.wait(srv.submit(codes, offs))
     assert res["candidates"] >= len(res["records"])
+    # the batch's stage times are host wall times inside the request's latency
+    assert len(res["stage_ms"]) == 5 and min(res["stage_ms"]) >= 0.0
+    assert sum(res["stage_ms"]) <= res["latency_ms"] + 1e-3
     srv.close()
