@@ -580,6 +580,8 @@ constexpr int kIdSmallCols = 64;               // spans of up to 64 columns: 8-l
 constexpr int kIdMidCols = 128;                // up to 128 columns: 16-lane groups
 constexpr int kIdClasses = 4;
 constexpr int kIdCoopCols = 2048;              // spans of >= 8 chunks: one block per span
+constexpr int kIdCoopColsSmall = 1024;         // >= 4 chunks, when the batch leaves warps idle
+constexpr int kIdSmallBatchPerSM = 64;         // pairs per SM up to which a batch counts as small
 constexpr int kIdSpinLimit = 1 << 25;          // bounded wait on the previous chunk's progress
 constexpr int32_t kNegInf = -(1 << 28);
 
@@ -597,6 +599,7 @@ struct IdentArgs {
     int8_t mat[kAlpha * kAlpha];
     int32_t go, ge;
     int32_t id_num, id_den, cov_num, cov_den;
+    int32_t coop_cols;         // spans of at least this many columns go cooperative
     int32_t* out;              // [n_pairs][3]: matches, columns, pass
     IdBnd* bnd;                // per-warp boundary columns, one entry per row
     int64_t bnd_stride;
@@ -671,7 +674,7 @@ __global__ void ident_classify_kernel(IdentArgs a) {
         }
         const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
         int64_t* list = a.lists + cls * a.n_pairs;
-        if (cls >= 2 && m >= kIdCoopCols) {
+        if (cls >= 2 && m >= a.coop_cols) {
             // spans of many chunks at the front of the list (the cooperative
             // launch takes them), the rest from its back
             list[(int64_t)atomicAdd(&a.ctr[5 + (cls - 2)], 1ull)] = p;
@@ -688,12 +691,17 @@ __global__ void ident_classify_kernel(IdentArgs a) {
 // columns).  PROF: lane-private substitution profile in shared memory
 // (prof[letter] = the 8 scores of the lane's columns) instead of one lookup
 // per cell.
+// PF: the letter, its profile word and lane 0's boundary entry are fetched
+// ahead of the step that uses them.  That takes their latency off the
+// step's dependency chain, which bounds a warp that runs alone (small
+// batches, cooperative spans); a full GPU hides it with other warps, and
+// there the extra instructions would cost throughput.
 // COOP (G = 32): the kIdWarps warps of a block share one span, warp w taking
 // chunks w, w + kIdWarps, ...; a chunk's boundary column goes to its warp's
 // buffer, and the next chunk's lane 0 waits (bounded) until the producing
 // warp's progress counter in shared memory passes the row it needs.  Chunk
 // c's progress is published as c (n + 1) + row, so the counters only grow.
-template <int G, class St, bool PROF, bool COOP = false>
+template <int G, class St, bool PROF, bool COOP, bool PF>
 __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
     static_assert(!COOP || G == 32, "cooperative spans use 32-lane chunks");
     constexpr int GROUPS = 32 / G;
@@ -789,6 +797,38 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
             int32_t hd_next = c0 == 0 ? 0 : -(oe + ge * (c0 - 1));
             St sd_next = 0;
             const bool read_b = G == 32 && c > 0 && gl == 0;
+            // the letter of span row `row` (any code outside the span: its
+            // cells are not computed)
+            auto letter = [&](int row) -> int { return row >= 1 && row <= n ? qs[row - 1] : 0; };
+            // lane 0 of a later chunk: the previous chunk's boundary at `row`
+            auto boundary = [&](int row) -> IdBnd {
+                if (COOP) {
+                    // the previous chunk's warp must have finished this row
+                    const long long want = (long long)(c - 1) * (n + 1) + row;
+                    volatile long long* prog = s_prog + (c - 1) % kIdWarps;
+                    volatile int* abort_flag = &s_abort;
+                    int spins = 0;
+                    while (*prog < want && !*abort_flag && ++spins < kIdSpinLimit) {
+                    }
+                    if (spins >= kIdSpinLimit) {
+                        *abort_flag = 1;
+                        atomicMax(a.status, 4);
+                    }
+                    __threadfence_block();
+                }
+                return rbuf[row];
+            };
+            // PF: the letter two rows on, its profile word and the boundary
+            // entry one row on
+            int qc_next = 0, qc_after = 0;
+            uint2 pw_next = make_uint2(0u, 0u);
+            IdBnd b_next{kNegInf, kNegInf, 0, 0};
+            if constexpr (PF) {
+                qc_next = letter(1 - gl);
+                qc_after = letter(2 - gl);
+                if (PROF) pw_next = prof[qc_next];
+                if (read_b && n >= 1) b_next = boundary(1);
+            }
             for (int t = 0; t < n_w + G - 1; ++t) {
                 const int arow = t - gl + 1;
                 const int32_t up_h = __shfl_up_sync(0xffffffffu, h_out, 1, G);
@@ -799,6 +839,15 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                 St shl = up_sh, sel = up_se;
                 const int32_t hd = hd_next;
                 const St sd = sd_next;
+                int qc = 0;
+                uint2 pw = make_uint2(0u, 0u);
+                if constexpr (PF) {
+                    qc = qc_next;
+                    pw = pw_next;
+                    qc_next = qc_after;
+                    if (PROF) pw_next = prof[qc_next];
+                    qc_after = letter(arow + 2);
+                }
                 if (gl == 0) {
                     if (!read_b) {
                         hl = -(oe + ge * (arow - 1));   // H(a, 0)
@@ -806,21 +855,13 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                         shl = 0;
                         sel = 0;
                     } else if (arow >= 1 && arow <= n) {
-                        if (COOP) {
-                            // the previous chunk's warp must have finished this row
-                            const long long want = (long long)(c - 1) * (n + 1) + arow;
-                            volatile long long* prog = s_prog + (c - 1) % kIdWarps;
-                            volatile int* abort_flag = &s_abort;
-                            int spins = 0;
-                            while (*prog < want && !*abort_flag && ++spins < kIdSpinLimit) {
-                            }
-                            if (spins >= kIdSpinLimit) {
-                                *abort_flag = 1;
-                                atomicMax(a.status, 4);
-                            }
-                            __threadfence_block();
+                        IdBnd v;
+                        if constexpr (PF) {
+                            v = b_next;
+                            if (arow + 1 <= n) b_next = boundary(arow + 1);
+                        } else {
+                            v = boundary(arow);
                         }
-                        const IdBnd v = rbuf[arow];
                         hl = v.h;
                         el = v.e;
                         shl = S::narrow(v.sh);
@@ -828,9 +869,10 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                     }
                 }
                 if (arow >= 1 && arow <= n && c0 < m) {
-                    const int qc = qs[arow - 1];
-                    uint2 pw = make_uint2(0u, 0u);
-                    if (PROF) pw = prof[qc];
+                    if constexpr (!PF) {
+                        qc = qs[arow - 1];
+                        if (PROF) pw = prof[qc];
+                    }
                     int32_t hleft = hl, eleft = el, hdiag = hd;
                     St shleft = shl, seleft = sel, sdiag = sd;
 #pragma unroll
@@ -1587,6 +1629,14 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     a.cov_den = th->cov_den;
     a.out = reinterpret_cast<int32_t*>(out);
     a.status = S->status;
+    // A batch that leaves warps idle (serving batches of a few thousand
+    // pairs) is bound by its longest spans, each walked by one warp: there
+    // spans of 4+ chunks go cooperative, on up to 4 blocks per SM.  A large
+    // batch fills the SMs anyway and keeps the cooperative launch for the
+    // longest spans, beside the regular ones.
+    const bool small_batch = n_pairs <= (int64_t)ctx->sm_count * kIdSmallBatchPerSM;
+    a.coop_cols = small_batch ? kIdCoopColsSmall : kIdCoopCols;
+    const int coop_blocks_per_sm = small_batch ? 4 : 2;
     // one boundary column per resident warp of the large classes (rows of the
     // longest query + 1)
     const int64_t max_rows = queries->max_len + 1;
@@ -1604,7 +1654,7 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     CK(cudaStreamSynchronize(st), "stream sync");
     int32_t launches = 1;
     const int64_t resident_blocks = (int64_t)ctx->sm_count * 8;
-    // classes 2 and 3 split: spans of >= kIdCoopCols columns at the front of
+    // classes 2 and 3 split: spans of >= coop_cols columns at the front of
     // their lists go to the cooperative launches, the rest to the regular ones
     const int64_t coop_n[2] = {(int64_t)cnt[4], (int64_t)cnt[5]};
     const int64_t reg_n[kIdClasses] = {(int64_t)cnt[0], (int64_t)cnt[1], (int64_t)cnt[2], (int64_t)cnt[3]};
@@ -1619,7 +1669,7 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     }
     int coop_blocks[2] = {0, 0};
     for (int k = 0; k < 2; ++k)
-        coop_blocks[k] = (int)std::min<int64_t>(coop_n[k], (int64_t)ctx->sm_count * 2);
+        coop_blocks[k] = (int)std::min<int64_t>(coop_n[k], (int64_t)ctx->sm_count * coop_blocks_per_sm);
     const int64_t coop_warps = (int64_t)std::max(coop_blocks[0], coop_blocks[1]) * kIdWarps;
     if (bnd_warps + coop_warps > 0)
         CK(grow(&S->bnd, &S->bnd_cap, (bnd_warps + coop_warps) * max_rows), "identity scratch");
@@ -1644,8 +1694,8 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         b.back_base = n_pairs - 1;
         b.bnd = S->bnd + bnd_warps * max_rows;
         b.ctr = S->ctr + 12 + k;
-        if (k == 0) ident_kernel<32, uint32_t, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
-        else ident_kernel<32, uint64_t, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
+        if (k == 0) ident_kernel<32, uint32_t, true, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
+        else ident_kernel<32, uint64_t, true, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
         CK(cudaGetLastError(), "ident kernel (cooperative)");
         launches += 1;
     }
@@ -1662,10 +1712,17 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         b.ctr = S->ctr + 8 + cls;
         const int blocks = blocks_of[cls];
         cudaStream_t s = cls >= 2 ? st : side;
-        if (cls == 0) ident_kernel<8, uint32_t, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
-        else if (cls == 1) ident_kernel<16, uint32_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
-        else if (cls == 2) ident_kernel<32, uint32_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
-        else ident_kernel<32, uint64_t, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        if (small_batch) {
+            if (cls == 0) ident_kernel<8, uint32_t, false, false, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else if (cls == 1) ident_kernel<16, uint32_t, true, false, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else if (cls == 2) ident_kernel<32, uint32_t, true, false, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else ident_kernel<32, uint64_t, true, false, true><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        } else {
+            if (cls == 0) ident_kernel<8, uint32_t, false, false, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else if (cls == 1) ident_kernel<16, uint32_t, true, false, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else if (cls == 2) ident_kernel<32, uint32_t, true, false, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
+            else ident_kernel<32, uint64_t, true, false, false><<<blocks, kIdWarps * 32, 0, s>>>(b);
+        }
         CK(cudaGetLastError(), "ident kernel");
         launches += 1;
     }

@@ -300,6 +300,27 @@ def test_identity_cooperative_spans_match_oracle(aligner, torch_mod, oracle_mod,
     assert ((rec[:, 4] - rec[:, 3] + 1) >= 2048).sum() >= 3
 
 
+def test_identity_large_batch_keeps_mid_spans_regular(aligner, torch_mod, oracle_mod, mat):
+    """A batch of more than 64 pairs per SM fills the GPU: there only spans of
+    2,048+ columns go cooperative, those of 1,024..2,047 columns stay on one
+    warp each (in a small batch both go cooperative)."""
+    n_small = torch_mod.cuda.get_device_properties(0).multi_processor_count * 64 + 500
+    long_wl = workload.generate(workload.Spec("idbig", 4, "uniform", 2300, 2600, seed=51,
+                                              homologous_fraction=1.0), mat)
+    mid_wl = workload.generate(workload.Spec("idmid", 4, "uniform", 1100, 1500, seed=52,
+                                             homologous_fraction=1.0), mat)
+    short_wl = workload.generate(workload.Spec("idshort", n_small, "uniform", 20, 60, seed=53), mat)
+    parts = [(long_wl, 4), (mid_wl, 4), (short_wl, n_small)]
+    qs = [w.q_res[w.q_off[i]:w.q_off[i + 1]] for w, n in parts for i in range(n)]
+    rs = [w.r_res[w.r_off[i]:w.r_off[i + 1]] for w, n in parts for i in range(n)]
+    rq, oq = pack(qs)
+    rr, orr = pack(rs)
+    pairs = np.array([[k, k] for k in range(len(qs))], np.int32)
+    ident, rec = identity_case(aligner, torch_mod, oracle_mod, mat, rq, oq, rr, orr, pairs)
+    cols = rec[:8, 4] - rec[:8, 3] + 1
+    assert (cols[:4] >= 2048).sum() >= 2 and ((cols[4:] >= 1024) & (cols[4:] < 2048)).sum() >= 2
+
+
 def test_identity_of_very_long_self_alignments(aligner, torch_mod, mat):
     """Closed form where the oracle's traceback matrix would not fit: a
     sequence of standard letters aligned with itself scores the sum of its
