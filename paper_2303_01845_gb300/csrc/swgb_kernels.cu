@@ -596,10 +596,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             __syncwarp();
 
             // ---- wavefront over the streamed query
-            // Row state of the last two steps: the step loop is unrolled by two
+            // Row state of the last two steps: the step loop is unrolled by four
             // and alternates the roles of HopA / HopB (and of the profile words
             // pwA / pwB), so the previous step's registers stay available
-            // without copies.  Between pairs of steps the state is in the A set.
+            // without copies.  Between groups of steps the state is in the A set.
             uint32_t HopA[R], HopB[R], F[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -802,18 +802,20 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 hin = h_next;
             };
 
+            // Steps go in fours with one exit test per group, so the four steps
+            // are straight-line code apart from the rare event branches.  Up to
+            // three steps run past the last: every lane is then past its last
+            // position and computes pad cells (each scores below a real cell
+            // feeding it, so it cannot be the pair's maximum; boundary rows are
+            // guarded by position), and in the reverse pass a step past stop_w
+            // cannot record an earlier cell.  The group ends in the A set.
             int t = 0;
-            for (;;) {
-                if (!(t < steps && t <= stop_w)) break;
+            while (t < steps && t <= stop_w) {
                 step(t, HopA, HopB, pwA, pwB);
-                ++t;
-                if (!(t < steps && t <= stop_w)) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) HopA[r] = HopB[r];
-                    break;
-                }
-                step(t, HopB, HopA, pwB, pwA);
-                ++t;
+                step(t + 1, HopB, HopA, pwB, pwA);
+                step(t + 2, HopA, HopB, pwA, pwB);
+                step(t + 3, HopB, HopA, pwB, pwA);
+                t += 4;
             }
             // a run of events still open at the last step
 #pragma unroll
