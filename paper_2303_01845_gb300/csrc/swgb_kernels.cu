@@ -399,7 +399,7 @@ __device__ __forceinline__ bool better(int v, int i, int j, int bv, int bi, int 
 // ---------------------------------------------------------------------------
 constexpr int kSmatBytes = kProfileRows * kMatStride;   // 800
 constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
-constexpr int kBoundEvery = 8;   // steps between refreshes of the group's score bound
+constexpr int kBoundEvery = 16;  // steps between refreshes of the group's score bound
 
 // bytes of profile a warp stages: per group and pair, prof_rows x G x LS
 __host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16, int prof_rows) {
@@ -648,6 +648,11 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // are not kept yet, else 0
             uint32_t pend = 0;
             uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
+            // multiplier and addend that give lane 0 of a group HZ for its
+            // inputs from above (one-tile wavefronts; run-time values, so the
+            // product is issued as a multiply-add, not a select)
+            const uint32_t not0 = gl == 0 ? 0u : one;
+            const uint32_t hz0 = gl == 0 ? HZ : 0u;
 
             // The step loop, compiled twice for the 32-lane tiles: with the
             // chunk-boundary exchange (BND, references longer than one tile) and
@@ -683,8 +688,11 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // initial state unchanged; after its last position it computes pad
             // cells, which score below the best real cell feeding them and can
             // never be the pair's maximum.  Only the boundary store is guarded.
+            // last marks the fourth step of a group (t % 4 == 3; a literal at
+            // every call, folded once inlined): only there can the batch and
+            // bound periods (multiples of four) end.
             auto step = [&](int t, const uint32_t (&Hp)[R], uint32_t (&Hn)[R],
-                            const ProfWords<LS> (&pw)[PACK], ProfWords<LS> (&pwn)[PACK]) {
+                            const ProfWords<LS> (&pw)[PACK], ProfWords<LS> (&pwn)[PACK], bool last) {
                 const int i = t - gl;
 #pragma unroll
                 for (int h = 0; h < PACK; ++h) {
@@ -703,11 +711,6 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                         hin = take ? bcur.y : HZ;
                     }
                     if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
-                } else {
-                    if (gl == 0) {
-                        ein = HZ;
-                        hin = HZ;
-                    }
                 }
                 // phase 1, independent rows: U = max(Hdiag + s, F, 0) - (o + e)
 #pragma unroll
@@ -762,7 +765,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 // the batch of the steps from t + 1 on was loaded a period ago;
                 // load the one after it
                 if constexpr (kBatch < kBoundEvery) {
-                    if ((t & (kBatch - 1)) == kBatch - 1) {
+                    if (last && (t & (kBatch - 1)) == kBatch - 1) {
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
                             xb[h] = xc[h];
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                         }
                     }
                 }
-                if ((t & (kBoundEvery - 1)) == kBoundEvery - 1) {
+                if (last && (t & (kBoundEvery - 1)) == kBoundEvery - 1) {
                     if constexpr (kBatch == kBoundEvery) {
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
@@ -798,8 +801,15 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                         stop_w = stop;
                     }
                 }
-                ein = e_next;
-                hin = h_next;
+                if constexpr (BND) {
+                    ein = e_next;
+                    hin = h_next;
+                } else {
+                    // lane 0 of a group takes "minus infinity" from above; as a
+                    // multiply-add (x * 0 + HZ, or x * 1 + 0) on the FMA pipe
+                    ein = e_next * not0 + hz0;
+                    hin = h_next * not0 + hz0;
+                }
             };
 
             // Steps go in fours with one exit test per group, so the four steps
@@ -811,10 +821,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // cannot record an earlier cell.  The group ends in the A set.
             int t = 0;
             while (t < steps && t <= stop_w) {
-                step(t, HopA, HopB, pwA, pwB);
-                step(t + 1, HopB, HopA, pwB, pwA);
-                step(t + 2, HopA, HopB, pwA, pwB);
-                step(t + 3, HopB, HopA, pwB, pwA);
+                step(t, HopA, HopB, pwA, pwB, false);
+                step(t + 1, HopB, HopA, pwB, pwA, false);
+                step(t + 2, HopA, HopB, pwA, pwB, false);
+                step(t + 3, HopB, HopA, pwB, pwA, true);
                 t += 4;
             }
             // a run of events still open at the last step
