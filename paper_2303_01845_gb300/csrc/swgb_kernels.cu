@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             uint32_t lb1 = L::addmax(T, MONE, lb);  // per half max(lb, T - 1)
             // the kept event's row values of each half; on the packed path two
             // rows per register (row 2k low, row 2k + 1 high)
-            constexpr int NS = P16 ? R / 2 : R;
+            constexpr int NS = P16 ? (R + 1) / 2 : R;   // odd R: the last high half unused
             uint32_t snap[PACK][NS];
             int si[PACK], sv[PACK];
 #pragma unroll
@@ -645,8 +645,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 xc[h] = code_at(h, 2 + kBatch + gl);   // steps kBatch .. 2 kBatch - 1
             }
             // per half 1 where the previous step had an event whose registers
-            // are not kept yet, else 0
-            uint32_t pend = 0;
+            // are not kept yet, else 0; endp: per half 1 where a run of events
+            // ended at the previous step (its last event one step before that),
+            // with the event's value in lbp
+            uint32_t pend = 0, endp = 0, lbp = lb;
             uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
             // multiplier and addend that give lane 0 of a group HZ for its
             // inputs from above (one-tile wavefronts; run-time values, so the
@@ -662,18 +664,19 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             uint2 bcur = make_uint2(HZ, HZ);
             if (BND && read_bnd && ls_c > 0) bcur = bnd[0];
 
-            // keeps the registers of an event at streamed position ii (Hp holds
-            // that step's values) as half h's candidate
-            auto keep = [&](int h, int ii, const uint32_t (&Hp)[R]) {
+            // keeps the registers of an event of value v at streamed position
+            // ii (Hs holds that step's values) as half h's candidate
+            auto keep = [&](int h, int ii, const uint32_t (&Hs)[R], int v) {
                 si[h] = ii;
-                sv[h] = L::get(lb, h);
+                sv[h] = v;
                 if constexpr (P16) {
 #pragma unroll
                     for (int k = 0; k < NS; ++k)
-                        snap[h][k] = prmt(Hp[2 * k], Hp[2 * k + 1], h ? 0x7632u : 0x5410u);
+                        snap[h][k] = prmt(Hs[2 * k], Hs[2 * k + 1 < R ? 2 * k + 1 : 2 * k],
+                                          h ? 0x7632u : 0x5410u);
                 } else {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) snap[h][r] = Hp[r];
+                    for (int r = 0; r < R; ++r) snap[h][r] = Hs[r];
                 }
                 if (REV && sv[h] == target[h] + zero_h && ii < fi[h]) fi[h] = ii;
             };
@@ -712,6 +715,15 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     }
                     if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
                 }
+                // A run of events that ended at the previous step had its last
+                // event two steps back, whose row state is still in Hn until
+                // phase 1 overwrites it: keep it now.  The test reads a flag set
+                // a step ago, so no branch waits on the last step's maximum.
+                if (endp != 0) {
+#pragma unroll
+                    for (int h = 0; h < PACK; ++h)
+                        if (L::get(endp, h) != 0) keep(h, i - 2, Hn, L::get(lbp, h));
+                }
                 // phase 1, independent rows: U = max(Hdiag + s, F, 0) - (o + e)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
@@ -746,18 +758,14 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     // T, i.e. m > max(lb, T - 1) = lb1.  Events come in runs while
                     // an alignment grows through the lane's rows; only the last of
                     // a run can hold the lane's maximum, so its registers are kept
-                    // at the step after the run ends, from Hp.
+                    // once the run has ended (at the start of the step after next).
                     const uint32_t m = tree_max<P16, R>(Hn, lb);
                     const uint32_t nlb1 = L::max3(lb1, m, m);
                     // nlb1 >= lb1 in each half, so the 32-bit difference is exact
                     // per half; up = 1 in the halves with an event, else 0
                     const uint32_t up = L::min3(nlb1 + lb1 * neg_one, ONE, ONE);
-                    const uint32_t ended = pend & ~up;
-                    if (ended != 0) {
-#pragma unroll
-                        for (int h = 0; h < PACK; ++h)
-                            if (L::get(ended, h) != 0) keep(h, i - 1, Hp);
-                    }
+                    endp = pend & ~up;
+                    lbp = lb;   // the previous step's maximum: its event's value
                     pend = up;
                     lb = m;
                     lb1 = nlb1;
@@ -827,10 +835,13 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 step(t + 3, HopB, HopA, pwB, pwA, true);
                 t += 4;
             }
-            // a run of events still open at the last step
+            // a run that ended at the last step (its event one step before, in
+            // the B set), then a run still open at the last step (A set)
 #pragma unroll
-            for (int h = 0; h < PACK; ++h)
-                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA);
+            for (int h = 0; h < PACK; ++h) {
+                if (L::get(endp, h) != 0) keep(h, t - 2 - gl, HopB, L::get(lbp, h));
+                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA, L::get(lb, h));
+            }
             };
             if constexpr (G == 32) {
                 if (nch > 1) wavefront(std::true_type{});
@@ -936,7 +947,10 @@ DPFn dp_pick(int shape) {
         case 9: return dp_fn<9, P16, REV>();
         case 10: return dp_fn<10, P16, REV>();
         case 11: return dp_fn<11, P16, REV>();
-        default: return dp_fn<12, P16, REV>();
+        case 12: return dp_fn<12, P16, REV>();
+        case 13: return dp_fn<13, P16, REV>();
+        case 14: return dp_fn<14, P16, REV>();
+        default: return dp_fn<15, P16, REV>();
     }
 }
 
