@@ -47,20 +47,17 @@ struct SeqView {
 // A pair's DP is laid out with the reference along the lanes ("held", rows of
 // a tile) and the query streamed through the wavefront.  Tile shapes: G lanes
 // per pair group x R rows per lane.
-//   shape: 0     1      2     3      4      5      6      7      8
-//   (G,R): (4,8) (4,12) (8,8) (8,12) (16,8) (16,10) (16,12) (16,14) (16,16)
-//   shape: 9       10      11      12      13      14      15
-//   (G,R): (32,10) (32,11) (32,12) (32,13) (32,14) (32,15) (32,16)
-// (32,8) would never win over (16,16), which has the same rows and half the
-// wavefront fill.  The 32-lane tiles step by one row per lane (32 rows), the
-// smaller ones by two: the 32-lane tiles hold most of the cells, and finer
-// steps cut the rows padded past the end of the reference.  Shapes from kFirstChunkable on (one group per warp) also
+//   shape: 0     1      2     3      4 .. 12               13 .. 20
+//   (G,R): (4,8) (4,12) (8,8) (8,12) (16,8) .. (16,16)     (32,9) .. (32,16)
+// The 16- and 32-lane tiles step by one row per lane (16 or 32 rows), which
+// keeps the rows padded past the end of the reference few; (32,8) would never
+// win over (16,16), which has the same rows and half the wavefront fill.  Shapes from kFirstChunkable on (one group per warp) also
 // cover references longer than one tile, in chunks of G*R rows.
-constexpr int kNumShapes = 16;
-constexpr int kFirstChunkable = 9;
-__host__ __device__ constexpr int shape_G(int s) { return s < 2 ? 4 : s < 4 ? 8 : s < 9 ? 16 : 32; }
+constexpr int kNumShapes = 21;
+constexpr int kFirstChunkable = 13;
+__host__ __device__ constexpr int shape_G(int s) { return s < 2 ? 4 : s < 4 ? 8 : s < 13 ? 16 : 32; }
 __host__ __device__ constexpr int shape_R(int s) {
-    return s < 4 ? ((s & 1) ? 12 : 8) : s < 9 ? 8 + 2 * (s - 4) : 10 + (s - 9);
+    return s < 4 ? ((s & 1) ? 12 : 8) : s < 13 ? 8 + (s - 4) : 9 + (s - 13);
 }
 // bytes of profile per lane and query letter: R rounded up to whole words
 __host__ __device__ constexpr int shape_LS(int s) { return (shape_R(s) + 3) / 4 * 4; }

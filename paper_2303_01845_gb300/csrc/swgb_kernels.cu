@@ -950,7 +950,12 @@ DPFn dp_pick(int shape) {
         case 12: return dp_fn<12, P16, REV>();
         case 13: return dp_fn<13, P16, REV>();
         case 14: return dp_fn<14, P16, REV>();
-        default: return dp_fn<15, P16, REV>();
+        case 15: return dp_fn<15, P16, REV>();
+        case 16: return dp_fn<16, P16, REV>();
+        case 17: return dp_fn<17, P16, REV>();
+        case 18: return dp_fn<18, P16, REV>();
+        case 19: return dp_fn<19, P16, REV>();
+        default: return dp_fn<20, P16, REV>();
     }
 }
 

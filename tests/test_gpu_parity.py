@@ -100,15 +100,16 @@ def test_matrices_at_the_packed_score_range(aligner, oracle_mod, plain10k):
 
 
 HELD_LENGTHS = [1, 2, 7, 8, 9, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129,
-                159, 160, 161, 191, 192, 193, 223, 224, 225, 255, 256, 257, 319, 320, 321,
+                143, 144, 145, 159, 160, 161, 175, 176, 177, 191, 192, 193, 207, 208, 209,
+                223, 224, 225, 239, 240, 241, 255, 256, 257, 287, 288, 289, 319, 320, 321,
                 351, 352, 353, 383, 384, 385, 415, 416, 417, 447, 448, 449, 479, 480, 481,
                 511, 512, 513, 767, 768, 769, 1023, 1024, 1025,
                 1537, 2999]
 STREAM_LENGTHS = [1, 2, 3, 30, 31, 32, 33, 100, 257, 512, 513, 1200]
 
-TILE_SHAPES = [(4, 8), (4, 12), (8, 8), (8, 12), (16, 8), (16, 10), (16, 12), (16, 14), (16, 16),
-               (32, 10), (32, 11), (32, 12), (32, 13), (32, 14), (32, 15), (32, 16)]
-FIRST_CHUNKABLE = 9
+TILE_SHAPES = [(4, 8), (4, 12), (8, 8), (8, 12)] + [(16, r) for r in range(8, 17)] + \
+    [(32, r) for r in range(9, 17)]
+FIRST_CHUNKABLE = 13
 
 
 def tile_of(lq, lr):
