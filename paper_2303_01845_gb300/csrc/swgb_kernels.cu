@@ -397,8 +397,14 @@ __device__ __forceinline__ bool better(int v, int i, int j, int bv, int bi, int 
 // ---------------------------------------------------------------------------
 // The DP kernel
 // ---------------------------------------------------------------------------
-constexpr int kSmatBytes = kProfileRows * kMatStride;   // 800
+// The block's copy of the score table, transposed: tabT[y][x] = table(x, y)
+// for reference code y (0..24, the pad code last) and profile row x (the pad
+// row mapped to the pad code).  Rows are 9 words apart, so lanes reading one
+// word of rows of different codes hit different banks.
+constexpr int kTabTStride = 36;
+constexpr int kTabTBytes = kProfileRows * kTabTStride;   // 900
 constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
+static_assert(kTabTBytes <= kSmatRegion, "transposed table exceeds its region");
 constexpr int kBoundEvery = 16;  // steps between refreshes of the group's score bound
 
 // bytes of profile a warp stages: per group and pair, prof_rows x G x LS
@@ -456,10 +462,13 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
     constexpr int NW = LS / 4;
 
     extern __shared__ __align__(16) uint8_t smem[];
-    int8_t* smat = reinterpret_cast<int8_t*>(smem);
-    for (int k = threadIdx.x; k < kSmatBytes; k += blockDim.x)
-        smat[k] = P16 ? (int8_t)a.sc.profu[k / kMatStride][k % kMatStride]
-                      : a.sc.prof[k / kMatStride][k % kMatStride];
+    uint8_t* tabT = smem;
+    for (int k = threadIdx.x; k < kTabTBytes; k += blockDim.x) {
+        const int y = k / kTabTStride, x = k % kTabTStride;
+        const int xr = x == pad_row ? kPadCode : x;
+        tabT[k] = x >= prows ? (uint8_t)0
+                             : P16 ? a.sc.profu[xr][y] : (uint8_t)a.sc.prof[xr][y];
+    }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5;
@@ -579,18 +588,29 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     y[k] = (k < R && j < lr[h]) ? (REV ? rp[h][lr[h] - 1 - j] : rp[h][j])
                                                 : (uint8_t)kPadCode;
                 }
+                // Four profile rows x = 4 xq .. 4 xq + 3 at a time: word xq of
+                // the transposed table rows of four held letters is a 4 x 4 byte
+                // block, transposed by byte permutes into the four rows' words
+                // for those letters.
                 int8_t* dst = prof + h * PROF + gl * LS;
-                for (int x = 0; x < prows; ++x) {
-                    const int8_t* row = smat + (x == pad_row ? kPadCode : x) * kMatStride;
-                    uint32_t w[NW];
+                for (int xq = 0; 4 * xq < prows; ++xq) {
+                    uint32_t o[4][NW];
 #pragma unroll
                     for (int k4 = 0; k4 < NW; ++k4) {
-                        w[k4] = (uint32_t)(uint8_t)row[y[4 * k4]] |
-                                ((uint32_t)(uint8_t)row[y[4 * k4 + 1]] << 8) |
-                                ((uint32_t)(uint8_t)row[y[4 * k4 + 2]] << 16) |
-                                ((uint32_t)(uint8_t)row[y[4 * k4 + 3]] << 24);
+                        uint32_t w[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            w[j] = *reinterpret_cast<const uint32_t*>(tabT + y[4 * k4 + j] * kTabTStride + 4 * xq);
+                        const uint32_t t0 = prmt(w[0], w[1], 0x5140u), t1 = prmt(w[0], w[1], 0x7362u);
+                        const uint32_t t2 = prmt(w[2], w[3], 0x5140u), t3 = prmt(w[2], w[3], 0x7362u);
+                        o[0][k4] = prmt(t0, t2, 0x5410u);
+                        o[1][k4] = prmt(t0, t2, 0x7632u);
+                        o[2][k4] = prmt(t1, t3, 0x5410u);
+                        o[3][k4] = prmt(t1, t3, 0x7632u);
                     }
-                    store_prof<LS>(dst + x * RS, w);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (4 * xq + m < prows) store_prof<LS>(dst + (4 * xq + m) * RS, o[m]);
                 }
             }
             __syncwarp();
