@@ -135,7 +135,7 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
     if ((e = cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.status, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
-    if ((e = cudaMalloc(&ctx->d_encode_flag, 2 * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ctx->d_encode_flag, 4 * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMemset(ws.status, 0, sizeof(int32_t))) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemset(ws.counters, 0, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "memset");
@@ -205,32 +205,37 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
     cudaStream_t st = (cudaStream_t)stream;
     const bool on_dev = flags & SWGB_SEQ_DEVICE;
 
-    std::vector<int64_t> off((size_t)n_seqs + 1, 0);
+    // Only the first and last offsets are read on the host (the residue range
+    // to copy); the offsets go to the device as given and are checked, measured
+    // and rebased there, so a load costs no host pass over the set.
+    int64_t ends[2] = {0, 0};
     if (n_seqs > 0) {
         if (on_dev) {
-            CK(cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * (n_seqs + 1),
-                               cudaMemcpyDeviceToHost, st), "offsets D2H");
+            CK(cudaMemcpyAsync(&ends[0], offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "offsets D2H");
+            CK(cudaMemcpyAsync(&ends[1], offsets + n_seqs, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+               "offsets D2H");
             CK(cudaStreamSynchronize(st), "stream sync");
         } else {
-            std::memcpy(off.data(), offsets, sizeof(int64_t) * (n_seqs + 1));
+            ends[0] = offsets[0];
+            ends[1] = offsets[n_seqs];
         }
     }
-    const int64_t base = off[0];
-    int64_t max_len = 0;
-    for (int64_t k = 0; k < n_seqs; ++k) {
-        const int64_t len = off[k + 1] - off[k];
-        if (len < 0) return fail(ctx, SWGB_ERANGE, "seqset: offsets decrease");
-        if (len > SWGB_MAX_LENGTH) return fail(ctx, SWGB_ERANGE, "seqset: sequence longer than SWGB_MAX_LENGTH");
-        max_len = std::max(max_len, len);
-    }
-    for (auto& v : off) v -= base;
-    const int64_t total = off[(size_t)n_seqs];
+    const int64_t base = ends[0];
+    const int64_t total = ends[1] - ends[0];
+    if (total < 0) return fail(ctx, SWGB_ERANGE, "seqset: offsets decrease");
     if (total > 0 && !residues) return fail(ctx, SWGB_EINVAL, "seqset: residues is NULL");
 
     CK(grow(&set->d_res, &set->res_capacity, std::max<int64_t>(total, 1)), "seqset alloc");
     CK(grow(&set->d_off, &set->off_capacity, n_seqs + 1), "seqset alloc");
-    CK(cudaMemcpyAsync(set->d_off, off.data(), sizeof(int64_t) * (n_seqs + 1),
-                       cudaMemcpyHostToDevice, st), "offsets H2D");
+    CK(cudaMemsetAsync(ctx->d_encode_flag, 0, 4 * sizeof(int32_t), st), "memset");
+    if (n_seqs > 0) {
+        CK(cudaMemcpyAsync(set->d_off, offsets, sizeof(int64_t) * (n_seqs + 1),
+                           on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "offsets copy");
+        CK(launch_offsets(set->d_off, n_seqs, base, SWGB_MAX_LENGTH, ctx->d_encode_flag + 2, st),
+           "offsets kernel");
+    } else {
+        CK(cudaMemsetAsync(set->d_off, 0, sizeof(int64_t), st), "memset");
+    }
     const uint8_t* src = static_cast<const uint8_t*>(residues);
     if (total > 0) {
         if (on_dev) {
@@ -241,15 +246,16 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
             src = set->d_res;   // encode in place
         }
     }
-    CK(cudaMemsetAsync(ctx->d_encode_flag, 0, 2 * sizeof(int32_t), st), "memset");
     CK(launch_encode(src, set->d_res, total, flags & SWGB_SEQ_ASCII, ctx->d_encode_flag, st), "encode kernel");
-    int32_t fl[2] = {0, 0};
-    CK(cudaMemcpyAsync(fl, ctx->d_encode_flag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "flag D2H");
+    int32_t fl[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(fl, ctx->d_encode_flag, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "flag D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    set->n = n_seqs;
-    set->total = total;
-    set->max_len = max_len;
+    set->n = fl[2] ? 0 : n_seqs;
+    set->total = fl[2] ? 0 : total;
+    set->max_len = fl[3];
     set->max_code = fl[1];
+    if (fl[2] & 1) return fail(ctx, SWGB_ERANGE, "seqset: offsets decrease");
+    if (fl[2] & 2) return fail(ctx, SWGB_ERANGE, "seqset: sequence longer than SWGB_MAX_LENGTH");
     if (fl[0]) return fail(ctx, SWGB_EBADRES, "seqset: residue outside the alphabet");
     return SWGB_OK;
 }

@@ -39,7 +39,8 @@ struct swgb_ctx {
     swgb_record* d_out = nullptr;
     int64_t d_pairs_capacity = 0;
     int64_t d_out_capacity = 0;
-    int32_t* d_encode_flag = nullptr;  // [2]: residue check and largest code of seqset loads
+    int32_t* d_encode_flag = nullptr;  // [4]: residue check, largest code, offsets check, longest
+                                       // sequence of seqset loads
     // resident blocks per SM of each DP kernel, [profile variant][direction]:
     // variant 0 = 21 profile rows (standard letters), 1 = all 25 rows
     int blocks_per_sm[2][2][kClasses][kNumShapes] = {};

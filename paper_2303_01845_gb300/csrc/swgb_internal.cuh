@@ -165,6 +165,10 @@ enum Counter {
 // flags[0] |= 1 on a residue outside the alphabet; flags[1] = max(flags[1], code)
 cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
                           int32_t* flags, cudaStream_t st);
+// Checks the n_seqs + 1 device offsets (flags[0] |= 1 decreasing, 2 longer than
+// max_len; flags[1] = longest length) and subtracts base from each.
+cudaError_t launch_offsets(int64_t* off, int64_t n_seqs, int64_t base, int64_t max_len, int32_t* flags,
+                           cudaStream_t st);
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
                         swgb_record* out, bool reverse, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st);

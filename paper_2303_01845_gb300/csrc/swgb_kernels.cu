@@ -95,6 +95,45 @@ cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii
     return cudaGetLastError();
 }
 
+// Sequence offsets of a set being loaded: flags[0] |= 1 where an offset
+// decreases, |= 2 where a sequence is longer than max_len; flags[1] = max(
+// flags[1], longest length within the limit).  Read only: the lengths are
+// differences of neighbours, so the rebase runs as a separate pass.
+__global__ void offsets_check_kernel(const int64_t* __restrict__ off, int64_t n, int64_t max_len,
+                                     int32_t* flags) {
+    int bad = 0, mx = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const int64_t len = off[k + 1] - off[k];
+        if (len < 0) bad |= 1;
+        else if (len > max_len) bad |= 2;
+        else mx = max(mx, (int)len);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad |= __shfl_xor_sync(kFull, bad, o);
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&flags[0], bad);
+        atomicMax(&flags[1], mx);
+    }
+}
+
+__global__ void offsets_rebase_kernel(int64_t* off, int64_t n, int64_t base) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) off[k] -= base;
+}
+
+cudaError_t launch_offsets(int64_t* off, int64_t n_seqs, int64_t base, int64_t max_len, int32_t* flags,
+                           cudaStream_t st) {
+    if (n_seqs <= 0) return cudaSuccess;
+    int64_t blocks = (n_seqs + 255) / 256;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    offsets_check_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n_seqs, max_len, flags);
+    if (base != 0) offsets_rebase_kernel<<<(unsigned)blocks, 256, 0, st>>>(off, n_seqs + 1, base);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Bucketing: keys + histogram, scan, scatter
 // ---------------------------------------------------------------------------

@@ -278,6 +278,37 @@ def test_ascii_and_host_paths(aligner, oracle_mod, blosum, plain10k, torch_cuda)
     assert_same(got, oracle_records(oracle_mod, sub, blosum, 11, 1), sub)
 
 
+def test_seqset_offsets_checked_and_rebased_on_device(aligner, oracle_mod, blosum, plain10k, torch_cuda):
+    """Sequence-set offsets are checked, measured and rebased on the device:
+    offsets that start past 0 (host and device buffers) give the same records
+    as the same sets starting at 0, the longest length is measured, and
+    offsets that decrease in the middle are refused with ERANGE."""
+    torch = torch_cuda
+    from paper_2303_01845_gb300 import swgb
+    sub = plain10k.subset(np.arange(0, 10000, 97))
+    want = oracle_records(oracle_mod, sub, blosum, 11, 1)
+    shift = 7
+    pad = np.full(shift, 3, np.uint8)
+    q_res = np.concatenate([pad, sub.q_res]); q_off = sub.q_off + shift
+    r_res = np.concatenate([pad, sub.r_res]); r_off = sub.r_off + shift
+    for on_device in (False, True):
+        conv = (lambda a: torch.from_numpy(a).cuda()) if on_device else (lambda a: a)
+        q = aligner.seqset(conv(q_res), conv(q_off))
+        r = aligner.seqset(conv(r_res), conv(r_off))
+        assert swgb.swgb_seqset_info(q.handle) == (len(sub.q_off) - 1, int(np.diff(sub.q_off).max()))
+        got = gpu_records(aligner, sub, params(blosum), sets=(q, r))
+        assert_same(got, want, sub)
+        q.close()
+        r.close()
+    bad = np.array([0, 3, 2, 5], np.int64)   # total >= 0, decreasing in the middle
+    for on_device in (False, True):
+        res = np.zeros(5, np.uint8)
+        args = (torch.from_numpy(res).cuda(), torch.from_numpy(bad).cuda()) if on_device else (res, bad)
+        with pytest.raises(swgb.SwgbError) as ei:
+            aligner.seqset(*args)
+        assert ei.value.code == swgb.SWGB_ERANGE
+
+
 def test_errors_are_reported(aligner, blosum, plain10k, torch_cuda):
     torch = torch_cuda
     from paper_2303_01845_gb300 import swgb
