@@ -193,6 +193,9 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
 // ---------------------------------------------------------------------------
 // Sequence sets
 // ---------------------------------------------------------------------------
+// Host residue uploads of at least this many bytes are split over the streams.
+constexpr int64_t kSplitCopyBytes = 64ll << 20;
+
 SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const int64_t* offsets,
                                  int64_t n_seqs, uint32_t flags, void* stream) {
     if (!set || !set->ctx) return SWGB_EINVAL;
@@ -241,8 +244,28 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
         if (on_dev) {
             src += base;
         } else {
-            CK(cudaMemcpyAsync(set->d_res, src + base, (size_t)total, cudaMemcpyHostToDevice, st),
-               "residues H2D");
+            // large host sets are copied in parts on the caller's stream and the
+            // context's side streams at once, so several copy engines share the
+            // upload; the encode waits for all parts
+            const int parts = total >= kSplitCopyBytes ? swgb_ctx::kSide + 1 : 1;
+            if (parts > 1) {
+                CK(cudaEventRecord(ctx->fork_ev, st), "event");
+                for (int k = 0; k < swgb_ctx::kSide; ++k)
+                    CK(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0), "stream wait");
+            }
+            const int64_t part = (total + parts - 1) / parts;
+            for (int k = 0; k < parts; ++k) {
+                const int64_t b = k * part, e = std::min(total, b + part);
+                if (b < e)
+                    CK(cudaMemcpyAsync(set->d_res + b, src + base + b, (size_t)(e - b), cudaMemcpyHostToDevice,
+                                       k == 0 ? st : ctx->side[k - 1]), "residues H2D");
+            }
+            if (parts > 1) {
+                for (int k = 0; k < swgb_ctx::kSide; ++k) {
+                    CK(cudaEventRecord(ctx->join_ev[k], ctx->side[k]), "event");
+                    CK(cudaStreamWaitEvent(st, ctx->join_ev[k], 0), "stream wait");
+                }
+            }
             src = set->d_res;   // encode in place
         }
     }

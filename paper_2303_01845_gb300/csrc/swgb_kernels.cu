@@ -605,7 +605,16 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             bi[h] = INT_MAX;
             bj[h] = INT_MAX;
         }
-        uint32_t T = HZ;   // lower bound of the final score (tracked units), per half
+        // lower bound of the final score (tracked units), per half.  The reverse
+        // pass knows the score S itself: with T = S a lane has an event only
+        // when it first reaches S, so earlier runs of events cost nothing.
+        uint32_t T = HZ;
+        if constexpr (REV) {
+            if constexpr (P16)
+                T = (uint32_t)(target[0] + zero_h) | ((uint32_t)(target[PACK - 1] + zero_h) << 16);
+            else
+                T = (uint32_t)(target[0] + zero_h);
+        }
         // reverse pass: the score S is known; fi = first streamed step at which
         // this lane recorded a cell of value S, per half
         int fi[PACK];
