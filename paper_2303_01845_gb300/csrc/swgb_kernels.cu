@@ -474,11 +474,11 @@ __device__ __forceinline__ int group_min(int v) {
 //              of each scored pair -> start cell.  The score S is known, so the
 //              pass stops once the wavefront is past the first step holding S.
 //
-// Position of the maximum.  Every lane keeps the running maximum lb of its
-// cells.  When the maximum of a step's R rows passes lb and also reaches T --
-// a lower bound of the pair's final score: the largest lb of the group,
-// refreshed every kBoundEvery steps -- the lane copies its R registers (a
-// snapshot per pair half) and the step.  The first row holding the value is
+// Position of the maximum.  Every lane keeps lb1 = max(its running maximum,
+// T - 1), T a lower bound of the pair's final score (the largest lb1 of the
+// group, refreshed every kBoundEvery steps).  When the maximum of a step's R
+// rows passes lb1 -- it grew and reached T -- the lane copies its R registers
+// (a snapshot per pair half) and the step.  The first row holding the value is
 // read from the snapshot once per chunk.  A lane whose maximum never reached T
 // holds no cell of the final score, so skipping its positions loses nothing;
 // ties with T are recorded.
@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 F[r] = HZ;
             }
             uint32_t hin_prev = HZ;
-            uint32_t lb = HZ;                       // this lane's maximum in this chunk
-            uint32_t lb1 = L::addmax(T, MONE, lb);  // per half max(lb, T - 1)
+            // per half max(this lane's maximum in this chunk, T - 1)
+            uint32_t lb1 = L::addmax(T, MONE, HZ);
             // the kept event's row values of each half; on the packed path two
             // rows per register (row 2k low, row 2k + 1 high)
             constexpr int NS = P16 ? (R + 1) / 2 : R;   // odd R: the last high half unused
@@ -716,7 +716,9 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // are not kept yet, else 0; endp: per half 1 where a run of events
             // ended at the previous step (its last event one step before that),
             // with the event's value in lbp
-            uint32_t pend = 0, endp = 0, lbp = lb;
+            // mp: the last step's maximum (with lb1, before a bound refresh
+            // raised it), i.e. the value of that step's event if it had one
+            uint32_t pend = 0, endp = 0, lbp = lb1, mp = lb1;
             uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
             // multiplier and addend that give lane 0 of a group HZ for its
             // inputs from above (one-tile wavefronts; run-time values, so the
@@ -822,20 +824,20 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 const uint32_t e_next = __shfl_up_sync(kFull, e, 1, G);
                 const uint32_t h_next = __shfl_up_sync(kFull, Hn[R - 1], 1, G);
                 {
-                    // A half has an event when its maximum m passes lb and reaches
-                    // T, i.e. m > max(lb, T - 1) = lb1.  Events come in runs while
-                    // an alignment grows through the lane's rows; only the last of
-                    // a run can hold the lane's maximum, so its registers are kept
-                    // once the run has ended (at the start of the step after next).
-                    const uint32_t m = tree_max<P16, R>(Hn, lb);
-                    const uint32_t nlb1 = L::max3(lb1, m, m);
+                    // A half has an event when the step's maximum passes lb1, i.e.
+                    // it grew the lane's maximum and reached T.  Events come in
+                    // runs while an alignment grows through the lane's rows; only
+                    // the last of a run can hold the lane's maximum, so its
+                    // registers are kept once the run has ended (at the start of
+                    // the step after next).  After an event lb1 is its value.
+                    const uint32_t nlb1 = tree_max<P16, R>(Hn, lb1);
                     // nlb1 >= lb1 in each half, so the 32-bit difference is exact
                     // per half; up = 1 in the halves with an event, else 0
                     const uint32_t up = L::min3(nlb1 + lb1 * neg_one, ONE, ONE);
                     endp = pend & ~up;
-                    lbp = lb;   // the previous step's maximum: its event's value
+                    lbp = mp;    // the previous step's event value, if it had one
+                    mp = nlb1;
                     pend = up;
-                    lb = m;
                     lb1 = nlb1;
                 }
                 // the batch of the steps from t + 1 on was loaded a period ago;
@@ -857,8 +859,8 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                             xc[h] = code_at(h, t + 3 + kBatch + gl);
                         }
                     }
-                    T = group_max<P16, G>(L::max3(lb, T, T));
-                    lb1 = L::addmax(T, MONE, lb);
+                    T = group_max<P16, G>(L::max3(lb1, T, T));
+                    lb1 = L::addmax(T, MONE, lb1);
                     if constexpr (REV) {
                         // once every half of every group has met S at some step,
                         // cells of later steps can no longer be the first such cell
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
                 if (L::get(endp, h) != 0) keep(h, t - 2 - gl, HopB, L::get(lbp, h));
-                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA, L::get(lb, h));
+                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA, L::get(mp, h));
             }
             };
             if constexpr (G == 32) {
@@ -921,10 +923,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // ---- the lane's candidate of this chunk: the recorded step and the
             // first row of the snapshot holding the value, if it is the lane's
             // maximum
-            T = group_max<P16, G>(L::max3(lb, T, T));
+            T = group_max<P16, G>(L::max3(lb1, T, T));
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                if (si[h] >= 0 && sv[h] == L::get(lb, h)) {
+                if (si[h] >= 0 && sv[h] == L::get(lb1, h)) {
                     int row = R - 1;
 #pragma unroll
                     for (int r = R - 1; r >= 0; --r)
