@@ -1,9 +1,11 @@
 """Throughput of batched Smith-Waterman (affine gaps, BLOSUM62, open 11 /
 extend 1) on one GB300, on the seeded 2,000,000-pair log-normal workload.
 
-One step = one call of the whole hot path (device bucketing, forward DP for
+One step = one pass of the whole hot path (device bucketing, forward DP for
 score and end, reverse DP for start, records in pair order) over all pairs,
-inputs resident in HBM.  Prints one JSON line.
+inputs resident in HBM, replayed from a CUDA graph captured once
+(swgb_plan_create; --no-graph times direct swgb_align calls).  Prints one
+JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -47,6 +49,8 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct swgb_align calls instead of replaying a captured CUDA graph")
     ap.add_argument("--tune-pairs", type=int, default=200000,
                     help="pairs of the batch the tile selection is tuned on")
     ap.add_argument("--tile-overhead", type=int, default=-1,
@@ -290,8 +294,15 @@ def run_ours(args):
                                               tune_out, stream)
         del tune_pairs, tune_out
 
+    # the timed step replays the whole pipeline captured once into a CUDA graph
+    # (swgb_plan_*): same kernels and records as swgb_align, no per-launch host work
+    plan = None if args.no_graph else swgb.swgb_plan_create(al.ctx, q.handle, r.handle, pairs, params, out)
+
     def step():
-        swgb.swgb_align(al.ctx, q.handle, r.handle, pairs, params, out, stream)
+        if plan is not None:
+            swgb.swgb_plan_launch(al.ctx, plan, stream)
+        else:
+            swgb.swgb_align(al.ctx, q.handle, r.handle, pairs, params, out, stream)
 
     for _ in range(args.warmup):
         step()
@@ -322,6 +333,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     clock = clocks.summary()
+    if plan is not None:
+        swgb.swgb_plan_destroy(plan)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     cells = stats["forward_cells"]
@@ -356,6 +369,7 @@ def run_ours(args):
                    "reverse_cells": stats["reverse_cells"],
                    "int32_pairs": stats["n_int32_pairs"], "gap_open": 11, "gap_extend": 1,
                    "matrix": "BLOSUM62", "tile_overhead": tile_overhead,
+                   "launch": "direct calls" if plan is None else "CUDA graph (swgb_plan)",
                    "l2": "inputs (%.2f GB of residues) exceed L2; no flush" %
                          ((len(wl.q_res) + len(wl.r_res)) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},

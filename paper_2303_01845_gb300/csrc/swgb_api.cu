@@ -398,6 +398,16 @@ int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, int64_t n_p
     return SWGB_OK;
 }
 
+// Records a timing event on st.  Under stream capture (swgb_plan_create) the
+// event must become an event node of the graph, so that replays record it.
+cudaError_t record_timing(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                                 : cudaEventRecordDefault);
+}
+
 // Enqueues the whole pipeline on st (no allocation: the store is prepared).
 int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_seqset* r,
             const int32_t* pairs, int64_t n_pairs, const swgb_params* params, swgb_record* out,
@@ -418,7 +428,7 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     int launches = 0;
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
     CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * 2 * kNumKernels, st), "memset");
-    if (timed) CK(cudaEventRecord(ctx->ev[0], st), "event");
+    if (timed) CK(record_timing(ctx->ev[0], st), "event");
 
     const SeqView qv = view(q), rv = view(r);
     for (int dir = 0; dir < 2; ++dir) {
@@ -428,7 +438,7 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
         CK(launch_scan(ws, st), "scan kernel");
         CK(launch_scatter(n_pairs, ws, st), "scatter kernel");
         launches += 3;
-        if (timed) CK(cudaEventRecord(ctx->ev[rev ? 3 : 1], st), "event");
+        if (timed) CK(record_timing(ctx->ev[rev ? 3 : 1], st), "event");
         CK(cudaEventRecord(ctx->fork_ev, st), "event");
         for (int k = 0; k < swgb_ctx::kSide; ++k)
             CK(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0), "stream wait");
@@ -465,9 +475,9 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
             CK(cudaEventRecord(ctx->join_ev[k], ctx->side[k]), "event");
             CK(cudaStreamWaitEvent(st, ctx->join_ev[k], 0), "stream wait");
         }
-        if (timed) CK(cudaEventRecord(ctx->ev[rev ? 4 : 2], st), "event");
+        if (timed) CK(record_timing(ctx->ev[rev ? 4 : 2], st), "event");
     }
-    if (timed) CK(cudaEventRecord(ctx->ev[5], st), "event");
+    if (timed) CK(record_timing(ctx->ev[5], st), "event");
     ctx->timed = timed;
     ctx->last_stream = st;
     ctx->last_launches = launches;

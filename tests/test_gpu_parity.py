@@ -413,6 +413,19 @@ def test_plan_replays_the_pipeline(aligner, blosum, plain10k, torch_cuda):
         assert (out.cpu().numpy() == want2).all()
     finally:
         swgb.swgb_plan_destroy(plan)
+    # a plan captured with timing records its kernel times at every replay
+    tprm = swgb.make_params(blosum, 11, 1, timing=True)
+    plan = swgb.swgb_plan_create(aligner.ctx, q.handle, r.handle, pairs, tprm, out)
+    try:
+        for _ in range(2):
+            swgb.swgb_plan_launch(aligner.ctx, plan)
+            swgb.swgb_sync(aligner.ctx)
+            st = aligner.stats()
+            assert st["forward_ms"] > 0 and st["reverse_ms"] > 0
+            assert st["total_ms"] >= st["forward_ms"] + st["reverse_ms"]
+        assert (out.cpu().numpy() == want2).all()
+    finally:
+        swgb.swgb_plan_destroy(plan)
 
 
 def test_tile_selection_does_not_change_records(aligner, blosum, plain10k, torch_cuda):
