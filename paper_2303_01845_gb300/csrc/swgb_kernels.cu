@@ -859,8 +859,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                             xc[h] = code_at(h, t + 3 + kBatch + gl);
                         }
                     }
-                    T = group_max<P16, G>(L::max3(lb1, T, T));
-                    lb1 = L::addmax(T, MONE, lb1);
+                    if constexpr (!REV) {   // the reverse pass's bound is S from the start
+                        T = group_max<P16, G>(L::max3(lb1, T, T));
+                        lb1 = L::addmax(T, MONE, lb1);
+                    }
                     if constexpr (REV) {
                         // once every half of every group has met S at some step,
                         // cells of later steps can no longer be the first such cell
@@ -923,7 +925,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // ---- the lane's candidate of this chunk: the recorded step and the
             // first row of the snapshot holding the value, if it is the lane's
             // maximum
-            T = group_max<P16, G>(L::max3(lb1, T, T));
+            if constexpr (!REV) T = group_max<P16, G>(L::max3(lb1, T, T));
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
                 if (si[h] >= 0 && sv[h] == L::get(lb1, h)) {
