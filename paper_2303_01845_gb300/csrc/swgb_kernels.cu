@@ -444,7 +444,9 @@ constexpr int kTabTStride = 36;
 constexpr int kTabTBytes = kProfileRows * kTabTStride;   // 900
 constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
 static_assert(kTabTBytes <= kSmatRegion, "transposed table exceeds its region");
-constexpr int kBoundEvery = 16;  // steps between refreshes of the group's score bound
+// Steps between refreshes of the group's score bound (forward) and between
+// tests for the end of the reverse pass, whose bound is fixed.
+__host__ __device__ constexpr int bound_every(bool reverse) { return reverse ? 32 : 16; }
 
 // bytes of profile a warp stages: per group and pair, prof_rows x G x LS
 __host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16, int prof_rows) {
@@ -476,7 +478,7 @@ __device__ __forceinline__ int group_min(int v) {
 //
 // Position of the maximum.  Every lane keeps lb1 = max(its running maximum,
 // T - 1), T a lower bound of the pair's final score (the largest lb1 of the
-// group, refreshed every kBoundEvery steps).  When the maximum of a step's R
+// group, refreshed every bound_every steps).  When the maximum of a step's R
 // rows passes lb1 -- it grew and reached T -- the lane copies its R registers
 // (a snapshot per pair half) and the step.  The first row holding the value is
 // read from the snapshot once per chunk.  A lane whose maximum never reached T
@@ -702,6 +704,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // the group by shuffle, and lane 0 reads them from a batch of
             // kBatch letters (xb); the group loads the batch after it (xc) one
             // batch period ahead.
+            constexpr int kBoundEvery = bound_every(REV);
             constexpr int kBatch = G < kBoundEvery ? G : kBoundEvery;
             ProfWords<LS> pwA[PACK], pwB[PACK];
             int xn[PACK], xb[PACK], xc[PACK];
