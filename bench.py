@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct swgb_align calls instead of replaying a captured CUDA graph")
-    ap.add_argument("--tune-pairs", type=int, default=200000,
+    ap.add_argument("--tune-pairs", type=int, default=400000,
                     help="pairs of the batch the tile selection is tuned on")
     ap.add_argument("--tile-overhead", type=int, default=-1,
                     help="fixed tile-cost overhead instead of tuning (profiling runs)")

@@ -199,8 +199,9 @@ int swgb_set_tile_overhead(swgb_ctx* ctx, int overhead);  /* EINVAL unless 0..64
 int swgb_get_tile_overhead(const swgb_ctx* ctx);          /* current value */
 
 /* Times swgb_align on the given batch (device buffers, like swgb_align) for a
- * fixed list of overhead values, keeps the fastest in ctx and reports it and
- * its whole-call time in ms.  Synchronous; out receives the batch's records.
+ * fixed list of overhead values (one warm-up call, then the fastest of three
+ * timed calls each), keeps the fastest in ctx and reports it and its
+ * whole-call time in ms.  Synchronous; out receives the batch's records.
  * The records do not depend on the setting.  Errors: those of swgb_align. */
 int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
                   const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
