@@ -351,10 +351,10 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(al, wl, mat, dev, stream, args)
+        e2e = measure_e2e(al, wl, mat, dev, stream, args, dist, world)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host baseline: N = 1 only
         cpu = cpu_oracle_sample(wl, np.asarray(mat), args.cpu_seconds)
 
     if rank != 0:
@@ -395,10 +395,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def measure_e2e(al, wl, mat, dev, stream, args):
+def measure_e2e(al, wl, mat, dev, stream, args, dist=None, world=1):
     """Same metric through the public host-buffer API: every step loads both
     sequence sets from pinned host memory, copies the pairs in and the records
-    out (swgb_seqset_load + swgb_align_host)."""
+    out (swgb_seqset_load + swgb_align_host).  Whole-job figure: a barrier on
+    both sides, the slowest rank's time, every rank's units."""
     import torch
 
     from paper_2303_01845_gb300 import swgb
@@ -418,18 +419,22 @@ def measure_e2e(al, wl, mat, dev, stream, args):
     step()
     n = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t = time.perf_counter()
     for _ in range(n):
         step()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t) / n
+    dt = max_over_ranks((time.perf_counter() - t) / n, dist, dev)
+    if dist is not None:
+        dist.barrier()
     st = swgb.swgb_last_stats(al.ctx)
     h2d = sum(x.numel() * x.element_size() for x in (q_res, q_off, r_res, r_off, pairs))
     qs.close()
     rs.close()
-    return {"value": st["forward_cells"] / dt / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+    return {"value": world * st["forward_cells"] / dt / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": out.numel() * out.element_size(), "ms_per_step": dt * 1e3,
-            "alignments_per_s": len(wl.pairs) / dt}
+            "alignments_per_s": world * len(wl.pairs) / dt}
 
 
 def search_oracle_sample(fs, mat, target_s, seed=5):
