@@ -196,6 +196,29 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
 // Host residue uploads of at least this many bytes are split over the streams.
 constexpr int64_t kSplitCopyBytes = 64ll << 20;
 
+// Device address of a byte of pinned (page-locked, mapped) host memory, or
+// null for any other pointer.
+static const uint8_t* mapped_byte(const uint8_t* p) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();   // a plain host pointer on some drivers: not an error here
+        return nullptr;
+    }
+    if (pa.type != cudaMemoryTypeHost || pa.devicePointer == nullptr) return nullptr;
+    return static_cast<const uint8_t*>(pa.devicePointer);
+}
+
+// Device address of the host bytes [p, p + n) when all of them are pinned
+// host memory (both ends mapped, n - 1 apart), else null.  Kernels may read
+// such memory in place over the host link.
+static const uint8_t* mapped_host(const uint8_t* p, int64_t n) {
+    const uint8_t* first = mapped_byte(p);
+    if (!first) return nullptr;
+    const uint8_t* last = mapped_byte(p + (n - 1));
+    if (!last || last - first != n - 1) return nullptr;
+    return first;
+}
+
 SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const int64_t* offsets,
                                  int64_t n_seqs, uint32_t flags, void* stream) {
     if (!set || !set->ctx) return SWGB_EINVAL;
@@ -243,6 +266,10 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
     if (total > 0) {
         if (on_dev) {
             src += base;
+        } else if (const uint8_t* mapped = mapped_host(src + base, total)) {
+            // pinned host memory: the encode pass reads it in place over the
+            // host link (no staging copy)
+            src = mapped;
         } else {
             // large host sets are copied in parts on the caller's stream and the
             // context's side streams at once, so several copy engines share the

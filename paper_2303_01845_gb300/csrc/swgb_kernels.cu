@@ -86,12 +86,59 @@ __global__ void encode_kernel(const uint8_t* __restrict__ in, uint8_t* __restric
     if (threadIdx.x == 0) atomicMax(&flags[1], block_max);
 }
 
+// Residues given as codes, 16 per thread: a code of 24 or more becomes 0 and
+// sets flags[0]; flags[1] = max(flags[1], largest code).  Per-byte SIMD compare
+// and max, so the pass moves at copy speed (also when `in` is pinned host
+// memory read over the host link).
+__global__ void encode_codes16_kernel(const uint4* __restrict__ in, uint4* __restrict__ out, int64_t n16,
+                                      int32_t* flags) {
+    __shared__ uint32_t block_max;
+    if (threadIdx.x == 0) block_max = 0;
+    __syncthreads();
+    uint32_t bad = 0, mx = 0;
+    const uint32_t lim = 0x18181818u;   // 24 in every byte
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n16; k += stride) {
+        uint4 v = in[k];
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t over = __vcmpgeu4(w[j], lim);   // 0xff in bytes >= 24
+            bad |= over;
+            w[j] &= ~over;
+            mx = __vmaxu4(mx, w[j]);
+        }
+        out[k] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    mx = max(max(mx & 0xffu, (mx >> 8) & 0xffu), max((mx >> 16) & 0xffu, mx >> 24));
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = max(mx, __shfl_xor_sync(kFull, mx, off));
+        bad |= __shfl_xor_sync(kFull, bad, off);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&block_max, mx);
+    if (__syncthreads_or(bad != 0) && threadIdx.x == 0) atomicOr(&flags[0], 1);
+    if (threadIdx.x == 0) atomicMax(&flags[1], (int32_t)block_max);
+}
+
 cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii,
                           int32_t* flags, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > sm_count() * 32) blocks = sm_count() * 32;
-    encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, n, ascii ? 1 : 0, flags);
+    int64_t head = 0;
+    if (!ascii && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0) {
+        const int64_t n16 = n / 16;
+        if (n16 > 0) {
+            int64_t blocks = (n16 + 255) / 256;
+            if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+            encode_codes16_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(in),
+                                                                    reinterpret_cast<uint4*>(out), n16, flags);
+        }
+        head = n16 * 16;
+    }
+    if (head < n) {
+        int64_t blocks = (n - head + 255) / 256;
+        if (blocks > sm_count() * 32) blocks = sm_count() * 32;
+        encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(in + head, out + head, n - head, ascii ? 1 : 0, flags);
+    }
     return cudaGetLastError();
 }
 

@@ -287,26 +287,39 @@ def test_seqset_offsets_checked_and_rebased_on_device(aligner, oracle_mod, blosu
     from paper_2303_01845_gb300 import swgb
     sub = plain10k.subset(np.arange(0, 10000, 97))
     want = oracle_records(oracle_mod, sub, blosum, 11, 1)
-    shift = 7
-    pad = np.full(shift, 3, np.uint8)
-    q_res = np.concatenate([pad, sub.q_res]); q_off = sub.q_off + shift
-    r_res = np.concatenate([pad, sub.r_res]); r_off = sub.r_off + shift
-    for on_device in (False, True):
-        conv = (lambda a: torch.from_numpy(a).cuda()) if on_device else (lambda a: a)
-        q = aligner.seqset(conv(q_res), conv(q_off))
-        r = aligner.seqset(conv(r_res), conv(r_off))
-        assert swgb.swgb_seqset_info(q.handle) == (len(sub.q_off) - 1, int(np.diff(sub.q_off).max()))
-        got = gpu_records(aligner, sub, params(blosum), sets=(q, r))
-        assert_same(got, want, sub)
-        q.close()
-        r.close()
+    convs = {"host": lambda a: a, "pinned": lambda a: torch.from_numpy(a).pin_memory(),
+             "device": lambda a: torch.from_numpy(a).cuda()}
+    for shift in (0, 7):   # residues read 16 bytes at a time, or byte by byte
+        pad = np.full(shift, 3, np.uint8)
+        q_res = np.concatenate([pad, sub.q_res]); q_off = sub.q_off + shift
+        r_res = np.concatenate([pad, sub.r_res]); r_off = sub.r_off + shift
+        for kind, conv in convs.items():
+            q = aligner.seqset(conv(q_res), conv(q_off))
+            r = aligner.seqset(conv(r_res), conv(r_off))
+            assert swgb.swgb_seqset_info(q.handle) == (len(sub.q_off) - 1, int(np.diff(sub.q_off).max()))
+            got = gpu_records(aligner, sub, params(blosum), sets=(q, r))
+            assert_same(got, want, sub)
+            q.close()
+            r.close()
     bad = np.array([0, 3, 2, 5], np.int64)   # total >= 0, decreasing in the middle
-    for on_device in (False, True):
+    for kind, conv in convs.items():
         res = np.zeros(5, np.uint8)
-        args = (torch.from_numpy(res).cuda(), torch.from_numpy(bad).cuda()) if on_device else (res, bad)
         with pytest.raises(swgb.SwgbError) as ei:
-            aligner.seqset(*args)
+            aligner.seqset(conv(res), conv(bad))
         assert ei.value.code == swgb.SWGB_ERANGE
+    # a code of 24 or more anywhere in a long set (the 16-byte pass) is refused
+    long_res = np.random.default_rng(4).integers(0, 20, size=4000).astype(np.uint8)
+    long_off = np.array([0, 1000, 4000], np.int64)
+    for pos, code in ((0, 24), (1999, 255), (3999, 30)):
+        res = long_res.copy()
+        res[pos] = code
+        for kind, conv in convs.items():
+            with pytest.raises(swgb.SwgbError) as ei:
+                aligner.seqset(conv(res), conv(long_off))
+            assert ei.value.code == swgb.SWGB_EBADRES
+    ok = aligner.seqset(convs["pinned"](long_res), convs["pinned"](long_off))
+    assert swgb.swgb_seqset_info(ok.handle) == (2, 3000)
+    ok.close()
 
 
 def test_errors_are_reported(aligner, blosum, plain10k, torch_cuda):
