@@ -180,7 +180,7 @@ def load(build_if_missing=True):
     if build_if_missing:
         path = _build.build_swgb()
     if not os.path.exists(path):
-        raise ImportError("libswgb.so is not built (%s); run __graft_entry__.build()" % path)
+        raise ImportError("libswgb.so is not built (%s); run paper_2303_01845_gb300.build.build_all()" % path)
     lib = ctypes.CDLL(path)
     for name, res, args in _SIGS:
         fn = getattr(lib, name)
