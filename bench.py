@@ -34,6 +34,7 @@ METRIC = "GCUPS & alignments/s on 1 GB300 (bit-exact); filter recall; p50/p99 la
 ADDMAX_OPS_PER_CELL = 2.5     # five packed 16x2 add-max per two cells
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dp_forward_traffic.json")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_kernels.cu")
+KERNEL_HEADER = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_internal.cuh")
 
 
 def parse():
@@ -92,6 +93,16 @@ def job_rate(units_per_rank, world, steps, total_ms):
 
 def sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def dp_source_sha():
+    """Hash of what the DP kernels' DRAM traffic depends on: the DP section of
+    swgb_kernels.cu (lane arithmetic, the kernel, its dispatch and launch
+    sizes) and swgb_internal.cuh (tile shapes, arguments)."""
+    src = open(KERNEL_SOURCE).read()
+    a = src.index("// Lane arithmetic")
+    b = src.index("// Issue-rate probe")
+    return hashlib.sha256(src[a:b].encode() + open(KERNEL_HEADER, "rb").read()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -246,13 +257,13 @@ def run_reference(args):
 
 
 def traffic_for_current_kernel():
-    """DRAM bytes per forward launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per forward pass from the committed ncu summary, if it was
+    taken on the current DP kernel source (else None)."""
     try:
         rec = json.load(open(PROFILE_SUMMARY))
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_sha") != sha(KERNEL_SOURCE):
+    if rec.get("dp_source_sha") != dp_source_sha():
         return None
     return rec.get("dram_bytes_per_forward_pass")
 

@@ -464,7 +464,7 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
         CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, ca, ws, st), "keys kernel");
         CK(launch_scan(ws, st), "scan kernel");
         CK(launch_scatter(n_pairs, ws, st), "scatter kernel");
-        launches += 3;
+        launches += 4;
         if (timed) CK(record_timing(ctx->ev[rev ? 3 : 1], st), "event");
         CK(cudaEventRecord(ctx->fork_ev, st), "event");
         for (int k = 0; k < swgb_ctx::kSide; ++k)

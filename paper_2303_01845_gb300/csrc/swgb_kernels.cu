@@ -276,40 +276,71 @@ cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs
     return cudaGetLastError();
 }
 
-// Exclusive scan of hist[kNumBins] by one block; also resets the cursors.
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = (kNumBins + kScanThreads - 1) / kScanThreads;
+// Exclusive scan of hist[kNumBins] into scan (and the scatter cursors), in
+// two launches over tiles of kScanTile bins, reads and writes coalesced:
+// scan_tiles_kernel scans each tile locally and leaves the tile's total in the
+// tile's first histogram entry (the histogram is not read again, and only the
+// tile's own block reads that entry); scan_offsets_kernel adds to each tile the
+// totals of the tiles before it.
+constexpr int kScanTile = 1024;
+constexpr int kScanTiles = (kNumBins + kScanTile - 1) / kScanTile;
 
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(Workspace ws) {
-    __shared__ uint32_t part[kScanThreads];
-    const int t = threadIdx.x;
-    const int base = t * kScanPer;
-    uint32_t local = 0;
-    for (int k = 0; k < kScanPer; ++k)
-        if (base + k < kNumBins) local += ws.hist[base + k];
-    part[t] = local;
+// Block-wide inclusive scan of one value per thread (kScanTile threads).
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_sums) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v += o;
+    }
+    if (lane == 31) warp_sums[w] = v;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partial sums
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-        uint32_t v = t >= off ? part[t - off] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[t] - local;  // exclusive prefix of this thread's span
-    for (int k = 0; k < kScanPer; ++k) {
-        const int b = base + k;
-        if (b < kNumBins) {
-            ws.scan[b] = run;
-            ws.cursor[b] = run;
-            run += ws.hist[b];
+    if (w == 0) {
+        uint32_t x = warp_sums[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(kFull, x, off);
+            if (lane >= off) x += o;
         }
+        warp_sums[lane] = x;
     }
-    if (t == kScanThreads - 1) ws.scan[kNumBins] = part[t];
+    __syncthreads();
+    return v + (w > 0 ? warp_sums[w - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_tiles_kernel(Workspace ws) {
+    __shared__ uint32_t warp_sums[32];
+    const int b = blockIdx.x * kScanTile + threadIdx.x;
+    const uint32_t v = b < kNumBins ? ws.hist[b] : 0u;
+    const uint32_t inc = block_inclusive_scan(v, warp_sums);
+    if (b < kNumBins) ws.scan[b] = inc - v;
+    __syncthreads();   // every thread has read its entry before the total overwrites the first
+    if (threadIdx.x == kScanTile - 1) ws.hist[blockIdx.x * kScanTile] = inc;
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_offsets_kernel(Workspace ws) {
+    __shared__ uint32_t offset;
+    if (threadIdx.x < 32) {
+        uint32_t sum = 0;
+        for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) sum += ws.hist[t * kScanTile];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+        if (threadIdx.x == 0) offset = sum;
+    }
+    __syncthreads();
+    const int b = blockIdx.x * kScanTile + threadIdx.x;
+    if (b < kNumBins) {
+        const uint32_t x = ws.scan[b] + offset;
+        ws.scan[b] = x;
+        ws.cursor[b] = x;
+    }
+    if (blockIdx.x == kScanTiles - 1 && threadIdx.x == 0)
+        ws.scan[kNumBins] = offset + ws.hist[blockIdx.x * kScanTile];
 }
 
 cudaError_t launch_scan(const Workspace& ws, cudaStream_t st) {
-    scan_kernel<<<1, kScanThreads, 0, st>>>(ws);
+    scan_tiles_kernel<<<kScanTiles, kScanTile, 0, st>>>(ws);
+    scan_offsets_kernel<<<kScanTiles, kScanTile, 0, st>>>(ws);
     return cudaGetLastError();
 }
 
