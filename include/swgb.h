@@ -137,8 +137,15 @@ void swgb_blosum62(int8_t* out);
  * SWGB_SEQ_DEVICE.  The data are copied (and encoded) into library-owned
  * device memory on `stream` (a cudaStream_t, NULL = legacy default); the call
  * returns after the copy has completed, so the inputs may be reused.
+ * The host reads only offsets[0] and offsets[n_seqs]: the offsets are checked
+ * (non-decreasing, lengths up to SWGB_MAX_LENGTH), measured and rebased on
+ * the device.  Host residues in pinned (page-locked) memory are read in place
+ * by the encode kernel over the host link; other host residues are uploaded
+ * first (in four concurrent parts from 64 MB on).
  * Errors: EINVAL, ERANGE (a sequence longer than SWGB_MAX_LENGTH, or offsets
- * decreasing), EBADRES (a letter/code outside the alphabet), ENOMEM, ECUDA. */
+ * decreasing), EBADRES (a letter/code outside the alphabet; such codes are
+ * stored as 0), ENOMEM, ECUDA.  After ERANGE from the offsets the set is
+ * empty. */
 int swgb_seqset_create(swgb_ctx* ctx, const void* residues, const int64_t* offsets,
                        int64_t n_seqs, uint32_t flags, void* stream, swgb_seqset** out);
 
