@@ -428,7 +428,7 @@ def measure_e2e(al, wl, mat, dev, stream, args, dist=None, world=1):
         swgb.swgb_align_host(al.ctx, qs.handle, rs.handle, pairs, params, out, stream)
 
     step()
-    n = max(1, min(args.steps, 3))
+    n = max(1, args.steps)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()

@@ -222,7 +222,9 @@ int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* 
  * swgb_sync and swgb_last_stats report its launches.  The buffers (sets,
  * pairs, out) must stay allocated while the plan exists; their CONTENTS may
  * change between launches (new pairs of the same count, sequences reloaded
- * into sets whose capacity and longest length do not grow).  Launches of one
+ * into sets whose capacity and longest length do not grow; a plan captured
+ * over queries of the 20 standard letters only refuses to launch, EINVAL,
+ * once its query set holds other codes).  Launches of one
  * context (plans and swgb_align) must be ordered, as for swgb_align. */
 typedef struct swgb_plan swgb_plan;
 
@@ -514,7 +516,13 @@ int swgb_server_stats(swgb_server* server, int32_t* max_overlap, int64_t* pendin
  * device.  Every pointer is a caller-owned DEVICE pointer: q_codes/q_offsets
  * (n_q sequences, codes 0..23, offsets n_q + 1 entries), r_codes/r_offsets
  * (n_r sequences), pairs int32 [n_pairs][2], out swgb_record [n_pairs].
- * params->matrix is a host pointer, as for swgb_align.
+ * Offsets index the codes array from 0 (they are not rebased): they must be
+ * non-negative and non-decreasing, and the last must not exceed the codes
+ * the array holds (the library cannot see that size and does not check it).
+ * params->matrix is a host pointer, as for swgb_align.  The query profile
+ * always stages all 25 rows (the 24 codes and the pad), whatever letters the
+ * queries use, so a batch of 20-letter queries keeps fewer DP blocks resident
+ * per SM than swgb_align gives it; the records are the same.
  * The first call on a device resolves the array's device address and
  * configures the kernels; make that first call before any stream capture.
  * Every call shares the one array and it keeps the previous call's contents
@@ -525,8 +533,8 @@ int swgb_server_stats(swgb_server* server, int32_t* max_overlap, int64_t* pendin
  * Errors: EINVAL (bad argument or penalty), ETOOBIG (n_pairs above
  * SWGB_NOALLOC_MAX_PAIRS, a query longer than SWGB_NOALLOC_MAX_QUERY_LENGTH
  * or a reference longer than SWGB_MAX_LENGTH; nothing is launched), EBADRES
- * (a code >= 24), ERANGE (decreasing offsets, or a pair index out of range:
- * that pair's record is zero), EINTERNAL, ECUDA. */
+ * (a code >= 24), ERANGE (a negative or decreasing offset, or a pair index
+ * out of range: that pair's record is zero), EINTERNAL, ECUDA. */
 int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offsets, int64_t n_q,
                        const uint8_t* r_codes, const int64_t* r_offsets, int64_t n_r,
                        const int32_t* pairs, int64_t n_pairs, const swgb_params* params,

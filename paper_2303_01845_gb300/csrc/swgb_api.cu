@@ -682,7 +682,8 @@ std::mutex g_noalloc_mu;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SWGB_NOALLOC_SCRATCH_BYTES];
 
-// One warp per sequence: codes must be < 24, lengths in [0, max_len].
+// One warp per sequence: offsets non-negative and non-decreasing, codes < 24,
+// lengths in [0, max_len].  A sequence with bad offsets reads no residue.
 __global__ void noalloc_check_kernel(const uint8_t* __restrict__ res, const int64_t* __restrict__ off,
                                      int64_t n, int64_t max_len, int32_t* flags) {
     const int lane = threadIdx.x & 31;
@@ -690,7 +691,7 @@ __global__ void noalloc_check_kernel(const uint8_t* __restrict__ res, const int6
     int32_t f = 0;
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < n; k += warps) {
         const int64_t b = off[k], e = off[k + 1];
-        if (e < b) {
+        if (b < 0 || e < b) {
             f |= kFlagBadOffsets;
             continue;
         }
@@ -857,6 +858,8 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
 // ---------------------------------------------------------------------------
 struct swgb_plan {
     swgb_ctx* ctx = nullptr;
+    const swgb_seqset* queries = nullptr;
+    bool std_profile = false;   // captured with the 21-row profile (codes 0..19 only)
     Store store;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -920,6 +923,8 @@ SWGB_EXPORT int swgb_plan_create(swgb_ctx* ctx, const swgb_seqset* queries, cons
         swgb_plan_destroy(plan);
         return rc;
     }
+    plan->queries = queries;
+    plan->std_profile = queries->max_code < kStdLetters;
     plan->timed = ctx->timed;
     plan->launches = ctx->last_launches;
     plan->n_pairs = n_pairs;
@@ -933,6 +938,13 @@ SWGB_EXPORT int swgb_plan_create(swgb_ctx* ctx, const swgb_seqset* queries, cons
 SWGB_EXPORT int swgb_plan_launch(swgb_plan* plan, void* stream) {
     if (!plan || !plan->ctx || !plan->exec) return SWGB_EINVAL;
     swgb_ctx* ctx = plan->ctx;
+    ctx->err.clear();
+    // The graph stages one profile row per query letter the set held at
+    // capture; a set reloaded since then with codes beyond the 20 standard
+    // letters would index rows that were never staged.
+    if (plan->std_profile && plan->queries->max_code >= kStdLetters)
+        return fail(ctx, SWGB_EINVAL, "plan: the query set now holds codes beyond the 20 standard letters; "
+                                      "create a new plan");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream), "graph launch");
     ctx->timed = plan->timed;

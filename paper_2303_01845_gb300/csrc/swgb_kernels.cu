@@ -230,10 +230,28 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
         } else {
             const swgb_record rec = out[p];
             if (rec.score > 0) {
-                lq = (int64_t)rec.q_end + 1;
-                lr = (int64_t)rec.r_end + 1;
-                // every cell of the reversed prefixes scores at most S
-                cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
+                // The reverse pass reads the prefixes q[0..q_end], r[0..r_end]
+                // through the forward record: check that the record lies inside
+                // its pair (0 <= q_end < lq, 0 <= r_end < lr) and that its score
+                // is attainable there (at most max_score per aligned column),
+                // else report EINTERNAL and leave the pair out with a zero record.
+                const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
+                bool ok = qi >= 0 && qi < q.n && ri >= 0 && ri < r.n;
+                if (ok) {
+                    const int64_t nq = q.off[qi + 1] - q.off[qi], nr = r.off[ri + 1] - r.off[ri];
+                    ok = rec.q_end >= 0 && rec.q_end < nq && rec.r_end >= 0 && rec.r_end < nr &&
+                         (int64_t)rec.score <=
+                             (int64_t)ca.max_score * (rec.q_end < rec.r_end ? rec.q_end + 1 : rec.r_end + 1);
+                }
+                if (ok) {
+                    lq = (int64_t)rec.q_end + 1;
+                    lr = (int64_t)rec.r_end + 1;
+                    // every cell of the reversed prefixes scores at most S
+                    cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
+                } else {
+                    set_status(ws.status, SWGB_EINTERNAL);
+                    zero_record(&out[p]);
+                }
             }
         }
         if (lq > 0) {

@@ -687,16 +687,29 @@ def swgb_align_noalloc(q_codes, q_offsets, r_codes, r_offsets, pairs, params, ou
     scratch is a fixed array compiled into it.  Synchronous.  Limits:
     SWGB_NOALLOC_MAX_PAIRS pairs per call, queries up to
     SWGB_NOALLOC_MAX_QUERY_LENGTH residues; larger inputs raise ETOOBIG."""
-    for t in (q_codes, q_offsets, r_codes, r_offsets, pairs, out):
-        if not t.is_cuda or not t.is_contiguous():
-            raise TypeError("swgb_align_noalloc takes contiguous CUDA tensors")
+    import torch
+    _cuda(q_codes, torch.uint8, "q_codes")
+    _cuda(q_offsets, torch.int64, "q_offsets")
+    _cuda(r_codes, torch.uint8, "r_codes")
+    _cuda(r_offsets, torch.int64, "r_offsets")
+    _cuda(pairs, torch.int32, "pairs")
+    _cuda(out, torch.int32, "out")
+    if q_offsets.dim() != 1 or r_offsets.dim() != 1 or q_offsets.numel() < 1 or r_offsets.numel() < 1:
+        raise ValueError("offsets must be 1-D with n + 1 entries")
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be int32 [P, 2]")
     n = pairs.shape[0]
     if out.numel() < 5 * n:
         raise ValueError("out must hold P x 5 int32")
-    rc = load().swgb_align_noalloc(_ptr(q_codes), _ptr(q_offsets), q_offsets.shape[0] - 1,
-                                   _ptr(r_codes), _ptr(r_offsets), r_offsets.shape[0] - 1,
-                                   _ptr(pairs), n, ctypes.byref(params), _ptr(out),
-                                   _stream_handle(stream))
+    dev = pairs.device
+    if any(t.device != dev for t in (q_codes, q_offsets, r_codes, r_offsets, out)):
+        raise ValueError("swgb_align_noalloc: every tensor must be on one device")
+    # the C call runs on the calling thread's current device
+    with torch.cuda.device(dev):
+        rc = load().swgb_align_noalloc(_ptr(q_codes), _ptr(q_offsets), q_offsets.shape[0] - 1,
+                                       _ptr(r_codes), _ptr(r_offsets), r_offsets.shape[0] - 1,
+                                       _ptr(pairs), n, ctypes.byref(params), _ptr(out),
+                                       _stream_handle(stream))
     if rc != SWGB_OK:
         extra = ""
         if rc == SWGB_ETOOBIG:

@@ -125,3 +125,79 @@ def enumerate_global(q, r, score, go, ge):
                 yield from rec(i, j + 1, "Z", 1, total + close(), same, cols + 1)
 
     yield from rec(0, 0, None, 0, 0, 0, 0)
+
+
+def enumerate_global_columns(q, r, score, go, ge):
+    """Yields (total, columns) for every global alignment of q against r, the
+    columns as a string over D (q_i with r_j), V (q_i with a gap) and Z (a gap
+    with r_j); a maximal run of L gap columns of one kind costs go + ge * L.
+    For tiny inputs only."""
+    lq, lr = len(q), len(r)
+
+    def rec(i, j, last, run, total, cols):
+        closing = -(go + ge * run) if last in ("V", "Z") else 0
+        if i == lq and j == lr:
+            yield total + closing, cols
+            return
+        if i < lq and j < lr:
+            yield from rec(i + 1, j + 1, "D", 0, total + closing + score(q[i], r[j]), cols + "D")
+        if i < lq:
+            if last == "V":
+                yield from rec(i + 1, j, "V", run + 1, total, cols + "V")
+            else:
+                yield from rec(i + 1, j, "V", 1, total + closing, cols + "V")
+        if j < lr:
+            if last == "Z":
+                yield from rec(i, j + 1, "Z", run + 1, total, cols + "Z")
+            else:
+                yield from rec(i, j + 1, "Z", 1, total + closing, cols + "Z")
+
+    yield from rec(0, 0, None, 0, 0, "")
+
+
+def preferred_alignment(optimal):
+    """The one alignment the identity convention picks among the optimal
+    global alignments `optimal` (column strings of equal score), chosen by
+    the convention's own rule applied to the strings, walking back from the
+    end: outside a gap, the last remaining column is a D if some optimal
+    alignment has one there, else a V, else a Z; inside a gap run, the run
+    starts at the current column (the column before it is of another kind)
+    if some optimal alignment does so, else it extends one column further.
+    Returns the column string."""
+    rem = list(optimal)
+    state = "H"
+    picked = []
+    while any(rem):
+        if state == "H":
+            for kind in "DVZ":
+                cand = [s for s in rem if s.endswith(kind)]
+                if cand:
+                    break
+            picked.append(kind)
+            rem = [s[:-1] for s in cand]
+            state = "H" if kind == "D" else kind
+        else:
+            opened = [s for s in rem if not s.endswith(state)]
+            if opened:
+                rem = opened
+                state = "H"
+            else:
+                rem = [s[:-1] for s in rem]
+                picked.append(state)
+    return "".join(reversed(picked))
+
+
+def identity_of(q, r, cols):
+    """(identical columns, columns) of the alignment `cols` of q against r."""
+    i = j = same = 0
+    for c in cols:
+        if c == "D":
+            same += q[i] == r[j]
+            i += 1
+            j += 1
+        elif c == "V":
+            i += 1
+        else:
+            j += 1
+    assert i == len(q) and j == len(r)
+    return same, len(cols)

@@ -11,7 +11,8 @@ import subprocess
 import numpy as np
 import pytest
 
-from brute_force import enumerate_global
+from brute_force import (enumerate_global, enumerate_global_columns, global_affine,
+                         identity_of, preferred_alignment)
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "discovery_oracle.c")
@@ -26,6 +27,22 @@ MUTANTS = {
     "mismatch_counted_identical": ("mt += q[qs + a - 1] == r[rs + b - 1];", "mt += 1;"),
     "span_gap_without_open": ("AT(E, a, b) = imax(AT(E, a, b - 1) - ge, AT(H, a, b - 1) - oe);",
                               "AT(E, a, b) = imax(AT(E, a, b - 1) - ge, AT(H, a, b - 1) - ge);"),
+    # traceback preference swaps: each still traces an optimal alignment
+    "gap_in_query_before_gap_in_reference": (
+        "} else if (a > 0 && AT(H, a, b) == AT(F, a, b)) {\n                    state = 1;\n"
+        "                } else {\n                    state = 2;\n                }",
+        "} else if (b > 0 && AT(H, a, b) == AT(E, a, b)) {\n                    state = 2;\n"
+        "                } else {\n                    state = 1;\n                }"),
+    "query_gap_extension_before_opening": (
+        "const int open = AT(F, a, b) == AT(H, a - 1, b) - oe;",
+        "const int open = AT(F, a, b) != AT(F, a - 1, b) - ge;"),
+    "reference_gap_extension_before_opening": (
+        "const int open = AT(E, a, b) == AT(H, a, b - 1) - oe;",
+        "const int open = AT(E, a, b) != AT(E, a, b - 1) - ge;"),
+    "gap_before_diagonal": (
+        "if (a > 0 && b > 0 &&\n                    AT(H, a, b) == AT(H, a - 1, b - 1) + mat[q[qs + a - 1] * 24 + r[rs + b - 1]]) {",
+        "if (a > 0 && b > 0 && AT(H, a, b) != AT(F, a, b) && AT(H, a, b) != AT(E, a, b) &&\n"
+        "                    AT(H, a, b) == AT(H, a - 1, b - 1) + mat[q[qs + a - 1] * 24 + r[rs + b - 1]]) {"),
 }
 
 
@@ -115,6 +132,25 @@ def _battery(lib, oracle_mod):
         st, got = _identity(lib, q, r, rec, mat, 3, 1)
         if st != 0 or got not in {(m_, c_) for a, m_, c_ in alns if a == best}:
             return False
+    # the traceback preference, selected by brute force, on tie-rich matrices
+    pm = np.full((24, 24), -1, np.int8)
+    np.fill_diagonal(pm, 1)
+    asym = np.random.default_rng(31).integers(-2, 3, size=(24, 24)).astype(np.int8)
+    np.fill_diagonal(asym, 3)
+    for m24, go, ge in ((pm, 1, 1), (pm, 2, 1), (asym, 0, 1), (asym, 1, 1), (asym, 1, 2)):
+        score = lambda u, v: int(m24[u, v])
+        for _ in range(300):
+            q = list(rng.integers(0, 4, size=rng.integers(1, 7)))
+            r = list(rng.integers(0, 4, size=rng.integers(1, 7)))
+            total = global_affine(q, r, score, go, ge)
+            if total == 0:
+                continue
+            alns = list(enumerate_global_columns(q, r, score, go, ge))
+            best = max(t for t, _ in alns)
+            want = identity_of(q, r, preferred_alignment([c for t, c in alns if t == best]))
+            st, got = _identity(lib, q, r, (total, 0, len(q) - 1, 0, len(r) - 1), m24, go, ge)
+            if st != 0 or got != want:
+                return False
     return True
 
 

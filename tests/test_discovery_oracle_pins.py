@@ -6,15 +6,18 @@ k-mers broken by non-standard letters), symmetry, and the one-vs-all and
 all-pairs entry points agreeing with each other.  Identity: identical and
 singly-substituted sequences, a planted gap of known length, and, on tiny
 inputs, exhaustive enumeration of global alignments: the traced alignment
-must be optimal (its score is the record's) and its (identical columns,
-columns) must be those of one optimal alignment.
+must be optimal (its score is the record's), and its (identical columns,
+columns) must be exactly those of the one optimal alignment that the stated
+traceback preference selects, the selection made by brute force over the
+enumerated alignments (tests/brute_force.py), on tie-rich matrices.
 """
 import itertools
 
 import numpy as np
 import pytest
 
-from brute_force import enumerate_global
+from brute_force import (enumerate_global, enumerate_global_columns, global_affine,
+                         identity_of, preferred_alignment)
 
 K = 6
 
@@ -163,3 +166,48 @@ def test_pass_fail_is_decided_exactly(oracle_mod):
     assert not oracle_mod.passes((5, 0, 5, 0, 6), 3, 10, 10, 10)
     assert not oracle_mod.passes((5, 0, 6, 0, 5), 3, 10, 10, 10)
     assert not oracle_mod.passes((0, -1, -1, -1, -1), 0, 0, 10, 10)
+
+
+def tie_rich_matrices():
+    """24 x 24 int8 matrices on which many alignments tie: +1 / -1 over four
+    letters, and a small asymmetric one."""
+    pm = np.full((24, 24), -1, np.int8)
+    np.fill_diagonal(pm, 1)
+    rng = np.random.default_rng(31)
+    asym = rng.integers(-2, 3, size=(24, 24)).astype(np.int8)
+    np.fill_diagonal(asym, 3)
+    return {"plus_minus_one": pm, "asymmetric": asym}
+
+
+@pytest.mark.parametrize("name", ["plus_minus_one", "asymmetric"])
+@pytest.mark.parametrize("go,ge", [(0, 1), (1, 1), (2, 1), (3, 2), (11, 1)])
+def test_identity_follows_the_stated_traceback_preference(oracle_mod, name, go, ge):
+    """Equality, not membership: over every global alignment of the whole
+    (tiny) span, the preference -- diagonal, then a query residue against a
+    gap, then a gap in the query, and a gap run opened as late as possible
+    walking back -- selects one alignment; the oracle's (identical columns,
+    columns) must be that alignment's."""
+    mat = tie_rich_matrices()[name]
+    score = lambda a, b: int(mat[a, b])
+    rng = np.random.default_rng(100 * go + ge + len(name))
+    checked = differ = 0
+    for trial in range(400):
+        q = codes(rng.integers(0, 4, size=rng.integers(1, 6)))
+        r = codes(rng.integers(0, 4, size=rng.integers(1, 6)))
+        total = global_affine(list(q), list(r), score, go, ge)
+        if total == 0:
+            continue   # a zero score is reported as no alignment
+        alns = list(enumerate_global_columns(list(q), list(r), score, go, ge))
+        best = max(t for t, _ in alns)
+        assert best == total
+        optimal = [c for t, c in alns if t == best]
+        want = identity_of(list(q), list(r), preferred_alignment(optimal))
+        rec = (total, 0, len(q) - 1, 0, len(r) - 1)
+        assert oracle_mod.span_identity(q, r, rec, mat, go, ge) == want, (q, r, optimal)
+        checked += 1
+        differ += len({identity_of(list(q), list(r), c) for c in optimal}) > 1
+    # the draw must hold many spans whose optimal alignments disagree
+    assert checked > 250, checked
+    if go <= 2:
+        # small gap costs: many spans whose optimal alignments disagree
+        assert differ > 3, differ

@@ -441,6 +441,39 @@ def test_plan_replays_the_pipeline(aligner, blosum, plain10k, torch_cuda):
         swgb.swgb_plan_destroy(plan)
 
 
+def test_plan_refuses_a_query_set_reloaded_with_other_letters(aligner, blosum, plain10k, torch_cuda):
+    """A plan captured over queries of the 20 standard letters stages 21
+    profile rows; once its query set is reloaded with B / Z / X / * codes the
+    replay is refused (nothing is launched), and a new plan aligns the set."""
+    torch = torch_cuda
+    from paper_2303_01845_gb300 import swgb
+    q, r = device_sets(aligner, plain10k)
+    prm = params(blosum)
+    pairs = torch.from_numpy(plain10k.pairs[:500].copy()).cuda()
+    out = torch.zeros((500, 5), dtype=torch.int32, device="cuda")
+    plan = swgb.swgb_plan_create(aligner.ctx, q.handle, r.handle, pairs, prm, out)
+    try:
+        res = plain10k.q_res.copy()
+        res[::7] = 22   # X
+        q.load(torch.from_numpy(res).cuda(), torch.from_numpy(plain10k.q_off).cuda())
+        with pytest.raises(swgb.SwgbError) as ei:
+            swgb.swgb_plan_launch(aligner.ctx, plan)
+        assert ei.value.code == swgb.SWGB_EINVAL
+    finally:
+        swgb.swgb_plan_destroy(plan)
+    want = aligner.align(q, r, pairs.clone(), prm).cpu().numpy()
+    plan = swgb.swgb_plan_create(aligner.ctx, q.handle, r.handle, pairs, prm, out)
+    try:
+        out.zero_()
+        swgb.swgb_plan_launch(aligner.ctx, plan)
+        swgb.swgb_sync(aligner.ctx)
+        assert (out.cpu().numpy() == want).all()
+    finally:
+        swgb.swgb_plan_destroy(plan)
+    q.close()
+    r.close()
+
+
 def test_tile_selection_does_not_change_records(aligner, blosum, plain10k, torch_cuda):
     """Records are identical under every tile-cost setting, and the autotuner
     keeps one of its candidates."""

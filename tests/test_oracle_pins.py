@@ -168,6 +168,50 @@ def test_blosum62_shape_facts(oracle_mod):
     assert m.max() == 11 == m[w, w]
 
 
+def test_blosum62_ambiguity_rows(oracle_mod):
+    """The B, Z and X rows of the NCBI BLOSUM62 file (the 24-letter table BLAST
+    distributes with B = N or D, Z = Q or E, X = any, * = stop), pinned by what
+    their construction fixes rather than by a second transcription.
+
+    B and Z are log-odds rows of pooled letters: the pooled ratio
+    (q_Nx + q_Dx) / ((p_N + p_D) p_x) is a weighted mean of the ratios of N and
+    D, so before rounding s(B, x) lies between s(N, x) and s(D, x), and half-bit
+    rounding is monotone, so the published integers do too (B against B, Z
+    and Z against Z pool four cells each).  X is the score of an unknown
+    residue: the published row is within one unit of the background-expected
+    score sum_y p_y s(y, x) of each standard letter (Robinson & Robinson
+    frequencies; the NCBI table was built with the BLOCKS background, so the
+    rounding can differ by one), and -1 against itself and the ambiguity
+    codes."""
+    a = oracle_mod.ALPHABET
+    m = oracle_mod.blosum62().astype(int)
+    ix = {c: a.index(c) for c in a}
+    std = [ix[c] for c in STD20]
+
+    def between(v, xs):
+        return min(xs) <= v <= max(xs)
+
+    for amb, (u, w) in (("B", ("N", "D")), ("Z", ("Q", "E"))):
+        for x in std:
+            assert between(m[ix[amb], x], (m[ix[u], x], m[ix[w], x])), (amb, a[x])
+        assert between(m[ix[amb], ix[amb]], [m[ix[s], ix[t]] for s in (u, w) for t in (u, w)])
+    assert between(m[ix["B"], ix["Z"]], [m[ix[s], ix[t]] for s in "ND" for t in "QE"])
+    freq = {}
+    for line in open(os.path.join(GOLDEN, "blosum62_karlin_altschul.txt")):
+        if line.startswith("freq"):
+            _, k, v = line.split()
+            freq[k] = float(v)
+    p = np.array([freq[c] for c in STD20])
+    p /= p.sum()
+    expected = p @ m[np.ix_(std, std)]
+    got = m[ix["X"], std]
+    assert (np.abs(got - expected) < 1.0).all(), (got, np.round(expected, 2))
+    assert (np.abs(got - np.round(expected)) <= 1).all()
+    assert m[ix["X"], ix["X"]] == m[ix["X"], ix["B"]] == m[ix["X"], ix["Z"]] == -1
+    # the stop code: the table's minimum against everything, +1 against itself
+    assert m[ix["*"], ix["*"]] == 1 and (np.delete(m[ix["*"]], ix["*"]) == m.min()).all()
+
+
 def test_self_alignment_closed_form(oracle_mod):
     """In the 20 x 20 standard block every off-diagonal entry is below both
     diagonal entries of its row and column, so a sequence aligned to itself

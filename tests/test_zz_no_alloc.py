@@ -4,7 +4,8 @@ swgb_align_noalloc serves callers that cannot allocate device memory while
 they align; its scratch is one fixed array inside the library, shared by every
 call.  Two calls in a row (different batches, so the second starts from the
 first one's leftovers) must each give exactly the records swgb_align gives.
-The file is collected last so that a failure here leaves every other test run.
+The first call's records are also compared with the CPU oracle's.  The file
+is collected last so that a failure here leaves every other test run.
 """
 import numpy as np
 import pytest
@@ -43,6 +44,9 @@ def test_noalloc_matches_swgb_align_on_two_calls_in_a_row():
     params = swgb.make_params(swgb.swgb_blosum62(), 11, 1)
     for call, seed in enumerate([21, 22]):
         wl, mat = _workload(seed)
+        if call == 0:
+            import oracle
+            oracle_rec = oracle.align_batch(wl.q_res, wl.q_off, wl.r_res, wl.r_off, wl.pairs, mat, 11, 1)
         qc, qo, rc, ro = _tensors(wl)
         pairs = torch.from_numpy(wl.pairs).cuda()
         if call == 1:
@@ -58,6 +62,9 @@ def test_noalloc_matches_swgb_align_on_two_calls_in_a_row():
         assert len(bad) == 0, "call %d: %d records differ, first %s vs %s" % (
             call, len(bad), got[bad[0]].tolist(), want[bad[0]].tolist())
         assert (got[:, 0] > 0).sum() > len(got) // 2
+        if call == 0:
+            # and both against the oracle, record by record
+            assert np.array_equal(got, oracle_rec)
         qs.close()
         rs.close()
     al.close()
@@ -81,3 +88,28 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     with pytest.raises(swgb.SwgbError) as ei:
         swgb.swgb_align_noalloc(short, off2, short, off2, many, params, out2)
     assert ei.value.code == swgb.SWGB_ETOOBIG
+
+
+def test_noalloc_rejects_bad_offsets_and_tensors():
+    """Negative or decreasing offsets are refused before any alignment kernel
+    runs (no residue is read through them); tensors of the wrong type or
+    shape are refused by the binding."""
+    import torch
+    from paper_2303_01845_gb300 import swgb
+    params = swgb.make_params(swgb.swgb_blosum62(), 11, 1)
+    codes = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    good = torch.tensor([0, 32, 64], dtype=torch.int64, device="cuda")
+    pairs = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    out = torch.zeros((1, 5), dtype=torch.int32, device="cuda")
+    for bad in ([-8, 32, 64], [0, 40, 32]):
+        off = torch.tensor(bad, dtype=torch.int64, device="cuda")
+        with pytest.raises(swgb.SwgbError) as ei:
+            swgb.swgb_align_noalloc(codes, off, codes, good, pairs, params, out)
+        assert ei.value.code == swgb.SWGB_ERANGE
+    with pytest.raises(TypeError):
+        swgb.swgb_align_noalloc(codes, good.to(torch.int32), codes, good, pairs, params, out)
+    with pytest.raises(ValueError):
+        swgb.swgb_align_noalloc(codes, good, codes, good, pairs.view(-1), params, out)
+    # a good call after the refused ones
+    swgb.swgb_align_noalloc(codes, good, codes, good, pairs, params, out)
+    torch.cuda.synchronize()
