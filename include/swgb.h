@@ -114,6 +114,9 @@ typedef struct {
     float reverse_ms;        /* reverse DP kernels, CUDA events (SWGB_TIMING), else -1 */
     float total_ms;          /* whole call on the stream (SWGB_TIMING), else -1 */
     int32_t kernel_launches; /* kernels the call launched */
+    int64_t n_band_pairs;    /* reverse passes run over a band (swgb_set_band_min) */
+    int64_t n_band_certified;/* of which the exactness certificate held (the others re-ran
+                                over the whole rectangle) */
 } swgb_stats;
 
 /* Creates a context on CUDA device `device` (made current on the calling
@@ -205,11 +208,49 @@ int swgb_probe_addmax_rate(swgb_ctx* ctx, double* ops_per_clk_per_sm, int* sm_co
 int swgb_set_tile_overhead(swgb_ctx* ctx, int overhead);  /* EINVAL unless 0..64 */
 int swgb_get_tile_overhead(const swgb_ctx* ctx);          /* current value */
 
-/* Times swgb_align on the given batch (device buffers, like swgb_align) for a
- * fixed list of overhead values (one warm-up call, then the fastest of three
- * timed calls each), keeps the fastest in ctx and reports it and its
- * whole-call time in ms.  Synchronous; out receives the batch's records.
- * The records do not depend on the setting.  Errors: those of swgb_align. */
+/* ---- banded reverse pass ----
+ * The reverse pass (start coordinates) of a scored pair may run over a
+ * diagonal band of the reversed prefixes instead of their whole rectangle:
+ * bands of 240 or 392 diagonals around the line from the end cell to the
+ * diagonal lr - lq, a ring of 16 x 16 or 32 x 12 lanes x rows (the paper's
+ * aligner fills the whole matrix, Sec. "Load balancing"; the band is this
+ * library's).  The band's start is kept only under an exactness certificate:
+ * every cell on the band's border through which an alignment could leave
+ * it bounds that alignment's score by the band's value there plus the
+ * forward pass's maximum over the reference rows beyond it plus one gap
+ * opening; if every such bound is below S, no alignment of score S leaves
+ * the band and its first cell of value S is the start of the whole-matrix
+ * definition.  Otherwise the pair is re-run over the whole rectangle, so the
+ * records never depend on the setting.  The forward pass records those
+ * maxima (64 slots of 4 bytes per pair) for pairs whose query and reference
+ * both have at least band_min residues on the packed 16-bit path; a cost
+ * model picks per pair between the rectangle and the bands.
+ * band_min: 0 (off) or 32..65536; default 0; a context setting read by
+ * swgb_align and swgb_plan_create, tuned by swgb_autotune. */
+int swgb_set_band_min(swgb_ctx* ctx, int band_min);      /* EINVAL outside the range */
+int swgb_get_band_min(const swgb_ctx* ctx);              /* current value */
+
+/* What the last swgb_autotune measured (fastest of its timed calls each). */
+typedef struct {
+    int32_t tile_overhead;      /* chosen tile-cost overhead */
+    int32_t band_min;           /* chosen band threshold (0 = no band) */
+    float best_ms;              /* whole-call time at the chosen pair */
+    float runner_up_ms;         /* best time of any other overhead at the chosen band_min */
+    int32_t runner_up_overhead;
+    float band_off_ms;          /* time with no band at the chosen overhead */
+    int32_t candidates;         /* settings timed */
+} swgb_tuning;
+int swgb_last_tuning(const swgb_ctx* ctx, swgb_tuning* out);  /* EINVAL on NULL */
+
+/* Times swgb_align on the given batch (device buffers, like swgb_align):
+ * first the tile-cost overhead over 2 .. 40 (13 values) at the current
+ * band_min, then band_min over {0, 256, 320, 384, 512, 768, 1024} at the
+ * chosen overhead, then the overhead again at the chosen band_min; each
+ * setting gets one warm-up call and the fastest of five timed calls.  Keeps
+ * the fastest pair in ctx and reports the overhead and its whole-call time in
+ * ms (swgb_last_tuning has the rest).  Synchronous; out receives the batch's
+ * records, which do not depend on either setting.  Errors: those of
+ * swgb_align. */
 int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
                   const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
                   swgb_record* out, void* stream, int* best_overhead, float* best_ms);
@@ -407,6 +448,25 @@ int swgb_mlp_grad(swgb_mlp* mlp, const float* features, const float* labels, int
 int swgb_mlp_train(swgb_mlp* mlp, const float* features, const float* labels,
                    const int32_t* order, int64_t n, int64_t batch, float lr, float pos_weight,
                    float* mean_loss, void* stream);
+
+/* The whole training loop: `epochs` passes of swgb_mlp_train, each in a
+ * sample order the library draws from `seed` (a Fisher-Yates shuffle driven
+ * by splitmix64, so a seed gives the same orders everywhere); pos_weight <= 0
+ * means sqrt(negatives / positives) of the labels (each count at least 1).
+ * losses: HOST float [epochs] receiving each epoch's mean minibatch loss, or
+ * NULL.  Training is reproducible: the gradient adds the blocks' partial sums
+ * in block order.  Synchronous; allocates a sample-order buffer.  Errors:
+ * EINVAL, ENOMEM, ECUDA. */
+int swgb_mlp_fit(swgb_mlp* mlp, const float* features, const float* labels, int64_t n, int epochs,
+                 int64_t batch, float lr, float pos_weight, uint64_t seed, float* losses, void* stream);
+
+/* The decision threshold for a target recall: the largest t such that the
+ * logits >= t keep at least `recall` (0..1) of the positives of (DEVICE
+ * features [n][32], DEVICE labels [n]): the k-th smallest positive logit,
+ * k = floor((1 - recall) * positives); -infinity with no positive.
+ * Synchronous; allocates a logits buffer.  Errors: EINVAL, ENOMEM, ECUDA. */
+int swgb_mlp_calibrate(swgb_mlp* mlp, const float* features, const float* labels, int64_t n,
+                       float recall, float* threshold, void* stream);
 
 /* Keeps the pairs whose logit is >= threshold, in order: kept (DEVICE int32
  * [n_pairs][2]) receives them, kept_index (DEVICE int64 [n_pairs], or NULL)

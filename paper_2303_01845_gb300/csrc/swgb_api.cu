@@ -133,7 +133,7 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
     if ((e = cudaMalloc(&ws.hist, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.scan, sizeof(uint32_t) * (kNumBins + 1))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins)) != cudaSuccess) return bail(e, "alloc");
-    if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * kTaskCounters)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.status, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ctx->d_encode_flag, 4 * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "alloc");
@@ -147,6 +147,10 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
                     ctx->blocks_per_sm[v][d][c][s] =
                         std::max(1, dp_blocks_per_sm(c, s, d == 1, v ? kProfileRows : kStdLetters + 1));
             }
+    for (int c = 0; c < kBandConfigs; ++c) {
+        if ((e = band_configure(c)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
+        ctx->band_blocks[c] = std::max(1, band_blocks_per_sm(c));
+    }
     for (auto& ev : ctx->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "cudaEventCreate");
     if ((e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -174,6 +178,8 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
     cudaFree(ws.status);
     cudaFree(ws.counters);
     cudaFree(ws.boundary);
+    cudaFree(ws.fmax);
+    cudaFree(ws.band_prof);
     cudaFree(ctx->d_pairs);
     cudaFree(ctx->d_out);
     cudaFree(ctx->d_encode_flag);
@@ -374,7 +380,7 @@ int alloc_store_fixed(swgb_ctx* ctx, Store& st) {
     CK(cudaMalloc(&ws.hist, sizeof(uint32_t) * kNumBins), "alloc");
     CK(cudaMalloc(&ws.scan, sizeof(uint32_t) * (kNumBins + 1)), "alloc");
     CK(cudaMalloc(&ws.cursor, sizeof(uint32_t) * kNumBins), "alloc");
-    CK(cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * 2 * kNumKernels), "alloc");
+    CK(cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * kTaskCounters), "alloc");
     return SWGB_OK;
 }
 
@@ -387,6 +393,8 @@ void free_store(Store& st, bool with_status) {
     cudaFree(ws.order);
     cudaFree(ws.task_ctr);
     cudaFree(ws.boundary);
+    cudaFree(ws.fmax);
+    cudaFree(ws.band_prof);
     if (with_status) {
         cudaFree(ws.status);
         cudaFree(ws.counters);
@@ -394,9 +402,33 @@ void free_store(Store& st, bool with_status) {
     ws = Workspace{};
 }
 
-// Grows a store for n_pairs pairs against the query set q (may allocate).
-int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, int64_t n_pairs) {
+// Grows a store for n_pairs pairs of the sets q, r (may allocate).
+int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, const swgb_seqset* r, int64_t n_pairs) {
     Workspace& ws = store.ws;
+    if (ctx->band_min > 0) {
+        // forward maxima per pair, and the band kernels' profiles: one slice per
+        // resident warp of each config (the configs run concurrently)
+        CK(grow(&ws.fmax, &store.fmax_capacity, std::max<int64_t>(n_pairs, 1) * kFmaxSlots), "workspace alloc");
+        const int64_t rstride = band_rstride(std::max<int64_t>(std::max(q->max_len, r->max_len), 1));
+        const int64_t per_warp = band_prof_bytes_per_warp(rstride, kProfileRows);
+        int64_t slots = 0;
+        for (int c = 0; c < kBandConfigs; ++c) {
+            store.band_region_off[c] = slots;
+            store.band_region_slots[c] = (int64_t)ctx->sm_count * ctx->band_blocks[c] * (kBandThreads / 32);
+            slots += store.band_region_slots[c];
+        }
+        if (ws.band_rstride < rstride || ws.band_slots < slots || !ws.band_prof) {
+            cudaFree(ws.band_prof);
+            ws.band_prof = nullptr;
+            ws.band_slots = 0;
+            store.band_capacity = 0;
+            CK(cudaMalloc(&ws.band_prof, (size_t)(per_warp * slots)), "band scratch alloc");
+            store.band_capacity = per_warp * slots;
+            ws.band_slots = slots;
+            ws.band_rstride = rstride;
+            ws.band_prof_stride = per_warp;
+        }
+    }
     CK(grow(&ws.bin_of, &store.bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     CK(grow(&ws.order, &store.order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     // chunk-boundary rows: one row per resident warp of every kernel that can
@@ -449,32 +481,67 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     ClassArgs ca = make_class_args(params->matrix, params->gap_open + params->gap_extend, max_score,
                                    force32);
     ca.tile_overhead = ctx->tile_overhead;
+    // the banded reverse pass needs the packed path and the store's scratch
+    const bool band = ctx->band_min > 0 && !ca.force32 && ws.fmax && ws.band_prof;
+    ca.band_min = band ? ctx->band_min : 0;
     const int pv = q->max_code < kStdLetters ? 0 : 1;   // profile variant
     sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;
 
     int launches = 0;
     CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
-    CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * 2 * kNumKernels, st), "memset");
+    CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * kTaskCounters, st), "memset");
     if (timed) CK(record_timing(ctx->ev[0], st), "event");
 
     const SeqView qv = view(q), rv = view(r);
-    for (int dir = 0; dir < 2; ++dir) {
-        const bool rev = dir == 1;
+    // one round: keys -> scan -> scatter -> the DP kernels of every (class,
+    // shape) and, in the reverse round, the band kernels, spread over the
+    // caller's stream and the side streams, largest tiles first
+    auto round = [&](int mode, int dir) -> int {
         CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st), "memset");
-        CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, ca, ws, st), "keys kernel");
+        CK(launch_keys(qv, rv, pairs, n_pairs, out, mode, ca, ws, st), "keys kernel");
         CK(launch_scan(ws, st), "scan kernel");
         CK(launch_scatter(n_pairs, ws, st), "scatter kernel");
         launches += 4;
-        if (timed) CK(record_timing(ctx->ev[rev ? 3 : 1], st), "event");
+        // the DP times exclude the bucketing of their first round
+        if (timed && mode != kKeysFallback) CK(record_timing(ctx->ev[mode == kKeysForward ? 1 : 3], st), "event");
         CK(cudaEventRecord(ctx->fork_ev, st), "event");
         for (int k = 0; k < swgb_ctx::kSide; ++k)
             CK(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0), "stream wait");
-        int rr = 0;   // round robin over {st, side...}, largest tiles first
+        int rr = 0;
+        auto next_stream = [&]() {
+            const int k = rr++ % (swgb_ctx::kSide + 1);
+            return k == 0 ? st : ctx->side[k - 1];
+        };
+        if (mode == kKeysReverse && band) {
+            for (int c = kBandConfigs - 1; c >= 0; --c) {
+                BandArgs b;
+                b.q = qv;
+                b.r = rv;
+                b.pairs = pairs;
+                b.order = ws.order;
+                b.scan = ws.scan;
+                b.task_ctr = ws.task_ctr + 3 * kNumKernels + c;
+                b.out = out;
+                b.status = ws.status;
+                b.fmax = ws.fmax;
+                b.prof = ws.band_prof + store.band_region_off[c] * ws.band_prof_stride;
+                b.prof_stride = ws.band_prof_stride;
+                b.rstride = ws.band_rstride;
+                b.slots = store.band_region_slots[c];
+                b.counters = ws.counters;
+                b.bucket = kBandFirstBucket + c;
+                b.sc = sc;
+                const int64_t per_block = (kBandThreads / 32) * (32 / band_G(c)) * 2;
+                int64_t grid = (int64_t)ctx->sm_count * ctx->band_blocks[c];
+                grid = std::min(grid, (n_pairs + per_block - 1) / per_block);
+                grid = std::min(grid, b.slots / (kBandThreads / 32));
+                CK(launch_band(c, b, (int)std::max<int64_t>(grid, 1), next_stream()), "band kernel");
+                ++launches;
+            }
+        }
         for (int c = 0; c < kClasses; ++c) {
             for (int s = kNumShapes - 1; s >= 0; --s) {
-                cudaStream_t ks = (rr % (swgb_ctx::kSide + 1)) == 0 ? st
-                                                                   : ctx->side[rr % (swgb_ctx::kSide + 1) - 1];
-                ++rr;
+                cudaStream_t ks = next_stream();
                 DPArgs a;
                 a.q = qv;
                 a.r = rv;
@@ -490,11 +557,14 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
                 a.boundary_slots = chunkable ? store.region_slots[c][s] : 0;
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
+                a.fmax = (mode == kKeysForward && band) ? ws.fmax : nullptr;
+                a.band_min = ca.band_min;
                 a.sc = sc;
-                int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[pv][dir][c][s];
+                const int rev = mode != kKeysForward ? 1 : 0;
+                int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[pv][rev][c][s];
                 const int64_t need = (n_pairs + pairs_per_block(c, s) - 1) / pairs_per_block(c, s);
                 grid = std::max<int64_t>(1, std::min(grid, need));
-                CK(launch_dp(c, s, rev, a, (int)grid, ks), "dp kernel");
+                CK(launch_dp(c, s, rev == 1, a, (int)grid, ks), "dp kernel");
                 ++launches;
             }
         }
@@ -502,8 +572,17 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
             CK(cudaEventRecord(ctx->join_ev[k], ctx->side[k]), "event");
             CK(cudaStreamWaitEvent(st, ctx->join_ev[k], 0), "stream wait");
         }
-        if (timed) CK(record_timing(ctx->ev[rev ? 4 : 2], st), "event");
-    }
+        return SWGB_OK;
+    };
+
+    // forward: score and end cell
+    if ((rc = round(kKeysForward, 0))) return rc;
+    if (timed) CK(record_timing(ctx->ev[2], st), "event");
+    // reverse: start cell (bands where chosen), then the pairs whose band
+    // certificate did not hold over the whole rectangle
+    if ((rc = round(kKeysReverse, 1))) return rc;
+    if (band && (rc = round(kKeysFallback, 2))) return rc;
+    if (timed) CK(record_timing(ctx->ev[4], st), "event");
     if (timed) CK(record_timing(ctx->ev[5], st), "event");
     ctx->timed = timed;
     ctx->last_stream = st;
@@ -540,7 +619,7 @@ SWGB_EXPORT int swgb_align(swgb_ctx* ctx, const swgb_seqset* queries, const swgb
         CK(cudaMemsetAsync(ctx->ws.counters, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream), "memset");
         return SWGB_OK;
     }
-    rc = prepare_store(ctx, ctx->store, queries, n_pairs);
+    rc = prepare_store(ctx, ctx->store, queries, refs, n_pairs);
     if (rc) return rc;
     return enqueue(ctx, ctx->store, queries, refs, pairs, n_pairs, params, out, (cudaStream_t)stream);
 }
@@ -600,6 +679,8 @@ SWGB_EXPORT int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out) {
         CK(cudaEventElapsedTime(&out->total_ms, ctx->ev[0], ctx->ev[5]), "event time");
     }
     out->kernel_launches = ctx->last_launches;
+    out->n_band_pairs = (int64_t)c[kCtrBandPairs];
+    out->n_band_certified = (int64_t)c[kCtrBandCertified];
     return SWGB_OK;
 }
 
@@ -819,7 +900,7 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
     for (int dir = 0; dir < 2; ++dir) {
         const bool rev = dir == 1;
         NA_CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st));
-        NA_CK(launch_keys(qv, rv, pairs, n_pairs, out, rev, ca, ws, st));
+        NA_CK(launch_keys(qv, rv, pairs, n_pairs, out, rev ? kKeysReverse : kKeysForward, ca, ws, st));
         NA_CK(launch_scan(ws, st));
         NA_CK(launch_scatter(n_pairs, ws, st));
         for (int c = 0; c < kClasses; ++c) {
@@ -838,6 +919,8 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
                 a.boundary_slots = ws.boundary_slots;
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
+                a.fmax = nullptr;
+                a.band_min = 0;
                 a.sc = sc;
                 int64_t grid = (int64_t)d->sm_count * d->blocks_per_sm[dir][c][s];
                 const int64_t per_block = (int64_t)(kDPThreads / 32) * (32 / shape_G(s)) * (c == 0 ? 2 : 1);
@@ -898,7 +981,7 @@ SWGB_EXPORT int swgb_plan_create(swgb_ctx* ctx, const swgb_seqset* queries, cons
     plan->store.ws.status = ctx->ws.status;
     plan->store.ws.counters = ctx->ws.counters;
     rc = alloc_store_fixed(ctx, plan->store);
-    if (!rc) rc = prepare_store(ctx, plan->store, queries, n_pairs);
+    if (!rc) rc = prepare_store(ctx, plan->store, queries, refs, n_pairs);
     if (rc) {
         swgb_plan_destroy(plan);
         return rc;
@@ -968,40 +1051,99 @@ SWGB_EXPORT int swgb_get_tile_overhead(const swgb_ctx* ctx) {
     return ctx ? ctx->tile_overhead : SWGB_EINVAL;
 }
 
+SWGB_EXPORT int swgb_set_band_min(swgb_ctx* ctx, int band_min) {
+    if (!ctx) return SWGB_EINVAL;
+    if (band_min != 0 && (band_min < 32 || band_min > SWGB_MAX_LENGTH))
+        return fail(ctx, SWGB_EINVAL, "band_min must be 0 or in [32, SWGB_MAX_LENGTH]");
+    ctx->band_min = band_min;
+    return SWGB_OK;
+}
+
+SWGB_EXPORT int swgb_get_band_min(const swgb_ctx* ctx) {
+    return ctx ? ctx->band_min : SWGB_EINVAL;
+}
+
+SWGB_EXPORT int swgb_last_tuning(const swgb_ctx* ctx, swgb_tuning* out) {
+    if (!ctx || !out) return SWGB_EINVAL;
+    *out = ctx->tuning;
+    return SWGB_OK;
+}
+
 SWGB_EXPORT int swgb_autotune(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
                               const int32_t* pairs, int64_t n_pairs, const swgb_params* params,
                               swgb_record* out, void* stream, int* best_overhead, float* best_ms) {
     if (!ctx || !params) return SWGB_EINVAL;
-    static const int kCandidates[] = {2, 4, 6, 8, 10, 14, 20};
+    static const int kOverheads[] = {2, 4, 6, 8, 10, 12, 14, 17, 20, 24, 28, 32, 40};
+    static const int kBandMins[] = {0, 256, 320, 384, 512, 768, 1024};
+    constexpr int kTimed = 5;
     swgb_params p = *params;
     p.flags |= SWGB_TIMING;
-    const int saved = ctx->tile_overhead;
-    int best = saved;
-    float best_t = -1.0f;
-    for (int c : kCandidates) {
-        ctx->tile_overhead = c;
-        // the first run warms up the workspace; the fastest of the next three
-        // counts (the candidates differ by about a percent, run-to-run noise
-        // by as much)
-        float t = -1.0f;
-        for (int rep = 0; rep < 4; ++rep) {
+    const int saved_ovh = ctx->tile_overhead, saved_band = ctx->band_min;
+    swgb_tuning tu{};
+    // whole-call time of one setting: a warm-up call, then the fastest of
+    // kTimed (the settings differ by about a percent, as does run-to-run noise)
+    auto timed = [&](int ovh, int band_min, float* t) -> int {
+        ctx->tile_overhead = ovh;
+        ctx->band_min = band_min;
+        *t = -1.0f;
+        for (int rep = 0; rep <= kTimed; ++rep) {
             int rc = swgb_align(ctx, queries, refs, pairs, n_pairs, &p, out, stream);
             if (!rc) rc = swgb_sync(ctx, stream);
             swgb_stats st;
             if (!rc) rc = swgb_last_stats(ctx, &st);
-            if (rc) {
-                ctx->tile_overhead = saved;
-                return rc;
-            }
-            if (rep > 0 && (t < 0.0f || st.total_ms < t)) t = st.total_ms;
+            if (rc) return rc;
+            if (rep > 0 && (*t < 0.0f || st.total_ms < *t)) *t = st.total_ms;
         }
-        if (best_t < 0.0f || t < best_t) {
-            best_t = t;
-            best = c;
+        ++tu.candidates;
+        return SWGB_OK;
+    };
+    auto fail_restore = [&](int rc) {
+        ctx->tile_overhead = saved_ovh;
+        ctx->band_min = saved_band;
+        return rc;
+    };
+    float t_ovh[sizeof(kOverheads) / sizeof(int)];
+    auto sweep_overhead = [&](int band_min, int* best) -> int {
+        float bt = -1.0f;
+        for (size_t i = 0; i < sizeof(kOverheads) / sizeof(int); ++i) {
+            int rc = timed(kOverheads[i], band_min, &t_ovh[i]);
+            if (rc) return rc;
+            if (bt < 0.0f || t_ovh[i] < bt) {
+                bt = t_ovh[i];
+                *best = kOverheads[i];
+            }
+        }
+        return SWGB_OK;
+    };
+    int ovh = saved_ovh, band_min = saved_band, rc;
+    if ((rc = sweep_overhead(band_min, &ovh))) return fail_restore(rc);
+    float bt = -1.0f;
+    for (int bm : kBandMins) {
+        float t;
+        if ((rc = timed(ovh, bm, &t))) return fail_restore(rc);
+        if (bm == 0) tu.band_off_ms = t;
+        if (bt < 0.0f || t < bt) {
+            bt = t;
+            band_min = bm;
         }
     }
-    ctx->tile_overhead = best;
-    if (best_overhead) *best_overhead = best;
-    if (best_ms) *best_ms = best_t;
+    if ((rc = sweep_overhead(band_min, &ovh))) return fail_restore(rc);
+    tu.tile_overhead = ovh;
+    tu.band_min = band_min;
+    tu.best_ms = -1.0f;
+    tu.runner_up_ms = -1.0f;
+    for (size_t i = 0; i < sizeof(kOverheads) / sizeof(int); ++i) {
+        if (kOverheads[i] == ovh) {
+            tu.best_ms = t_ovh[i];
+        } else if (tu.runner_up_ms < 0.0f || t_ovh[i] < tu.runner_up_ms) {
+            tu.runner_up_ms = t_ovh[i];
+            tu.runner_up_overhead = kOverheads[i];
+        }
+    }
+    ctx->tile_overhead = ovh;
+    ctx->band_min = band_min;
+    ctx->tuning = tu;
+    if (best_overhead) *best_overhead = ovh;
+    if (best_ms) *best_ms = tu.best_ms;
     return SWGB_OK;
 }

@@ -67,8 +67,50 @@ constexpr int kClasses = 2;                   // 0 = packed 16x2, 1 = 32-bit
 constexpr int kNumBuckets = kClasses * kBucketsPerClass;
 constexpr int kQBins = 512;                   // streamed-length bins per bucket
 constexpr int kQBinShift = 3;                 // 8 residues per bin
-constexpr int kNumBins = kNumBuckets * kQBins;
 constexpr int kNumKernels = kClasses * kNumShapes;
+
+// ---- banded reverse pass ---------------------------------------------------
+// A scored pair on the packed path may run its reverse pass over a diagonal
+// band of the reversed prefixes instead of the whole rectangle (band_kernel,
+// swgb_band.cu).  Config c uses groups of band_G(c) lanes of band_R(c) rows
+// arranged as a ring: a lane moves on to rows G*R further up when its window
+// of (G-1)(R+1) streamed positions ends, so every lane stays busy and the
+// computed region is a staircase band that always covers band_width(c) whole
+// diagonals.  A pair takes config c only when the drift of its end diagonal
+// plus twice band_margin(its length) fits that width.  The band's result is kept only
+// under the exactness certificate checked by the kernel; otherwise the pair
+// is re-run by the full reverse pass.
+constexpr int kBandConfigs = 2;
+__host__ __device__ constexpr int band_G(int c) { return c == 0 ? 16 : 32; }
+__host__ __device__ constexpr int band_R(int c) { return c == 0 ? 16 : 12; }
+// Diagonals a band must keep free on each side of the drift for a pair of
+// length L (the longer prefix) to certify: the forward maxima bound a block of
+// about L / 63 rows, and the path's wander grows with L.
+__host__ __device__ constexpr int64_t band_margin(int64_t L) { return 40 + L / 24; }
+__host__ __device__ constexpr int band_width(int c) { return band_G(c) * (band_R(c) + 1) - 2 * band_R(c); }
+// Per-pair maxima of the forward pass's H over blocks of reference rows, the
+// certificate's bound on the part of an alignment before a band exit: entry 0
+// holds the block height SB (or kFmaxNone: no maxima recorded), entry 1 + k the
+// largest H of reference rows [k SB, (k + 1) SB).  SB is a whole number of the
+// forward tile's rows per lane, so every forward lane lies in one block and
+// adds its maximum there alone; at most kFmaxSlots - 1 blocks.
+constexpr int kFmaxSlots = 64;
+constexpr int32_t kFmaxNone = 0x7fffffff;
+__host__ __device__ inline int fmax_slot_rows(int64_t lr, int lane_rows) {
+    const int64_t per = (lr + kFmaxSlots - 2) / (kFmaxSlots - 1);
+    return (int)((per + lane_rows - 1) / lane_rows * lane_rows);
+}
+// Shortest query and reference (whole sequences) of a pair whose forward pass
+// records those maxima; the context's setting, tuned by swgb_autotune (0 = no
+// banded reverse pass, the default).
+constexpr int kBandMinDefault = 0;
+
+// bins: the two classes' buckets, then one bucket per band config
+constexpr int kBandFirstBucket = kNumBuckets;
+constexpr int kNumBins = (kNumBuckets + kBandConfigs) * kQBins;
+// work-queue counters: forward, reverse, reverse fallback (per class and
+// shape), then one per band config
+constexpr int kTaskCounters = 3 * kNumKernels + kBandConfigs;
 
 // Tile of a pair: the shape (and chunk count) of least modelled cost, where a
 // pair costs (streamed steps incl. the G-1 wavefront fill) x chunks x G x
@@ -120,7 +162,38 @@ struct ClassArgs {
     int8_t colmax[kMatStride];    // max(0, max_x s(x, y)) per reference code y
     int32_t force32;
     int32_t tile_overhead;        // per-step lane work in rows (choose_shape)
+    int32_t band_min;             // forward maxima / banded reverse from this length (0 = off)
 };
+
+// Modelled cost of a reverse pass of query prefix lq, reference prefix lr and
+// score S over the whole rectangle (choose_shape's model) or a band; returns
+// the band config of least cost, or -1 when the rectangle is cheaper or no
+// band fits the end diagonal.  The reverse pass stops after the start: an
+// alignment that scores S spans about S / 2 streamed positions on these
+// workloads (homologous pairs gain 2 to 3 per column), so the model streams
+// a = min(lq, S / 2 + 1) positions.  The choice changes no result.
+__host__ __device__ inline int choose_band(int64_t lq, int64_t lr, int64_t S, int overhead) {
+    int64_t a = S / 2 + 1;
+    if (a > lq) a = lq;
+    int shape = 0, nch = 1;
+    choose_shape(a, lr, overhead, &shape, &nch);
+    int64_t best = (a + shape_G(shape) - 1) * nch * shape_G(shape) * (shape_R(shape) + overhead);
+    int pick = -1;
+    const int64_t delta = lr - lq;
+    const int64_t ad = delta < 0 ? -delta : delta;
+    const int64_t margin = band_margin(lq > lr ? lq : lr);
+    for (int c = 0; c < kBandConfigs; ++c) {
+        if (ad + 2 * margin > band_width(c)) continue;
+        const int64_t khi = (delta > 0 ? delta : 0) + (band_width(c) - ad) / 2;
+        const int64_t t = a + khi + (a + khi) / band_R(c) + band_G(c);
+        const int64_t cost = t * band_G(c) * (band_R(c) + overhead);
+        if (cost < best) {
+            best = cost;
+            pick = c;
+        }
+    }
+    return pick;
+}
 
 // Per-call device workspace (owned by the context).
 struct Workspace {
@@ -129,12 +202,17 @@ struct Workspace {
     uint32_t* cursor;      // [kNumBins] scatter cursors
     int32_t* bin_of;       // [n_pairs] bin of each pair (-1 = not aligned)
     int32_t* order;        // [n_pairs] pair ids sorted by bin
-    uint32_t* task_ctr;    // [2 * kNumKernels] work-queue counters (fwd, rev)
+    uint32_t* task_ctr;    // [kTaskCounters] work-queue counters
     int32_t* status;       // [1] device status word
     unsigned long long* counters;  // [8] cells / class counts
     uint2* boundary;       // chunk-boundary rows, [slots][boundary_stride]
     int64_t boundary_stride;
     int64_t boundary_slots;
+    int32_t* fmax;         // [n_pairs][kFmaxSlots] forward maxima (null: no banded reverse)
+    uint8_t* band_prof;    // band kernels' profiles, [band_slots][band_prof_stride]
+    int64_t band_prof_stride;
+    int64_t band_rstride;  // bytes of one profile row
+    int64_t band_slots;
 };
 
 // Arguments of one DP launch.
@@ -150,6 +228,27 @@ struct DPArgs {
     int64_t boundary_stride;
     int64_t boundary_slots;
     int32_t first_bucket, end_bucket;
+    int32_t* fmax;              // forward: per-pair row-block maxima (null: none)
+    int32_t band_min;           // forward: pairs with both lengths >= band_min record them
+    ScoreArgs sc;
+};
+
+// Arguments of one band_kernel launch (config c).
+struct BandArgs {
+    SeqView q, r;
+    const int32_t* pairs;
+    const int32_t* order;
+    const uint32_t* scan;
+    uint32_t* task_ctr;
+    swgb_record* out;
+    int32_t* status;
+    const int32_t* fmax;
+    uint8_t* prof;             // profile scratch of the launch's warps
+    int64_t prof_stride;       // bytes per warp
+    int64_t rstride;           // bytes per profile row
+    int64_t slots;             // warps the scratch holds
+    unsigned long long* counters;
+    int32_t bucket;            // the config's bin bucket
     ScoreArgs sc;
 };
 
@@ -159,7 +258,13 @@ enum Counter {
     kCtrInt16 = 2,
     kCtrInt32 = 3,
     kCtrRevPairs = 4,
+    kCtrBandPairs = 5,      // reverse passes run over a band
+    kCtrBandCertified = 6,  // of which the certificate held
 };
+
+// Marker left in q_start by the band kernel for a pair whose certificate did
+// not hold: the fallback keys pass sends it to the full reverse pass.
+constexpr int32_t kBandFallback = -2;
 
 // ---- launchers (swgb_kernels.cu) -------------------------------------------
 // flags[0] |= 1 on a residue outside the alphabet; flags[1] = max(flags[1], code)
@@ -169,8 +274,11 @@ cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii
 // max_len; flags[1] = longest length) and subtracts base from each.
 cudaError_t launch_offsets(int64_t* off, int64_t n_seqs, int64_t base, int64_t max_len, int32_t* flags,
                            cudaStream_t st);
+// mode 0: forward keys; 1: reverse keys (band or full rectangle); 2: the
+// pairs the band kernels left for the full reverse pass
+enum KeysMode { kKeysForward = 0, kKeysReverse = 1, kKeysFallback = 2 };
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
-                        swgb_record* out, bool reverse, const ClassArgs& ca,
+                        swgb_record* out, int mode, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scan(const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st);
@@ -184,6 +292,15 @@ int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows);
 constexpr int kDPThreads = 64;
 size_t dp_smem_bytes(int cls, int shape, int prof_rows);
 cudaError_t dp_configure(int cls, int shape, bool reverse);
+// The banded reverse kernel of config c (swgb_band.cu).
+constexpr int kBandThreads = 64;
+cudaError_t launch_band(int cfg, const BandArgs& a, int grid_blocks, cudaStream_t st);
+int band_blocks_per_sm(int cfg);
+cudaError_t band_configure(int cfg);
+// Row length of the band scratch for sequences up to max_len residues, and
+// its bytes per warp with prof_rows profile rows (plus a query row) per pair.
+int64_t band_rstride(int64_t max_len);
+int64_t band_prof_bytes_per_warp(int64_t rstride, int prof_rows);
 cudaError_t launch_probe_addmax(unsigned long long* cycles, uint32_t* sink, int blocks,
                                 int iters, cudaStream_t st);
 constexpr int kProbeThreads = 256;

@@ -30,10 +30,9 @@
 #include <type_traits>
 
 #include "swgb_internal.cuh"
+#include "swgb_lane.cuh"
 
 namespace swgb {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // SMs of the current device: caps the grids of the grid-stride kernels.
 static int64_t sm_count() {
@@ -184,14 +183,6 @@ cudaError_t launch_offsets(int64_t* off, int64_t n_seqs, int64_t base, int64_t m
 // ---------------------------------------------------------------------------
 // Bucketing: keys + histogram, scan, scatter
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void zero_record(swgb_record* r) {
-    *r = swgb_record{0, -1, -1, -1, -1};
-}
-
-__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
-    atomicCAS(status, 0, code);
-}
-
 // Upper bound of the score of a pair from its residues (see ClassArgs).
 __device__ int64_t score_bound(const uint8_t* __restrict__ q, int64_t lq, const uint8_t* __restrict__ r,
                                int64_t lr, const ClassArgs& ca) {
@@ -202,15 +193,15 @@ __device__ int64_t score_bound(const uint8_t* __restrict__ q, int64_t lq, const 
 }
 
 __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pairs,
-                            int64_t n_pairs, swgb_record* out, int reverse, ClassArgs ca,
+                            int64_t n_pairs, swgb_record* out, int mode, ClassArgs ca,
                             Workspace ws) {
-    unsigned long long cells = 0, n16 = 0, n32 = 0;
+    unsigned long long cells = 0, n16 = 0, n32 = 0, nband = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += stride) {
         int bin = -1;
         int64_t lq = 0, lr = 0;
-        int cls = 0;
-        if (!reverse) {
+        int cls = 0, band = -1;
+        if (mode == kKeysForward) {
             const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
             if (qi < 0 || qi >= q.n || ri < 0 || ri >= r.n) {
                 set_status(ws.status, SWGB_ERANGE);
@@ -226,10 +217,23 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 } else if ((int64_t)ca.max_score * (lq < lr ? lq : lr) > 32767) {
                     cls = score_bound(q.res + q.off[qi], lq, r.res + r.off[ri], lr, ca) > 32767;
                 }
+                // a pair long enough for a banded reverse pass: the block height of
+                // its forward maxima (from its forward tile) and cleared blocks,
+                // which the packed forward kernels fill; absent on the 32-bit path
+                if (ws.fmax && ca.band_min > 0 && lq >= ca.band_min && lr >= ca.band_min) {
+                    int shape = 0, nch = 1;
+                    choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
+                    const int sb = cls == 0 ? fmax_slot_rows(lr, shape_R(shape)) : kFmaxNone;
+                    int4* f = reinterpret_cast<int4*>(ws.fmax + p * kFmaxSlots);
+#pragma unroll
+                    for (int k = 0; k < kFmaxSlots / 4; ++k)
+                        f[k] = k > 0 ? make_int4(0, 0, 0, 0) : make_int4(sb, 0, 0, 0);
+                }
             }
         } else {
             const swgb_record rec = out[p];
-            if (rec.score > 0) {
+            const bool take = mode == kKeysReverse ? rec.score > 0 : (rec.score > 0 && rec.q_start == kBandFallback);
+            if (take) {
                 // The reverse pass reads the prefixes q[0..q_end], r[0..r_end]
                 // through the forward record: check that the record lies inside
                 // its pair (0 <= q_end < lq, 0 <= r_end < lr) and that its score
@@ -237,8 +241,10 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 // else report EINTERNAL and leave the pair out with a zero record.
                 const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
                 bool ok = qi >= 0 && qi < q.n && ri >= 0 && ri < r.n;
+                int64_t nq = 0, nr = 0;
                 if (ok) {
-                    const int64_t nq = q.off[qi + 1] - q.off[qi], nr = r.off[ri + 1] - r.off[ri];
+                    nq = q.off[qi + 1] - q.off[qi];
+                    nr = r.off[ri + 1] - r.off[ri];
                     ok = rec.q_end >= 0 && rec.q_end < nq && rec.r_end >= 0 && rec.r_end < nr &&
                          (int64_t)rec.score <=
                              (int64_t)ca.max_score * (rec.q_end < rec.r_end ? rec.q_end + 1 : rec.r_end + 1);
@@ -248,6 +254,9 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                     lr = (int64_t)rec.r_end + 1;
                     // every cell of the reversed prefixes scores at most S
                     cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
+                    if (mode == kKeysReverse && cls == 0 && ws.fmax && ca.band_min > 0 &&
+                        nq >= ca.band_min && nr >= ca.band_min && ws.fmax[p * kFmaxSlots] != kFmaxNone)
+                        band = choose_band(lq, lr, rec.score, ca.tile_overhead);
                 } else {
                     set_status(ws.status, SWGB_EINTERNAL);
                     zero_record(&out[p]);
@@ -257,12 +266,21 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
         if (lq > 0) {
             int64_t qb = lq >> kQBinShift;
             if (qb > kQBins - 1) qb = kQBins - 1;
-            int shape = 0, nch = 1;
-            choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
-            bin = bucket_of(cls, shape, nch) * kQBins + (kQBins - 1 - (int)qb);
+            int bucket;
+            if (band >= 0) {
+                bucket = kBandFirstBucket + band;
+                ++nband;
+            } else {
+                int shape = 0, nch = 1;
+                choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
+                bucket = bucket_of(cls, shape, nch);
+            }
+            bin = bucket * kQBins + (kQBins - 1 - (int)qb);
             atomicAdd(&ws.hist[bin], 1u);
-            cells += (unsigned long long)(lq * lr);
-            if (cls == 0) ++n16; else ++n32;
+            if (mode != kKeysFallback) {
+                cells += (unsigned long long)(lq * lr);
+                if (cls == 0) ++n16; else ++n32;
+            }
         }
         ws.bin_of[p] = bin;
     }
@@ -271,26 +289,28 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
         cells += __shfl_xor_sync(kFull, cells, off);
         n16 += __shfl_xor_sync(kFull, n16, off);
         n32 += __shfl_xor_sync(kFull, n32, off);
+        nband += __shfl_xor_sync(kFull, nband, off);
     }
-    if ((threadIdx.x & 31) == 0 && (cells | n16 | n32)) {
-        if (!reverse) {
+    if ((threadIdx.x & 31) == 0 && (cells | n16 | n32 | nband)) {
+        if (mode == kKeysForward) {
             atomicAdd(&ws.counters[kCtrFwdCells], cells);
             atomicAdd(&ws.counters[kCtrInt16], n16);
             atomicAdd(&ws.counters[kCtrInt32], n32);
-        } else {
+        } else if (mode == kKeysReverse) {
             atomicAdd(&ws.counters[kCtrRevCells], cells);
             atomicAdd(&ws.counters[kCtrRevPairs], n16 + n32);
+            atomicAdd(&ws.counters[kCtrBandPairs], nband);
         }
     }
 }
 
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
-                        swgb_record* out, bool reverse, const ClassArgs& ca,
+                        swgb_record* out, int mode, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     int64_t blocks = (n_pairs + 255) / 256;
     if (blocks > sm_count() * 16) blocks = sm_count() * 16;
-    keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, reverse ? 1 : 0, ca, ws);
+    keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(q, r, pairs, n_pairs, out, mode, ca, ws);
     return cudaGetLastError();
 }
 
@@ -382,164 +402,8 @@ cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st
 }
 
 // ---------------------------------------------------------------------------
-// Lane arithmetic: packed 16x2 (two pairs per register) or 32-bit
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-template <bool P16>
-struct Lane;
-
-// Packed path: two pairs per register, every score kept biased by kBias so
-// that both 16-bit halves stay in [0, 65535]; unsigned add-max / max then act
-// per half, and a 32-bit add of two such words never carries from one half
-// into the other (which lets constant shifts run as integer multiply-adds).
-constexpr int kBias = 16384;
-
-template <>
-struct Lane<true> {
-    static constexpr int kPack = 2;
-    __device__ __forceinline__ static uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
-        return __viaddmax_u16x2(a, b, c);
-    }
-    __device__ __forceinline__ static uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
-        return __vimax3_u16x2(a, b, c);
-    }
-    __device__ __forceinline__ static uint32_t splat(int v) {
-        return ((uint32_t)v & 0xffffu) * 0x10001u;
-    }
-    __device__ __forceinline__ static int get(uint32_t w, int h) {
-        return h ? (int)(w >> 16) : (int)(w & 0xffffu);
-    }
-    __device__ __forceinline__ static uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
-        return __vimin3_u16x2(a, b, c);
-    }
-    // score of row b (0..3) of the word pair: low half from a (pair 0),
-    // high half from c (pair 1); packed-path profile bytes are 0..127, so
-    // extending the sign bit fills zeros
-    __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t c, int b) {
-        const uint32_t sel = (uint32_t)b | ((uint32_t)(b | 8) << 4) | ((uint32_t)(4 + b) << 8) |
-                             ((uint32_t)((4 + b) | 8) << 12);
-        return prmt(a, c, sel);
-    }
-};
-
-template <>
-struct Lane<false> {
-    static constexpr int kPack = 1;
-    __device__ __forceinline__ static uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
-        return (uint32_t)__viaddmax_s32((int)a, (int)b, (int)c);
-    }
-    __device__ __forceinline__ static uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
-        return (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
-    }
-    __device__ __forceinline__ static uint32_t splat(int v) { return (uint32_t)v; }
-    __device__ __forceinline__ static int get(uint32_t w, int) { return (int)w; }
-    __device__ __forceinline__ static uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
-        return (uint32_t)__vimin3_s32((int)a, (int)b, (int)c);
-    }
-    __device__ __forceinline__ static uint32_t widen(uint32_t a, uint32_t, int b) {
-        const uint32_t s = (uint32_t)(b | 8);
-        const uint32_t sel = (uint32_t)b | (s << 4) | (s << 8) | (s << 12);
-        return prmt(a, 0u, sel);
-    }
-};
-
-// Maximum of N values as a tree of 3-input maxima: every level takes the
-// values three at a time and carries the one or two left over, so N values cost
-// ceil((N - 1) / 2) instructions at depth about log3(N).
-template <bool P16, int N>
-__device__ __forceinline__ uint32_t max_reduce(const uint32_t (&x)[N]) {
-    if constexpr (N == 1) {
-        return x[0];
-    } else if constexpr (N == 2) {
-        return Lane<P16>::max3(x[0], x[1], x[1]);
-    } else {
-        constexpr int NG = N / 3, NL = N % 3, M = NG + NL;
-        uint32_t y[M];
-#pragma unroll
-        for (int k = 0; k < NG; ++k) y[k] = Lane<P16>::max3(x[3 * k], x[3 * k + 1], x[3 * k + 2]);
-#pragma unroll
-        for (int k = 0; k < NL; ++k) y[NG + k] = x[3 * NG + k];
-        return max_reduce<P16, M>(y);
-    }
-}
-
-// Maximum of v[0..R) and init.
-template <bool P16, int R>
-__device__ __forceinline__ uint32_t tree_max(const uint32_t (&v)[R], uint32_t init) {
-    uint32_t x[R + 1];
-#pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = v[k];
-    x[R] = init;
-    return max_reduce<P16, R + 1>(x);
-}
-
-// A lane's profile bytes for one query letter: R rows rounded up to whole
-// words (LS bytes, 8, 12 or 16), loaded as one 8-byte, three 4-byte or one
-// 16-byte access; they start at a multiple of LS.
-template <int LS>
-struct ProfWords {
-    uint32_t w[LS / 4];
-};
-
-template <int LS>
-__device__ __forceinline__ ProfWords<LS> load_prof(const int8_t* p) {
-    ProfWords<LS> out;
-    if constexpr (LS == 8) {
-        const uint2 v = *reinterpret_cast<const uint2*>(p);
-        out.w[0] = v.x;
-        out.w[1] = v.y;
-    } else if constexpr (LS == 12) {
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
-        out.w[0] = q[0];
-        out.w[1] = q[1];
-        out.w[2] = q[2];
-    } else {
-        static_assert(LS == 16, "lane stride must be 8, 12 or 16 bytes");
-        const uint4 v = *reinterpret_cast<const uint4*>(p);
-        out.w[0] = v.x;
-        out.w[1] = v.y;
-        out.w[2] = v.z;
-        out.w[3] = v.w;
-    }
-    return out;
-}
-
-template <int LS>
-__device__ __forceinline__ void store_prof(int8_t* p, const uint32_t (&w)[LS / 4]) {
-    if constexpr (LS == 8) {
-        *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
-    } else if constexpr (LS == 12) {
-        uint32_t* q = reinterpret_cast<uint32_t*>(p);
-        q[0] = w[0];
-        q[1] = w[1];
-        q[2] = w[2];
-    } else {
-        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-}
-
-// (value, i, j) ordering of candidate end cells: larger value first, then the
-// row-major-first cell (smaller streamed index i, then smaller held index j).
-__device__ __forceinline__ bool better(int v, int i, int j, int bv, int bi, int bj) {
-    return v > bv || (v == bv && (i < bi || (i == bi && j < bj)));
-}
-
-// ---------------------------------------------------------------------------
 // The DP kernel
 // ---------------------------------------------------------------------------
-// The block's copy of the score table, transposed: tabT[y][x] = table(x, y)
-// for reference code y (0..24, the pad code last) and profile row x (the pad
-// row mapped to the pad code).  Rows are 9 words apart, so lanes reading one
-// word of rows of different codes hit different banks.
-constexpr int kTabTStride = 36;
-constexpr int kTabTBytes = kProfileRows * kTabTStride;   // 900
-constexpr int kSmatRegion = 1024;                        // keeps profiles 16-B aligned
-static_assert(kTabTBytes <= kSmatRegion, "transposed table exceeds its region");
 // Steps between refreshes of the group's score bound (forward) and between
 // tests for the end of the reverse pass, whose bound is fixed.
 __host__ __device__ constexpr int bound_every(bool reverse) { return reverse ? 32 : 16; }
@@ -547,24 +411,6 @@ __host__ __device__ constexpr int bound_every(bool reverse) { return reverse ? 3
 // bytes of profile a warp stages: per group and pair, prof_rows x G x LS
 __host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16, int prof_rows) {
     return (32 / G) * (P16 ? 2 : 1) * prof_rows * G * ((R + 3) / 4 * 4);
-}
-
-// Packed per-half maximum over the G lanes of a group.
-template <bool P16, int G>
-__device__ __forceinline__ uint32_t group_max(uint32_t v) {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        const uint32_t o = __shfl_xor_sync(kFull, v, off, G);
-        v = Lane<P16>::max3(v, o, o);
-    }
-    return v;
-}
-
-template <int G>
-__device__ __forceinline__ int group_min(int v) {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(kFull, v, off, G));
-    return v;
 }
 
 // REV = false: forward pass over q x r -> score and end cell.
@@ -585,8 +431,9 @@ __device__ __forceinline__ int group_min(int v) {
 // the register budget: 65536 / (64 threads x blocks) registers per thread.
 __host__ __device__ constexpr int dp_min_blocks(int R) { return R <= 8 ? 8 : R <= 12 ? 6 : 5; }
 
-template <int G, int R, bool P16, bool REV>
+template <int G, int R, bool P16, bool REV, bool FMAX>
 __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const DPArgs a) {
+    static_assert(!FMAX || (P16 && !REV), "forward maxima are recorded by packed forward kernels");
     using L = Lane<P16>;
     constexpr int PACK = L::kPack;
     constexpr int GROUPS = 32 / G;
@@ -775,6 +622,9 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             uint32_t hin_prev = HZ;
             // per half max(this lane's maximum in this chunk, T - 1)
             uint32_t lb1 = L::addmax(T, MONE, HZ);
+            // forward maxima variant: this lane's own running maximum over its
+            // rows in this chunk (lb1 also holds T - 1), for the banded reverse pass
+            uint32_t pmax = HZ;
             // the kept event's row values of each half; on the packed path two
             // rows per register (row 2k low, row 2k + 1 high)
             constexpr int NS = P16 ? (R + 1) / 2 : R;   // odd R: the last high half unused
@@ -929,7 +779,13 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     // the last of a run can hold the lane's maximum, so its
                     // registers are kept once the run has ended (at the start of
                     // the step after next).  After an event lb1 is its value.
-                    const uint32_t nlb1 = tree_max<P16, R>(Hn, lb1);
+                    uint32_t nlb1;
+                    if constexpr (FMAX) {
+                        pmax = tree_max<P16, R>(Hn, pmax);
+                        nlb1 = L::max3(pmax, lb1, lb1);
+                    } else {
+                        nlb1 = tree_max<P16, R>(Hn, lb1);
+                    }
                     // nlb1 >= lb1 in each half, so the 32-bit difference is exact
                     // per half; up = 1 in the halves with an event, else 0
                     const uint32_t up = L::min3(nlb1 + lb1 * neg_one, ONE, ONE);
@@ -1021,6 +877,23 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 wavefront(std::false_type{});
             }
 
+            // ---- forward maxima of the lane's rows for the banded reverse
+            // pass: block k of a pair holds the largest H of reference rows
+            // [k SB, (k + 1) SB); SB is a multiple of R, so the lane's rows lie
+            // in one block
+            if constexpr (FMAX) {
+                if (a.fmax) {
+#pragma unroll
+                    for (int h = 0; h < PACK; ++h) {
+                        if (pid[h] >= 0 && lq[h] >= a.band_min && lr[h] >= a.band_min && jl < lr[h]) {
+                            const int sb = fmax_slot_rows(lr[h], R);
+                            const int v = L::get(pmax, h) - zero_h;   // H
+                            atomicMax(a.fmax + (int64_t)pid[h] * kFmaxSlots + 1 + jl / sb, v);
+                        }
+                    }
+                }
+            }
+
             // ---- the lane's candidate of this chunk: the recorded step and the
             // first row of the snapshot holding the value, if it is the lane's
             // maximum
@@ -1098,41 +971,46 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 // ---------------------------------------------------------------------------
 using DPFn = void (*)(const DPArgs);
 
-template <int S, bool P16, bool REV>
+template <int S, bool P16, bool REV, bool FMAX>
 constexpr DPFn dp_fn() {
-    return &dp_kernel<shape_G(S), shape_R(S), P16, REV>;
+    return &dp_kernel<shape_G(S), shape_R(S), P16, REV, FMAX>;
 }
 
-template <bool P16, bool REV>
+template <bool P16, bool REV, bool FMAX>
 DPFn dp_pick(int shape) {
     switch (shape) {
-        case 0: return dp_fn<0, P16, REV>();
-        case 1: return dp_fn<1, P16, REV>();
-        case 2: return dp_fn<2, P16, REV>();
-        case 3: return dp_fn<3, P16, REV>();
-        case 4: return dp_fn<4, P16, REV>();
-        case 5: return dp_fn<5, P16, REV>();
-        case 6: return dp_fn<6, P16, REV>();
-        case 7: return dp_fn<7, P16, REV>();
-        case 8: return dp_fn<8, P16, REV>();
-        case 9: return dp_fn<9, P16, REV>();
-        case 10: return dp_fn<10, P16, REV>();
-        case 11: return dp_fn<11, P16, REV>();
-        case 12: return dp_fn<12, P16, REV>();
-        case 13: return dp_fn<13, P16, REV>();
-        case 14: return dp_fn<14, P16, REV>();
-        case 15: return dp_fn<15, P16, REV>();
-        case 16: return dp_fn<16, P16, REV>();
-        case 17: return dp_fn<17, P16, REV>();
-        case 18: return dp_fn<18, P16, REV>();
-        case 19: return dp_fn<19, P16, REV>();
-        default: return dp_fn<20, P16, REV>();
+        case 0: return dp_fn<0, P16, REV, FMAX>();
+        case 1: return dp_fn<1, P16, REV, FMAX>();
+        case 2: return dp_fn<2, P16, REV, FMAX>();
+        case 3: return dp_fn<3, P16, REV, FMAX>();
+        case 4: return dp_fn<4, P16, REV, FMAX>();
+        case 5: return dp_fn<5, P16, REV, FMAX>();
+        case 6: return dp_fn<6, P16, REV, FMAX>();
+        case 7: return dp_fn<7, P16, REV, FMAX>();
+        case 8: return dp_fn<8, P16, REV, FMAX>();
+        case 9: return dp_fn<9, P16, REV, FMAX>();
+        case 10: return dp_fn<10, P16, REV, FMAX>();
+        case 11: return dp_fn<11, P16, REV, FMAX>();
+        case 12: return dp_fn<12, P16, REV, FMAX>();
+        case 13: return dp_fn<13, P16, REV, FMAX>();
+        case 14: return dp_fn<14, P16, REV, FMAX>();
+        case 15: return dp_fn<15, P16, REV, FMAX>();
+        case 16: return dp_fn<16, P16, REV, FMAX>();
+        case 17: return dp_fn<17, P16, REV, FMAX>();
+        case 18: return dp_fn<18, P16, REV, FMAX>();
+        case 19: return dp_fn<19, P16, REV, FMAX>();
+        default: return dp_fn<20, P16, REV, FMAX>();
     }
 }
 
-static DPFn dp_lookup(int cls, int shape, bool reverse) {
-    if (cls == 0) return reverse ? dp_pick<true, true>(shape) : dp_pick<true, false>(shape);
-    return reverse ? dp_pick<false, true>(shape) : dp_pick<false, false>(shape);
+// fmax: the packed forward variant that records forward maxima for the
+// banded reverse pass (ignored otherwise)
+static DPFn dp_lookup(int cls, int shape, bool reverse, bool fmax = false) {
+    if (cls == 0) {
+        if (reverse) return dp_pick<true, true, false>(shape);
+        return fmax ? dp_pick<true, false, true>(shape) : dp_pick<true, false, false>(shape);
+    }
+    return reverse ? dp_pick<false, true, false>(shape) : dp_pick<false, false, false>(shape);
 }
 
 size_t dp_smem_bytes(int cls, int shape, int prof_rows) {
@@ -1141,9 +1019,13 @@ size_t dp_smem_bytes(int cls, int shape, int prof_rows) {
 }
 
 cudaError_t dp_configure(int cls, int shape, bool reverse) {
-    return cudaFuncSetAttribute(dp_lookup(cls, shape, reverse),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dp_smem_bytes(cls, shape, kProfileRows));
+    cudaError_t e = cudaFuncSetAttribute(dp_lookup(cls, shape, reverse),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dp_smem_bytes(cls, shape, kProfileRows));
+    if (e == cudaSuccess && cls == 0 && !reverse)
+        e = cudaFuncSetAttribute(dp_lookup(cls, shape, false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dp_smem_bytes(cls, shape, kProfileRows));
+    return e;
 }
 
 int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows) {
@@ -1156,7 +1038,7 @@ int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows) {
 
 cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
                       cudaStream_t st) {
-    DPFn fn = dp_lookup(cls, shape, reverse);
+    DPFn fn = dp_lookup(cls, shape, reverse, a.fmax != nullptr);
     fn<<<grid_blocks, kDPThreads, dp_smem_bytes(cls, shape, a.sc.prof_rows), st>>>(a);
     return cudaGetLastError();
 }

@@ -66,7 +66,15 @@ class swgb_stats(ctypes.Structure):
                 ("n_int32_pairs", ctypes.c_int64), ("n_reverse_pairs", ctypes.c_int64),
                 ("forward_cells", ctypes.c_int64), ("reverse_cells", ctypes.c_int64),
                 ("forward_ms", ctypes.c_float), ("reverse_ms", ctypes.c_float),
-                ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32)]
+                ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32),
+                ("n_band_pairs", ctypes.c_int64), ("n_band_certified", ctypes.c_int64)]
+
+
+class swgb_tuning(ctypes.Structure):
+    _fields_ = [("tile_overhead", ctypes.c_int32), ("band_min", ctypes.c_int32),
+                ("best_ms", ctypes.c_float), ("runner_up_ms", ctypes.c_float),
+                ("runner_up_overhead", ctypes.c_int32), ("band_off_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
 
 
 class swgb_thresholds(ctypes.Structure):
@@ -117,6 +125,9 @@ _SIGS = [
                                               ctypes.POINTER(ctypes.c_int)]),
     ("swgb_set_tile_overhead", ctypes.c_int, [_VP, ctypes.c_int]),
     ("swgb_get_tile_overhead", ctypes.c_int, [_VP]),
+    ("swgb_set_band_min", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("swgb_get_band_min", ctypes.c_int, [_VP]),
+    ("swgb_last_tuning", ctypes.c_int, [_VP, ctypes.POINTER(swgb_tuning)]),
     ("swgb_autotune", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(swgb_params),
                                      _VP, _VP, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_float)]),
@@ -147,6 +158,11 @@ _SIGS = [
     ("swgb_mlp_train", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64,
                                       ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                       _VP]),
+    ("swgb_mlp_fit", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                    ctypes.POINTER(ctypes.c_float), _VP]),
+    ("swgb_mlp_calibrate", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_float), _VP]),
     ("swgb_select_pairs", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP,
                                          ctypes.POINTER(ctypes.c_int64), _VP]),
     ("swgb_server_default_config", None, [ctypes.POINTER(swgb_server_config)]),
@@ -349,9 +365,24 @@ def swgb_get_tile_overhead(ctx):
     return load().swgb_get_tile_overhead(ctx)
 
 
+def swgb_set_band_min(ctx, band_min):
+    _check(ctx, load().swgb_set_band_min(ctx, int(band_min)))
+
+
+def swgb_get_band_min(ctx):
+    return load().swgb_get_band_min(ctx)
+
+
+def swgb_last_tuning(ctx):
+    t = swgb_tuning()
+    _check(ctx, load().swgb_last_tuning(ctx, ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in swgb_tuning._fields_}
+
+
 def swgb_autotune(ctx, queries, refs, pairs, params, out, stream=None):
-    """Times the tile-cost overhead candidates on this batch (CUDA buffers),
-    keeps the fastest in the context; returns (overhead, ms)."""
+    """Times the tile-cost overhead and band threshold candidates on this batch
+    (CUDA buffers), keeps the fastest in the context; returns (overhead, ms);
+    swgb_last_tuning gives the rest."""
     best = ctypes.c_int()
     ms = ctypes.c_float()
     rc = load().swgb_autotune(ctx, queries, refs, _ptr(pairs), pairs.shape[0], ctypes.byref(params),
@@ -591,6 +622,30 @@ class MLP:
                                                float(lr), float(pos_weight), ctypes.byref(ml),
                                                _stream_handle(stream)))
         return ml.value
+
+    def fit(self, features, labels, epochs, batch=8192, lr=3e-3, pos_weight=0.0, seed=1, stream=None):
+        """swgb_mlp_fit: `epochs` seeded passes; pos_weight <= 0 means the
+        library's default; returns the per-epoch mean losses."""
+        import torch
+        _cuda(features, torch.float32, "features")
+        _cuda(labels, torch.float32, "labels")
+        losses = (ctypes.c_float * max(int(epochs), 1))()
+        _check(self.ctx, load().swgb_mlp_fit(self.handle, _ptr(features), _ptr(labels), features.shape[0],
+                                             int(epochs), int(batch), float(lr), float(pos_weight),
+                                             ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), losses,
+                                             _stream_handle(stream)))
+        return [losses[k] for k in range(int(epochs))]
+
+    def calibrate(self, features, labels, recall, stream=None):
+        """swgb_mlp_calibrate: the logit threshold keeping `recall` of the positives."""
+        import torch
+        _cuda(features, torch.float32, "features")
+        _cuda(labels, torch.float32, "labels")
+        t = ctypes.c_float()
+        _check(self.ctx, load().swgb_mlp_calibrate(self.handle, _ptr(features), _ptr(labels),
+                                                   features.shape[0], float(recall), ctypes.byref(t),
+                                                   _stream_handle(stream)))
+        return t.value
 
 
 def server_config(**kw):

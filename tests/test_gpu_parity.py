@@ -496,7 +496,7 @@ def test_tile_selection_does_not_change_records(aligner, blosum, plain10k, torch
             swgb.swgb_set_tile_overhead(aligner.ctx, 65)
         out = torch.zeros((pairs.shape[0], 5), dtype=torch.int32, device="cuda")
         best, ms = swgb.swgb_autotune(aligner.ctx, q.handle, r.handle, pairs, prm, out)
-        assert best in (2, 4, 6, 8, 10, 14, 20) and ms > 0
+        assert best in (2, 4, 6, 8, 10, 12, 14, 17, 20, 24, 28, 32, 40) and ms > 0
         assert swgb.swgb_get_tile_overhead(aligner.ctx) == best
         assert (out.cpu().numpy() == ref).all()
     finally:
