@@ -23,6 +23,8 @@
 // gradient once at the end.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -64,8 +66,9 @@ struct MlpArgs {
     int64_t first, n;
     float pos_weight;
     float* logits;                // [n] (forward)
-    float* grad;                  // [kParams] (gradient, accumulated)
-    float* loss;                  // [1] (gradient, accumulated sum of weighted losses / n)
+    float* grad;                  // [kParams] (gradient)
+    float* loss;                  // [1] (gradient: sum of weighted losses / n)
+    float* part;                  // [blocks][kParams + 1] per-block sums (gradient, loss last)
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -101,7 +104,9 @@ struct Smem {
     __nv_bfloat16 a1t[kH1 * kTStride];
     __nv_bfloat16 dz1t[kH1 * kTStride];
     __nv_bfloat16 dz2t[kH2 * kTStride];
-    float gb1[kH1], gb2[kH2], gw3[kH2], gb3, loss;
+    // per-warp sums of the bias gradients, w3's gradient and the loss, added
+    // in warp order at the end (no atomics: the gradient is reproducible)
+    float gb1[kWarps][kH1], gb2[kWarps][kH2], gw3[kWarps][kH2], gb3[kWarps], loss[kWarps];
 };
 
 __device__ void load_weights(Smem& s, const MlpArgs& a, bool with_w2) {
@@ -243,9 +248,9 @@ __global__ void __launch_bounds__(kWarps * 32) mlp_grad_kernel(MlpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& s = *reinterpret_cast<Smem*>(smem_raw);
     load_weights(s, a, true);
-    for (int k = threadIdx.x; k < kH1; k += blockDim.x) s.gb1[k] = 0.f;
-    for (int k = threadIdx.x; k < kH2; k += blockDim.x) s.gb2[k] = s.gw3[k] = 0.f;
-    if (threadIdx.x == 0) s.gb3 = s.loss = 0.f;
+    for (int k = threadIdx.x; k < kWarps * kH1; k += blockDim.x) s.gb1[k / kH1][k % kH1] = 0.f;
+    for (int k = threadIdx.x; k < kWarps * kH2; k += blockDim.x) s.gb2[k / kH2][k % kH2] = s.gw3[k / kH2][k % kH2] = 0.f;
+    if (threadIdx.x < kWarps) s.gb3[threadIdx.x] = s.loss[threadIdx.x] = 0.f;
     __syncthreads();
     const float b3 = a.params[kOffB3];
     const float inv_n = 1.0f / (float)a.n;
@@ -291,8 +296,8 @@ __global__ void __launch_bounds__(kWarps * 32) mlp_grad_kernel(MlpArgs a) {
             gb += __shfl_xor_sync(0x11111111u, gb, 8);
             gb += __shfl_xor_sync(0x11111111u, gb, 16);
             if (lane == 0) {
-                atomicAdd(&s.loss, l * inv_n);
-                atomicAdd(&s.gb3, gb);
+                s.loss[warp] += l * inv_n;
+                s.gb3[warp] += gb;
             }
         }
         // dz2 = bf16(g3 w3 [z2 > 0]) in place of acc2; its column sums and a2 . g3
@@ -313,10 +318,10 @@ __global__ void __launch_bounds__(kWarps * 32) mlp_grad_kernel(MlpArgs a) {
             T.acc2[nt][3] = d11;
             const float s0 = sum_rows(d00 + d10), s1 = sum_rows(d01 + d11);
             if (g == 0) {
-                atomicAdd(&s.gw3[c], w30);
-                atomicAdd(&s.gw3[c + 1], w31);
-                atomicAdd(&s.gb2[c], s0);
-                atomicAdd(&s.gb2[c + 1], s1);
+                s.gw3[warp][c] += w30;
+                s.gw3[warp][c + 1] += w31;
+                s.gb2[warp][c] += s0;
+                s.gb2[warp][c + 1] += s1;
             }
         }
         // da1 = dz2 W2^T: [16 x 128] x [128 x 64], A fragments straight from dz2
@@ -368,8 +373,8 @@ __global__ void __launch_bounds__(kWarps * 32) mlp_grad_kernel(MlpArgs a) {
                 s.dz1t[(c + 1) * kTStride + sr1] = __float2bfloat16_rn(d11);
                 const float s0 = sum_rows(d00 + d10), s1 = sum_rows(d01 + d11);
                 if (g == 0) {
-                    atomicAdd(&s.gb1[c], s0);
-                    atomicAdd(&s.gb1[c + 1], s1);
+                    s.gb1[warp][c] += s0;
+                    s.gb1[warp][c + 1] += s1;
                 }
             }
 #pragma unroll
@@ -407,32 +412,59 @@ __global__ void __launch_bounds__(kWarps * 32) mlp_grad_kernel(MlpArgs a) {
         }
         __syncthreads();
     }
-    // this block's sums into the global gradient
+    // this block's sums into its own slice of the per-block buffer: every
+    // parameter's entry is written once (the warps' dW2 and dW1 slices are
+    // disjoint; the bias, w3 and loss sums are added in warp order)
+    float* part = a.part + (int64_t)blockIdx.x * (kParams + 1);
 #pragma unroll
     for (int nt = 0; nt < 16; ++nt) {
         const int r = warp * 16 + g, c = nt * 8 + 2 * q;
-        atomicAdd(&a.grad[kOffW2 + r * kH2 + c], gW2[nt][0]);
-        atomicAdd(&a.grad[kOffW2 + r * kH2 + c + 1], gW2[nt][1]);
-        atomicAdd(&a.grad[kOffW2 + (r + 8) * kH2 + c], gW2[nt][2]);
-        atomicAdd(&a.grad[kOffW2 + (r + 8) * kH2 + c + 1], gW2[nt][3]);
+        part[kOffW2 + r * kH2 + c] = gW2[nt][0];
+        part[kOffW2 + r * kH2 + c + 1] = gW2[nt][1];
+        part[kOffW2 + (r + 8) * kH2 + c] = gW2[nt][2];
+        part[kOffW2 + (r + 8) * kH2 + c + 1] = gW2[nt][3];
     }
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
         const int r = (warp & 1) * 16 + g, c = (warp >> 1) * 32 + nt * 8 + 2 * q;
-        atomicAdd(&a.grad[kOffW1 + r * kH1 + c], gW1[nt][0]);
-        atomicAdd(&a.grad[kOffW1 + r * kH1 + c + 1], gW1[nt][1]);
-        atomicAdd(&a.grad[kOffW1 + (r + 8) * kH1 + c], gW1[nt][2]);
-        atomicAdd(&a.grad[kOffW1 + (r + 8) * kH1 + c + 1], gW1[nt][3]);
+        part[kOffW1 + r * kH1 + c] = gW1[nt][0];
+        part[kOffW1 + r * kH1 + c + 1] = gW1[nt][1];
+        part[kOffW1 + (r + 8) * kH1 + c] = gW1[nt][2];
+        part[kOffW1 + (r + 8) * kH1 + c + 1] = gW1[nt][3];
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kH1; k += blockDim.x) atomicAdd(&a.grad[kOffB1 + k], s.gb1[k]);
+    for (int k = threadIdx.x; k < kH1; k += blockDim.x) {
+        float v = 0.f;
+        for (int w = 0; w < kWarps; ++w) v += s.gb1[w][k];
+        part[kOffB1 + k] = v;
+    }
     for (int k = threadIdx.x; k < kH2; k += blockDim.x) {
-        atomicAdd(&a.grad[kOffB2 + k], s.gb2[k]);
-        atomicAdd(&a.grad[kOffW3 + k], s.gw3[k]);
+        float v = 0.f, u = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+            v += s.gb2[w][k];
+            u += s.gw3[w][k];
+        }
+        part[kOffB2 + k] = v;
+        part[kOffW3 + k] = u;
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&a.grad[kOffB3], s.gb3);
-        atomicAdd(a.loss, s.loss);
+        float v = 0.f, u = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+            v += s.gb3[w];
+            u += s.loss[w];
+        }
+        part[kOffB3] = v;
+        part[kParams] = u;
+    }
+}
+
+// grad[k] = sum over the blocks of their slices, in block order; the loss likewise.
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int blocks, float* grad, float* loss) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= kParams; k += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int b = 0; b < blocks; ++b) v += part[(int64_t)b * (kParams + 1) + k];
+        if (k < kParams) grad[k] = v;
+        else *loss = v;
     }
 }
 
@@ -478,6 +510,8 @@ struct swgb_mlp {
     float* v = nullptr;
     float* grad = nullptr;
     float* loss = nullptr;        // [1]
+    float* part = nullptr;        // [part_blocks][kParams + 1] per-block gradient sums
+    int part_blocks = 0;
     __nv_bfloat16* w1t = nullptr;
     __nv_bfloat16* w2t = nullptr;
     __nv_bfloat16* w2 = nullptr;
@@ -497,6 +531,7 @@ MlpArgs base_args(const swgb_mlp* m) {
     a.w2 = m->w2;
     a.grad = m->grad;
     a.loss = m->loss;
+    a.part = m->part;
     return a;
 }
 
@@ -505,8 +540,6 @@ int mlp_check(const swgb_mlp* m) { return (m && m->ctx) ? SWGB_OK : SWGB_EINVAL;
 int grad_launch(swgb_mlp* m, const float* x, const float* y, const int32_t* order, int64_t first,
                 int64_t n, float pos_weight, cudaStream_t st) {
     swgb_ctx* ctx = m->ctx;
-    CK(cudaMemsetAsync(m->grad, 0, sizeof(float) * kParams, st), "memset");
-    CK(cudaMemsetAsync(m->loss, 0, sizeof(float), st), "memset");
     MlpArgs a = base_args(m);
     a.x = x;
     a.y = y;
@@ -515,9 +548,11 @@ int grad_launch(swgb_mlp* m, const float* x, const float* y, const int32_t* orde
     a.n = n;
     a.pos_weight = pos_weight;
     const int64_t steps = (n + kBlockRows - 1) / kBlockRows;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(steps, (int64_t)ctx->sm_count * 2));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(steps, (int64_t)m->part_blocks));
     mlp_grad_kernel<<<blocks, kWarps * 32, kSmemBytes, st>>>(a);
     CK(cudaGetLastError(), "mlp_grad kernel");
+    grad_reduce_kernel<<<(kParams + 256) / 256, 256, 0, st>>>(m->part, blocks, m->grad, m->loss);
+    CK(cudaGetLastError(), "grad_reduce kernel");
     return SWGB_OK;
 }
 
@@ -541,6 +576,8 @@ SWGB_EXPORT int swgb_mlp_create(swgb_ctx* ctx, const float* init, swgb_mlp** out
     alloc(&m->v, sizeof(float) * kParams);
     alloc(&m->grad, sizeof(float) * kParams);
     alloc(&m->loss, sizeof(float));
+    m->part_blocks = std::max(1, ctx->sm_count * 2);
+    alloc(&m->part, sizeof(float) * (kParams + 1) * (size_t)m->part_blocks);
     alloc(&m->w1t, sizeof(__nv_bfloat16) * kIn * kH1);
     alloc(&m->w2t, sizeof(__nv_bfloat16) * kH1 * kH2);
     alloc(&m->w2, sizeof(__nv_bfloat16) * kH1 * kH2);
@@ -567,6 +604,7 @@ SWGB_EXPORT void swgb_mlp_destroy(swgb_mlp* m) {
     cudaFree(m->v);
     cudaFree(m->grad);
     cudaFree(m->loss);
+    cudaFree(m->part);
     cudaFree(m->w1t);
     cudaFree(m->w2t);
     cudaFree(m->w2);
@@ -672,6 +710,117 @@ SWGB_EXPORT int swgb_mlp_train(swgb_mlp* m, const float* features, const float* 
     }
     cudaFree(losses);
     if (rc == SWGB_OK && mean_loss) *mean_loss = (float)(loss_sum / (double)nb);
-    ctx->last_search_launches = (int32_t)(3 * nb);
+    ctx->last_search_launches = (int32_t)(4 * nb);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Training loop and calibration behind the ABI
+// ---------------------------------------------------------------------------
+namespace {
+
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the state advances by the golden-ratio increment
+// and each output is the state passed through the published finalizer.
+struct SplitMix64 {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    }
+    // uniform in [0, n) by rejection of the biased tail
+    uint64_t below(uint64_t n) {
+        const uint64_t lim = UINT64_MAX - UINT64_MAX % n;
+        uint64_t x;
+        do x = next(); while (x >= lim);
+        return x % n;
+    }
+};
+
+int copy_labels(swgb_ctx* ctx, const float* labels, int64_t n, std::vector<float>& h, cudaStream_t st) {
+    h.resize((size_t)n);
+    CK(cudaMemcpyAsync(h.data(), labels, sizeof(float) * n, cudaMemcpyDeviceToHost, st), "labels D2H");
+    CK(cudaStreamSynchronize(st), "stream sync");
+    return SWGB_OK;
+}
+
+}  // namespace
+
+SWGB_EXPORT int swgb_mlp_fit(swgb_mlp* m, const float* features, const float* labels, int64_t n, int epochs,
+                             int64_t batch, float lr, float pos_weight, uint64_t seed, float* losses,
+                             void* stream) {
+    if (mlp_check(m)) return SWGB_EINVAL;
+    swgb_ctx* ctx = m->ctx;
+    if (n < 1 || n > INT32_MAX || epochs < 0 || batch < 1 || !features || !labels || !(lr > 0.f))
+        return fail(ctx, SWGB_EINVAL, "mlp_fit: bad argument");
+    CK(cudaSetDevice(m->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(pos_weight > 0.f)) {
+        // sqrt(negatives / positives) of the labels, each at least 1
+        std::vector<float> h;
+        int rc = copy_labels(ctx, labels, n, h, st);
+        if (rc) return rc;
+        double pos = 0.0;
+        for (float v : h) pos += v > 0.5f;
+        pos_weight = (float)std::sqrt(std::max(1.0, (double)n - pos) / std::max(1.0, pos));
+    }
+    std::vector<int32_t> order((size_t)n);
+    int32_t* d_order = nullptr;
+    CK(cudaMalloc(&d_order, sizeof(int32_t) * (size_t)n), "mlp_fit scratch");
+    SplitMix64 rng{seed};
+    int rc = SWGB_OK;
+    for (int ep = 0; ep < epochs && rc == SWGB_OK; ++ep) {
+        // Fisher-Yates from the identity
+        for (int64_t k = 0; k < n; ++k) order[(size_t)k] = (int32_t)k;
+        for (int64_t k = n - 1; k > 0; --k) std::swap(order[(size_t)k], order[(size_t)rng.below((uint64_t)k + 1)]);
+        cudaError_t e = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // order is reused by the next epoch
+        if (e != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "mlp_fit order H2D");
+            break;
+        }
+        float mean = 0.f;
+        rc = swgb_mlp_train(m, features, labels, d_order, n, batch, lr, pos_weight, &mean, stream);
+        if (rc == SWGB_OK && losses) losses[ep] = mean;
+    }
+    cudaFree(d_order);
+    ctx->last_search_launches = (int32_t)(4 * ((n + batch - 1) / batch) * epochs);
+    return rc;
+}
+
+SWGB_EXPORT int swgb_mlp_calibrate(swgb_mlp* m, const float* features, const float* labels, int64_t n,
+                                   float recall, float* threshold, void* stream) {
+    if (mlp_check(m)) return SWGB_EINVAL;
+    swgb_ctx* ctx = m->ctx;
+    if (n < 1 || !features || !labels || !threshold || !(recall >= 0.f && recall <= 1.f))
+        return fail(ctx, SWGB_EINVAL, "mlp_calibrate: bad argument");
+    CK(cudaSetDevice(m->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    float* d_logits = nullptr;
+    CK(cudaMalloc(&d_logits, sizeof(float) * (size_t)n), "mlp_calibrate scratch");
+    int rc = swgb_mlp_forward(m, features, n, d_logits, stream);
+    std::vector<float> z((size_t)n), y;
+    if (rc == SWGB_OK) {
+        cudaError_t e = cudaMemcpyAsync(z.data(), d_logits, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "logits D2H");
+    }
+    if (rc == SWGB_OK) rc = copy_labels(ctx, labels, n, y, st);
+    cudaFree(d_logits);
+    if (rc) return rc;
+    // the largest threshold that keeps at least `recall` of the positives: the
+    // k-th smallest positive logit, k = floor((1 - recall) * positives)
+    std::vector<float> pos;
+    for (int64_t k = 0; k < n; ++k)
+        if (y[(size_t)k] > 0.5f) pos.push_back(z[(size_t)k]);
+    if (pos.empty()) {
+        *threshold = -INFINITY;
+        return SWGB_OK;
+    }
+    size_t k = (size_t)std::floor((1.0 - (double)recall) * (double)pos.size());
+    if (k >= pos.size()) k = pos.size() - 1;
+    std::nth_element(pos.begin(), pos.begin() + (std::ptrdiff_t)k, pos.end());
+    *threshold = pos[k];
+    return SWGB_OK;
 }

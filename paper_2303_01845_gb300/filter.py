@@ -2,10 +2,10 @@
 features, training on the device, threshold calibration, and the filtered
 many-against-many search.
 
-Orchestration only: every step runs in libswgb's kernels (discovery, features,
-alignment, identity, the network's forward and backward passes, Adam,
-selection); this module chooses batches, epochs and permutations (drawn with
-numpy from a stated seed) and the decision threshold.
+Orchestration only: every step runs in libswgb (discovery, features,
+alignment, identity, the network's forward and backward passes, Adam, the
+seeded training loop, threshold calibration, selection); this module passes
+the sizes, seeds and recall target through.
 
 The paper's own filter is the common-k-mer threshold (program-parameters
 table); the learned one is trained on pass/fail labels of exact alignments
@@ -27,23 +27,17 @@ def exact_labels(al, s, cand, params, thresholds=None):
 
 def train(al, features, labels, epochs=20, batch=2048, lr=3e-3, seed=1, pos_weight=None,
           init=None):
-    """Trains a network on CUDA features [P, 32] / labels [P] (0 or 1): epochs
-    of minibatch Adam in seeded random orders.  pos_weight defaults to
-    sqrt(negatives / positives).  Returns (MLP, per-epoch mean losses)."""
+    """Trains a network on CUDA features [P, 32] / labels [P] (0 or 1) with
+    swgb_mlp_fit: epochs of minibatch Adam in sample orders the library draws
+    from `seed`; pos_weight None means the library's sqrt(negatives /
+    positives).  Returns (MLP, per-epoch mean losses)."""
     import torch
     y = labels.to(torch.float32).contiguous()
-    n_pos = float(y.sum().item())
-    n = y.numel()
-    if pos_weight is None:
-        pos_weight = float(np.sqrt(max(n - n_pos, 1.0) / max(n_pos, 1.0)))
     if init is None:
         init = init_params(seed)
     net = swgb.MLP(al.ctx, init)
-    rng = np.random.default_rng(seed)
-    losses = []
-    for _ in range(epochs):
-        order = torch.from_numpy(rng.permutation(n).astype(np.int32)).to(features.device)
-        losses.append(net.train(features, y, order, batch, lr, pos_weight))
+    losses = net.fit(features, y, epochs, batch=batch, lr=lr,
+                     pos_weight=0.0 if pos_weight is None else pos_weight, seed=seed)
     return net, losses
 
 
@@ -65,13 +59,9 @@ def init_params(seed):
 
 def calibrate(net, features, labels, recall=0.995):
     """The largest threshold keeping at least `recall` of the positives of
-    (features, labels): a quantile of their logits."""
-    z = net.forward(features).cpu().numpy()
-    pos = np.sort(z[labels.cpu().numpy() > 0.5])
-    if len(pos) == 0:
-        return float("-inf")
-    k = int(np.floor((1.0 - recall) * len(pos)))
-    return float(pos[min(k, len(pos) - 1)])
+    (features, labels) (swgb_mlp_calibrate)."""
+    import torch
+    return net.calibrate(features, labels.to(torch.float32).contiguous(), recall)
 
 
 def filtered_search(al, s, net, threshold, params, k=6, min_shared=2, thresholds=None):

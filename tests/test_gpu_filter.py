@@ -166,6 +166,23 @@ def test_gradient_matches_oracle(aligner, torch_mod, oracle_mod, mlp_mod, family
     net.close()
 
 
+def test_training_is_reproducible(aligner, torch_mod, family2k):
+    """The gradient sums the blocks' partial sums in block order (no float
+    atomics), so two trainings from the same start and sample order give the
+    same parameters bit for bit, on one GPU."""
+    from paper_2303_01845_gb300 import filter as F
+    X = real_features(aligner, torch_mod, family2k)
+    n = X.shape[0]
+    y = torch_mod.from_numpy((np.random.default_rng(11).uniform(size=n) < 0.3).astype(np.float32)).cuda()
+    runs = []
+    for _ in range(2):
+        net, losses = F.train(aligner, X, y, epochs=3, batch=512, lr=3e-3, seed=2)
+        runs.append((net.get(), losses))
+        net.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+
+
 def test_training_step_matches_oracle_adam(aligner, torch_mod, mlp_mod, family2k):
     """A full-batch Adam step on the device against the oracle's Adam step on
     the device's own gradient of that batch.  Entries whose gradient is within
