@@ -35,6 +35,7 @@ ADDMAX_OPS_PER_CELL = 2.5     # five packed 16x2 add-max per two cells
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dp_forward_traffic.json")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_kernels.cu")
 KERNEL_HEADER = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_internal.cuh")
+LANE_HEADER = os.path.join(ROOT, "paper_2303_01845_gb300", "csrc", "swgb_lane.cuh")
 
 
 def parse():
@@ -56,6 +57,8 @@ def parse():
                     help="pairs of the batch the tile selection is tuned on")
     ap.add_argument("--tile-overhead", type=int, default=-1,
                     help="fixed tile-cost overhead instead of tuning (profiling runs)")
+    ap.add_argument("--band-min", type=int, default=-1,
+                    help="fixed band threshold (0 = no banded reverse pass) with --tile-overhead")
     ap.add_argument("--filter-epochs", type=int, default=20,
                     help="family blocks: training epochs of the learned filter")
     ap.add_argument("--filter-recall", type=float, default=0.995,
@@ -64,6 +67,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=400, help="serving: timed requests")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
     ap.add_argument("--serve-slots", type=int, default=3, help="serving: batches in flight")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="batched run: skip the other workloads' figures (next_rows)")
+    ap.add_argument("--next-steps", type=int, default=3,
+                    help="timed steps of the family block in next_rows")
+    ap.add_argument("--next-requests", type=int, default=200,
+                    help="serving requests timed in next_rows")
     return ap.parse_args()
 
 
@@ -97,12 +106,14 @@ def sha(path):
 
 def dp_source_sha():
     """Hash of what the DP kernels' DRAM traffic depends on: the DP section of
-    swgb_kernels.cu (lane arithmetic, the kernel, its dispatch and launch
-    sizes) and swgb_internal.cuh (tile shapes, arguments)."""
+    swgb_kernels.cu (the kernel, its dispatch and launch sizes), the lane
+    arithmetic of swgb_lane.cuh and swgb_internal.cuh (tile shapes,
+    arguments)."""
     src = open(KERNEL_SOURCE).read()
-    a = src.index("// Lane arithmetic")
+    a = src.index("// The DP kernel")
     b = src.index("// Issue-rate probe")
-    return hashlib.sha256(src[a:b].encode() + open(KERNEL_HEADER, "rb").read()).hexdigest()[:16]
+    return hashlib.sha256(src[a:b].encode() + open(LANE_HEADER, "rb").read() +
+                          open(KERNEL_HEADER, "rb").read()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -293,6 +304,9 @@ def run_ours(args):
     P = len(wl.pairs)
 
     # tile selection tuned on an evenly strided sample of the batch (untimed)
+    tuning = None
+    if args.band_min >= 0:
+        swgb.swgb_set_band_min(al.ctx, args.band_min)
     if args.tile_overhead >= 0:
         swgb.swgb_set_tile_overhead(al.ctx, args.tile_overhead)
         tile_overhead = args.tile_overhead
@@ -303,11 +317,13 @@ def run_ours(args):
         tune_out = torch.empty((tune_n, 5), dtype=torch.int32, device=dev)
         tile_overhead, _ = swgb.swgb_autotune(al.ctx, q.handle, r.handle, tune_pairs, params,
                                               tune_out, stream)
+        tuning = swgb.swgb_last_tuning(al.ctx)
         del tune_pairs, tune_out
 
     # the timed step replays the whole pipeline captured once into a CUDA graph
     # (swgb_plan_*): same kernels and records as swgb_align, no per-launch host work
     plan = None if args.no_graph else swgb.swgb_plan_create(al.ctx, q.handle, r.handle, pairs, params, out)
+    launch_kind = "direct calls" if plan is None else "CUDA graph (swgb_plan)"
 
     def step():
         if plan is not None:
@@ -344,8 +360,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     clock = clocks.summary()
-    if plan is not None:
-        swgb.swgb_plan_destroy(plan)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     cells = stats["forward_cells"]
@@ -368,6 +382,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host baseline: N = 1 only
         cpu = cpu_oracle_sample(wl, np.asarray(mat), args.cpu_seconds)
 
+    next_rows = None
+    if rank == 0 and world == 1 and not args.no_next_rows and not args.pairs:
+        if plan is not None:
+            swgb.swgb_plan_destroy(plan)
+            plan = None
+        next_rows = measure_next_rows(args, al, dev)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -380,7 +401,10 @@ def run_ours(args):
                    "reverse_cells": stats["reverse_cells"],
                    "int32_pairs": stats["n_int32_pairs"], "gap_open": 11, "gap_extend": 1,
                    "matrix": "BLOSUM62", "tile_overhead": tile_overhead,
-                   "launch": "direct calls" if plan is None else "CUDA graph (swgb_plan)",
+                   "band_min": swgb.swgb_get_band_min(al.ctx),
+                   "autotune": tuning,
+                   "band_pairs": stats["n_band_pairs"], "band_certified": stats["n_band_certified"],
+                   "launch": launch_kind,
                    "l2": "inputs (%.2f GB of residues) exceed L2; no flush" %
                          ((len(wl.q_res) + len(wl.r_res)) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -401,9 +425,111 @@ def run_ours(args):
         "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                    "reasons": clock["reasons"]},
     }
+    if next_rows is not None:
+        line["next_rows"] = next_rows
     print(json.dumps(line), flush=True)
+    if plan is not None:
+        swgb.swgb_plan_destroy(plan)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_plain(al, dev, name, steps, warmup):
+    """The small plain workload (10,000 pairs, lengths U[50,500]): every record
+    checked against the oracle, then the same step as the batched line
+    (CUDA-graph replay) timed on the device, and the oracle timed on all host
+    cores over the whole workload."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2303_01845_gb300 import swgb
+    mat = swgb.swgb_blosum62()
+    wl = make_workload(name, mat)
+    stream = torch.cuda.current_stream(dev)
+    q = al.seqset(torch.from_numpy(wl.q_res).to(dev), torch.from_numpy(wl.q_off).to(dev))
+    r = al.seqset(torch.from_numpy(wl.r_res).to(dev), torch.from_numpy(wl.r_off).to(dev))
+    pairs = torch.from_numpy(wl.pairs).to(dev)
+    out = torch.empty((len(wl.pairs), 5), dtype=torch.int32, device=dev)
+    params = swgb.make_params(mat, 11, 1, timing=True)
+    plan = swgb.swgb_plan_create(al.ctx, q.handle, r.handle, pairs, params, out)
+    for _ in range(warmup):
+        swgb.swgb_plan_launch(al.ctx, plan, stream)
+    swgb.swgb_sync(al.ctx, stream)
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    want = oracle.align_batch(wl.q_res, wl.q_off, wl.r_res, wl.r_off, wl.pairs, np.asarray(mat), 11, 1,
+                              n_threads=cores)
+    cpu_s = time.perf_counter() - t
+    exact = bool(np.array_equal(out.cpu().numpy(), want))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    fwd = []
+    for k in range(steps):
+        ev[k][0].record(stream)
+        swgb.swgb_plan_launch(al.ctx, plan, stream)
+        ev[k][1].record(stream)
+        swgb.swgb_sync(al.ctx, stream)
+        st = swgb.swgb_last_stats(al.ctx)
+        fwd.append(st["forward_ms"])
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    swgb.swgb_plan_destroy(plan)
+    q.close()
+    r.close()
+    cells = st["forward_cells"]
+    return {"workload": name, "pairs": len(wl.pairs), "forward_cells": cells,
+            "records_bit_exact_vs_oracle": exact, "ms_per_step": ms, "gcups": cells / ms / 1e6,
+            "alignments_per_s": len(wl.pairs) / ms * 1e3,
+            "gcups_forward_kernel": cells / statistics.mean(fwd) / 1e6, "steps": steps,
+            "launch": "CUDA graph (swgb_plan)",
+            "cpu_baseline": {"gcups": cells / cpu_s / 1e9, "alignments_per_s": len(wl.pairs) / cpu_s,
+                             "cores": cores, "kind": "oracle", "sample": "the whole workload"}}
+
+
+def measure_next_rows(args, al, dev):
+    """The other workloads' figures, added to the batched line: the small plain
+    workload, the many-against-many block with and without the learned filter,
+    and the query server under Poisson load.  Each leg is fenced: a failure
+    is reported in its place."""
+    import traceback
+    out = {}
+    steps = max(1, args.next_steps)
+    warm = max(1, min(args.warmup, 2))
+    try:
+        out["plain_10k"] = measure_plain(al, dev, "plain_10k", max(3, args.steps), warm)
+    except Exception as e:   # noqa: BLE001 -- reported in the line
+        out["plain_10k"] = {"error": "%s: %s" % (type(e).__name__, e), "trace": traceback.format_exc()[-800:]}
+    mlp = thr = None
+    try:
+        line, mlp, thr = measure_families(args, al, dev, "families_200k", steps, warm,
+                                          None if args.no_cpu_baseline else 4.0)
+        f = line["filter"]
+        out["families_200k"] = {
+            "candidates": line["config"]["candidates"], "passing_pairs": line["config"]["passing_pairs"],
+            "plain_ms_per_step": line["plain"]["ms_per_step"], "filtered_ms_per_step": line["ms_per_step"],
+            "plain_candidates_per_s": line["plain"]["alignments_per_s"],
+            "filtered_candidates_per_s": line["value"], "speedup": f["speedup_vs_plain"],
+            "recall": f["recall"], "kept_fraction": f["kept_fraction"],
+            "kept_results_exact": f["kept_results_exact"], "kmer_threshold_3": f["kmer_threshold_3"],
+            "stage_ms": {"plain": {k: line["plain"][k] for k in ("discover_ms", "align_ms", "identity_ms")},
+                         "filtered": f["ms"]},
+            "gcups_forward_kernel": line["plain"]["gcups_forward_kernel"],
+            "trained_on": f["trained_on"], "steps": steps, "cpu_baseline": line["cpu_baseline"],
+            "clocks": line["clocks"]}
+    except Exception as e:   # noqa: BLE001
+        out["families_200k"] = {"error": "%s: %s" % (type(e).__name__, e), "trace": traceback.format_exc()[-800:]}
+    if mlp is not None:
+        try:
+            line = measure_serving(args, al, dev, mlp, thr, 0.0, args.next_requests, args.serve_rate, warm)
+            out["serving_1m"] = {
+                "references": line["config"]["references"], "arrivals": line["config"]["arrivals"],
+                "requests": line["config"]["requests"], "slots": line["config"]["slots"],
+                "latency_ms": line["latency_ms"], "queue_ms": line["queue_ms"],
+                "throughput": line["throughput"], "max_batches_in_flight": line["max_batches_in_flight"],
+                "filter": "the network trained for families_200k", "clocks": line["clocks"]}
+        except Exception as e:   # noqa: BLE001
+            out["serving_1m"] = {"error": "%s: %s" % (type(e).__name__, e), "trace": traceback.format_exc()[-800:]}
+    return out
 
 
 def measure_e2e(al, wl, mat, dev, stream, args, dist=None, world=1):
@@ -488,16 +614,11 @@ def search_oracle_sample(fs, mat, target_s, seed=5):
 
 
 def run_search(args):
-    """The many-against-many block: discovery + alignment + identity, plain and
-    with the learned filter (trained beforehand, untimed, on a block drawn
-    with another seed)."""
-    import ctypes
-
-    import numpy as np
+    """The many-against-many block as its own bench line (--workload
+    families_200k)."""
     import torch
 
-    from paper_2303_01845_gb300 import filter as F
-    from paper_2303_01845_gb300 import swgb, workload
+    from paper_2303_01845_gb300 import swgb
 
     rank, world, local = dist_env()
     dist = None
@@ -506,36 +627,71 @@ def run_search(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    mat = swgb.swgb_blosum62()
-    spec = workload.FAMILY_SPECS[args.workload]
     al = swgb.Aligner(local)
+    line, _, _ = measure_families(args, al, dev, args.workload, args.steps, args.warmup,
+                                  None if args.no_cpu_baseline or rank != 0 else args.cpu_seconds,
+                                  dist, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def train_filter(al, dev, mat, spec, seed, epochs, recall):
+    """The learned filter, trained (untimed) on a family block drawn with
+    `seed`: exact labels, features, network, threshold.  Returns (MLP,
+    threshold, summary)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2303_01845_gb300 import filter as F
+    from paper_2303_01845_gb300 import swgb, workload
+    t = time.perf_counter()
+    fs = workload.generate_families(dataclasses.replace(spec, seed=seed), mat)
+    s = al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
+    cand, _ = al.discover(s, 6, 2)
+    params = swgb.make_params(mat, 11, 1)
+    _, ident = F.exact_labels(al, s, cand, params, swgb.make_thresholds())
+    X = swgb.swgb_pair_features(al.ctx, s.handle, s.handle, cand)
+    y = ident[:, 2].to(torch.float32).contiguous()
+    net, losses = F.train(al, X, y, epochs=epochs, batch=8192, lr=3e-3, seed=1)
+    threshold = F.calibrate(net, X, y, recall)
+    torch.cuda.synchronize()
+    summary = {"candidates": int(cand.shape[0]), "passing": int(y.sum().item()), "epochs": epochs,
+               "seconds": time.perf_counter() - t, "final_loss": losses[-1], "seed": seed}
+    del cand, ident, X, y
+    s.close()
+    return net, threshold, summary
+
+
+def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None, world=1):
+    """The many-against-many block: discovery + alignment + identity, plain and
+    with the learned filter (trained beforehand, untimed, on a block drawn
+    with another seed).  Returns (bench line, trained network parameters,
+    threshold)."""
+    import ctypes
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_2303_01845_gb300 import swgb, workload
+
+    mat = swgb.swgb_blosum62()
+    spec = workload.FAMILY_SPECS[name]
     stream = torch.cuda.current_stream(dev)
     params = swgb.make_params(mat, 11, 1, timing=True)
     th = swgb.make_thresholds()
     lib = swgb.load()
 
-    def load_block(seed):
-        import dataclasses
-        fs = workload.generate_families(dataclasses.replace(spec, seed=seed), mat)
-        return fs, al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
-
     # ---- training block (untimed): exact labels, features, network, threshold
-    t_train = time.perf_counter()
-    _, s_tr = load_block(spec.seed + 1)
-    cand_tr, _ = al.discover(s_tr, 6, 2)
-    _, ident_tr = F.exact_labels(al, s_tr, cand_tr, params, th)
-    X_tr = swgb.swgb_pair_features(al.ctx, s_tr.handle, s_tr.handle, cand_tr)
-    y_tr = ident_tr[:, 2].to(torch.float32).contiguous()
-    net, losses = F.train(al, X_tr, y_tr, epochs=args.filter_epochs, batch=8192, lr=3e-3, seed=1)
-    threshold = F.calibrate(net, X_tr, y_tr, args.filter_recall)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t_train
-    n_train, n_train_pos = int(cand_tr.shape[0]), int(y_tr.sum().item())
-    del cand_tr, ident_tr, X_tr, y_tr
-    s_tr.close()
+    net, threshold, trained = train_filter(al, dev, mat, spec, spec.seed + 1, args.filter_epochs,
+                                           args.filter_recall)
 
     # ---- the measured block
-    fs, s = load_block(spec.seed)
+    fs = workload.generate_families(dataclasses.replace(spec, seed=spec.seed), mat)
+    s = al.seqset(torch.from_numpy(fs.res).to(dev), torch.from_numpy(fs.off).to(dev))
     cap = al.discover(s, 6, 2)[0].shape[0]
     cand = torch.empty((cap, 2), dtype=torch.int32, device=dev)
     counts = torch.empty((cap,), dtype=torch.int32, device=dev)
@@ -611,21 +767,21 @@ def run_search(args):
             filt.setdefault("discover", []).append(ev[0].elapsed_time(ev[1]))
             launches["filtered"] += nl + swgb.swgb_last_stats(al.ctx)["kernel_launches"]
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain_step(False)
         filtered_step(False)
     stats = None
-    with ClockSampler(local) as clocks:
+    with ClockSampler(dev.index) as clocks:
         torch.cuda.synchronize()
-        for _ in range(args.steps):
+        for _ in range(steps):
             stats = plain_step(True)
             filtered_step(True)
     clock = clocks.summary()
     assert n_found.value == cap
     plain_ms = max_over_ranks(sum(plain["step"]), dist, dev)
     filt_ms = max_over_ranks(sum(filt["step"]), dist, dev)
-    plain_rate = job_rate(cap, world, args.steps, plain_ms)
-    filt_rate = job_rate(cap, world, args.steps, filt_ms)
+    plain_rate = job_rate(cap, world, steps, plain_ms)
+    filt_rate = job_rate(cap, world, steps, filt_ms)
     # recall of the filter against the exact pass / fail of every candidate
     y = ident[:, 2].cpu().numpy() > 0
     keep = np.zeros(cap, bool)
@@ -634,17 +790,18 @@ def run_search(args):
     recall = float(keep[y].mean()) if y.any() else None
     cnt = counts.cpu().numpy()
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = search_oracle_sample(fs, np.asarray(mat), args.cpu_seconds)
-    if rank != 0:
-        return
+    if cpu_seconds:
+        cpu = search_oracle_sample(fs, np.asarray(mat), cpu_seconds)
+    mlp_params = net.get()
+    net.close()
+    s.close()
     mean = lambda d, k: statistics.mean(d[k])
     line = {
         "metric": METRIC, "value": filt_rate, "unit": "alignments/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": filt_ms / args.steps,
+        "steps": steps, "warmup": warmup, "ms_per_step": filt_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i16x2+i32 align, bf16 net", "data": "synthetic",
-        "config": {"workload": args.workload, "sequences": len(fs), "residues": int(fs.off[-1]),
+        "config": {"workload": name, "sequences": len(fs), "residues": int(fs.off[-1]),
                    "k": 6, "min_shared": 2, "candidates": cap,
                    "forward_cells": stats["forward_cells"],
                    "passing_pairs": int(y.sum()),
@@ -657,14 +814,14 @@ def run_search(args):
                    "kept_results_exact": same, "threshold": threshold,
                    "trained_on": "%s seed %d: %d candidates, %d passing; %d epochs, %.1f s "
                                  "(labels, features, training)" %
-                                 (args.workload, spec.seed + 1, n_train, n_train_pos,
-                                  args.filter_epochs, t_train),
-                   "final_loss": losses[-1],
+                                 (name, trained["seed"], trained["candidates"], trained["passing"],
+                                  trained["epochs"], trained["seconds"]),
+                   "final_loss": trained["final_loss"],
                    "kmer_threshold_3": {"recall": float((cnt[y] >= 3).mean()) if y.any() else None,
                                         "kept_fraction": float((cnt >= 3).mean())},
                    "speedup_vs_plain": filt_rate / plain_rate,
                    "ms": {k: mean(filt, k) for k in filt}},
-        "plain": {"alignments_per_s": plain_rate, "ms_per_step": plain_ms / args.steps,
+        "plain": {"alignments_per_s": plain_rate, "ms_per_step": plain_ms / steps,
                   "discover_ms": mean(plain, "discover"), "align_ms": mean(plain, "align"),
                   "identity_ms": mean(plain, "identity"), "forward_ms": mean(plain, "fwd"),
                   "gcups_forward_kernel": stats["forward_cells"] / (mean(plain, "fwd") / 1e3) / 1e9},
@@ -678,47 +835,43 @@ def run_search(args):
         "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                    "reasons": clock["reasons"]},
     }
-    print(json.dumps(line), flush=True)
+    return line, mlp_params, threshold
 
 
 def run_serving(args):
-    """The query server over 1,000,000 resident references: requests of 1 to
-    1,000 queries arrive as a Poisson process; each goes through shared-6-mer
-    candidates from the resident index, the learned filter (trained
-    beforehand on a family block of another seed), exact alignment and
-    identity.  Latency = submission to completion of a request."""
-    import dataclasses
-
-    import numpy as np
+    """The query server as its own bench line (--workload serving_1m)."""
     import torch
 
-    from paper_2303_01845_gb300 import filter as F
     from paper_2303_01845_gb300 import swgb, workload
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     mat = swgb.swgb_blosum62()
-    params = swgb.make_params(mat, 11, 1)
     al = swgb.Aligner(local)
-    # ---- the filter, trained on an all-vs-all family block (untimed)
-    t_train = time.perf_counter()
-    fs_tr = workload.generate_families(dataclasses.replace(workload.FAMILY_SPECS["families_200k"],
-                                                           seed=4), mat)
-    s_tr = al.seqset(torch.from_numpy(fs_tr.res).to(dev), torch.from_numpy(fs_tr.off).to(dev))
-    cand_tr, _ = al.discover(s_tr, 6, 2)
-    _, ident_tr = F.exact_labels(al, s_tr, cand_tr, params)
-    X_tr = swgb.swgb_pair_features(al.ctx, s_tr.handle, s_tr.handle, cand_tr)
-    y_tr = ident_tr[:, 2].to(torch.float32).contiguous()
-    net, _ = F.train(al, X_tr, y_tr, epochs=args.filter_epochs, batch=8192, lr=3e-3, seed=1)
-    threshold = F.calibrate(net, X_tr, y_tr, args.filter_recall)
+    net, threshold, trained = train_filter(al, dev, mat, workload.FAMILY_SPECS["families_200k"], 4,
+                                           args.filter_epochs, args.filter_recall)
     mlp_params = net.get()
     net.close()
-    del cand_tr, ident_tr, X_tr, y_tr
-    s_tr.close()
-    t_train = time.perf_counter() - t_train
-    # ---- resident references: 100,000 families x 10 copies; queries: an
-    # 11th copy of random families (or an unrelated draw)
+    line = measure_serving(args, al, dev, mlp_params, threshold, trained["seconds"],
+                           args.serve_requests, args.serve_rate, args.warmup)
+    print(json.dumps(line), flush=True)
+
+
+def measure_serving(args, al, dev, mlp_params, threshold, train_s, n_requests, rate, warmup):
+    """The query server over args.serve_refs resident references: requests of
+    1 to 1,000 queries arrive as a Poisson process at `rate`; each goes
+    through shared-6-mer candidates from the resident index, the learned
+    filter, exact alignment and identity.  Latency = submission to completion
+    of a request.  Returns the bench line."""
+    import numpy as np
+    import torch
+
+    from paper_2303_01845_gb300 import swgb, workload
+
+    mat = swgb.swgb_blosum62()
+    params = swgb.make_params(mat, 11, 1)
+    # ---- resident references: families x 10 copies; queries: an 11th copy
     n_fam = args.serve_refs // 10
     spec = workload.FamilySpec("serving_refs", n_fam, 11, "lognormal", 20, 5000, median=250.0,
                                sigma=0.7, seed=5)
@@ -731,9 +884,8 @@ def run_serving(args):
         lens = (fs.off[idx + 1] - fs.off[idx]).astype(np.int64)
         off = np.zeros(len(idx) + 1, np.int64)
         np.cumsum(lens, out=off[1:])
-        starts = fs.off[idx]
-        res = np.concatenate([fs.res[s:s + l] for s, l in zip(starts, lens)]).astype(np.uint8)
-        return res, off
+        take = np.repeat(fs.off[idx] - off[:-1], lens) + np.arange(int(off[-1]), dtype=np.int64)
+        return fs.res[take].astype(np.uint8), off
     rr, ro = pack(np.nonzero(~is_q)[0])
     qr, qo = pack(np.nonzero(is_q)[0])
     t_index = time.perf_counter()
@@ -741,7 +893,7 @@ def run_serving(args):
     index = swgb.Index(al, refs, 6)
     torch.cuda.synchronize()
     t_index = time.perf_counter() - t_index
-    srv = swgb.Server(refs, index, params, mlp_params, device=local, slots=args.serve_slots,
+    srv = swgb.Server(refs, index, params, mlp_params, device=dev.index, slots=args.serve_slots,
                       threshold=threshold, max_batch_queries=4096, max_batch_residues=1 << 21,
                       max_inflight_bytes=8 << 30, candidates_per_query=1024)
     rng = np.random.default_rng(17)
@@ -753,12 +905,12 @@ def run_serving(args):
         off = qo[q0:q0 + size + 1] - qo[q0]
         return qr[qo[q0]:qo[q0 + size]], off
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         srv.wait(srv.submit(*make_request()))
-    reqs = [make_request() for _ in range(args.serve_requests)]
-    gaps = rng.exponential(1.0 / args.serve_rate, len(reqs))
+    reqs = [make_request() for _ in range(n_requests)]
+    gaps = rng.exponential(1.0 / rate, len(reqs))
     tickets = []
-    with ClockSampler(local) as clocks:
+    with ClockSampler(dev.index) as clocks:
         t0 = time.perf_counter()
         next_t = t0
         for (c, o), g in zip(reqs, gaps):
@@ -779,17 +931,19 @@ def run_serving(args):
     stats = srv.stats()
     info = index.info()
     srv.close()
-    line = {
+    index.close()
+    refs.close()
+    return {
         "metric": METRIC, "value": aligned / wall, "unit": "alignments/s", "n_gpus": 1,
-        "steps": len(reqs), "warmup": args.warmup, "ms_per_step": 1000 * wall / len(reqs),
+        "steps": len(reqs), "warmup": warmup, "ms_per_step": 1000 * wall / len(reqs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i16x2+i32 align, bf16 net", "data": "synthetic",
         "config": {"workload": "serving_%dk" % (args.serve_refs // 1000),
                    "references": int(len(ro) - 1), "reference_residues": int(ro[-1]),
                    "requests": len(reqs), "queries_per_request": "uniform 1..1000",
-                   "arrivals": "Poisson, %.1f requests/s" % args.serve_rate,
+                   "arrivals": "Poisson, %.1f requests/s" % rate,
                    "slots": args.serve_slots, "index_bytes": info["bytes"],
-                   "index_build_s": t_index, "filter_training_s": t_train,
+                   "index_build_s": t_index, "filter_training_s": train_s,
                    "filter_threshold": threshold,
                    "step": "one request (submission to completion)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -806,7 +960,6 @@ def run_serving(args):
         "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                    "reasons": clock["reasons"]},
     }
-    print(json.dumps(line), flush=True)
 
 
 def main():

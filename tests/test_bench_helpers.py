@@ -19,13 +19,13 @@ def test_traffic_follows_the_dp_source_hash(tmp_path, monkeypatch):
 
 def test_dp_source_hash_covers_the_dp_section_only(tmp_path, monkeypatch):
     src = open(bench.KERNEL_SOURCE).read()
-    head, rest = src.split("// Lane arithmetic", 1)
+    head, rest = src.split("// The DP kernel", 1)
     copy = tmp_path / "k.cu"
     monkeypatch.setattr(bench, "KERNEL_SOURCE", str(copy))
     copy.write_text(src)
     base = bench.dp_source_sha()
-    copy.write_text(head + "// an edit before the DP section\n// Lane arithmetic" + rest)
+    copy.write_text(head + "// an edit before the DP section\n// The DP kernel" + rest)
     assert bench.dp_source_sha() == base
     dp, tail = rest.split("// Issue-rate probe", 1)
-    copy.write_text(head + "// Lane arithmetic" + dp + "// an edit in it\n// Issue-rate probe" + tail)
+    copy.write_text(head + "// The DP kernel" + dp + "// an edit in it\n// Issue-rate probe" + tail)
     assert bench.dp_source_sha() != base
