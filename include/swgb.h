@@ -210,21 +210,27 @@ int swgb_get_tile_overhead(const swgb_ctx* ctx);          /* current value */
 
 /* ---- banded reverse pass ----
  * The reverse pass (start coordinates) of a scored pair may run over a
- * diagonal band of the reversed prefixes instead of their whole rectangle:
- * bands of 240 or 392 diagonals around the line from the end cell to the
- * diagonal lr - lq, a ring of 16 x 16 or 32 x 12 lanes x rows (the paper's
- * aligner fills the whole matrix, Sec. "Load balancing"; the band is this
- * library's).  The band's start is kept only under an exactness certificate:
- * every cell on the band's border through which an alignment could leave
- * it bounds that alignment's score by the band's value there plus the
- * forward pass's maximum over the reference rows beyond it plus one gap
- * opening; if every such bound is below S, no alignment of score S leaves
- * the band and its first cell of value S is the start of the whole-matrix
- * definition.  Otherwise the pair is re-run over the whole rectangle, so the
- * records never depend on the setting.  The forward pass records those
- * maxima (64 slots of 4 bytes per pair) for pairs whose query and reference
- * both have at least band_min residues on the packed 16-bit path; a cost
- * model picks per pair between the rectangle and the bands.
+ * staircase band of the reversed prefixes (la x lb) instead of their whole
+ * rectangle (the paper's aligner fills the whole matrix, Sec. "Load
+ * balancing"; the band is this library's).  On a 32-lane tile of 32 R rows
+ * (R = 9..13), chunk c of the reversed reference streams only the query
+ * positions [c 32 R - khi, (c + 1) 32 R + W - khi), which hold the diagonals
+ * from min(0, lb - la) - m to max(0, lb - la) + m of the chunk's rows, with
+ * W = |lb - la| + 2 m, khi = max(0, lb - la) + m and m = 64 + max(la, lb) / 32.
+ * The DP there is anchored at the end cell.  The band's start is kept only
+ * under an exactness certificate: every cell of the computed region through
+ * which an alignment could leave it bounds that alignment's score by the
+ * region's value there plus the forward pass's maximum over the reference
+ * rows beyond it plus one gap opening; if every such bound at a position up
+ * to the first cell of value S is below S, no alignment of score S leaves
+ * the region first and its first cell of value S is the start of the
+ * whole-matrix definition.  Otherwise the pair is re-run over the whole
+ * rectangle, so the records never depend on the setting.  The forward pass
+ * records those maxima (one int32 per forward lane, from a pool of at most
+ * 512 MB per workspace; pairs past it keep the rectangle) for pairs whose
+ * query and reference both have at least band_min residues on the packed
+ * 16-bit path; a cost model picks per pair between the rectangle and the
+ * band tiles.
  * band_min: 0 (off) or 32..65536; default 0; a context setting read by
  * swgb_align and swgb_plan_create, tuned by swgb_autotune. */
 int swgb_set_band_min(swgb_ctx* ctx, int band_min);      /* EINVAL outside the range */

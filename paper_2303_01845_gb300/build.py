@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SWGB_LIB = os.path.join(OUT, "libswgb.so")
 WORKLOAD_LIB = os.path.join(OUT, "libswgb_workload.so")
 
-CUDA_SOURCES = ["swgb_api.cu", "swgb_kernels.cu", "swgb_band.cu", "swgb_search.cu", "swgb_filter.cu",
+CUDA_SOURCES = ["swgb_api.cu", "swgb_kernels.cu", "swgb_search.cu", "swgb_filter.cu",
                 "swgb_server.cu"]
 CUDA_HEADERS = ["swgb_internal.cuh", "swgb_host.cuh", "swgb_lane.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -147,10 +147,10 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
                     ctx->blocks_per_sm[v][d][c][s] =
                         std::max(1, dp_blocks_per_sm(c, s, d == 1, v ? kProfileRows : kStdLetters + 1));
             }
-    for (int c = 0; c < kBandConfigs; ++c) {
-        if ((e = band_configure(c)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
-        ctx->band_blocks[c] = std::max(1, band_blocks_per_sm(c));
-    }
+    for (int s = kFirstChunkable; s < kBandShapeEnd; ++s)
+        for (int v = 0; v < 2; ++v)
+            ctx->band_blocks[v][s - kFirstChunkable] =
+                std::max(1, dp_blocks_per_sm(0, s, true, v ? kProfileRows : kStdLetters + 1, true));
     for (auto& ev : ctx->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "cudaEventCreate");
     if ((e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -179,7 +179,7 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
     cudaFree(ws.counters);
     cudaFree(ws.boundary);
     cudaFree(ws.fmax);
-    cudaFree(ws.band_prof);
+    cudaFree(ws.fmax_off);
     cudaFree(ctx->d_pairs);
     cudaFree(ctx->d_out);
     cudaFree(ctx->d_encode_flag);
@@ -394,7 +394,7 @@ void free_store(Store& st, bool with_status) {
     cudaFree(ws.task_ctr);
     cudaFree(ws.boundary);
     cudaFree(ws.fmax);
-    cudaFree(ws.band_prof);
+    cudaFree(ws.fmax_off);
     if (with_status) {
         cudaFree(ws.status);
         cudaFree(ws.counters);
@@ -406,28 +406,19 @@ void free_store(Store& st, bool with_status) {
 int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, const swgb_seqset* r, int64_t n_pairs) {
     Workspace& ws = store.ws;
     if (ctx->band_min > 0) {
-        // forward maxima per pair, and the band kernels' profiles: one slice per
-        // resident warp of each config (the configs run concurrently)
-        CK(grow(&ws.fmax, &store.fmax_capacity, std::max<int64_t>(n_pairs, 1) * kFmaxSlots), "workspace alloc");
-        const int64_t rstride = band_rstride(std::max<int64_t>(std::max(q->max_len, r->max_len), 1));
-        const int64_t per_warp = band_prof_bytes_per_warp(rstride, kProfileRows);
-        int64_t slots = 0;
-        for (int c = 0; c < kBandConfigs; ++c) {
-            store.band_region_off[c] = slots;
-            store.band_region_slots[c] = (int64_t)ctx->sm_count * ctx->band_blocks[c] * (kBandThreads / 32);
-            slots += store.band_region_slots[c];
+        // forward maxima: a slice of 1 + ceil(lr / Rf) entries per recording
+        // pair (Rf >= 8), handed out by the keys kernel; pairs past the pool
+        // record none and keep the full reverse pass
+        const int64_t per_pair = 2 + (std::max<int64_t>(r->max_len, 1) + 7) / 8;
+        const int64_t want = std::min<int64_t>(std::max<int64_t>(n_pairs, 1) * per_pair, kFmaxPoolMax);
+        if (ws.fmax_capacity < want) {
+            cudaFree(ws.fmax);
+            ws.fmax = nullptr;
+            ws.fmax_capacity = 0;
+            CK(cudaMalloc(&ws.fmax, sizeof(int32_t) * (size_t)want), "workspace alloc");
+            ws.fmax_capacity = want;
         }
-        if (ws.band_rstride < rstride || ws.band_slots < slots || !ws.band_prof) {
-            cudaFree(ws.band_prof);
-            ws.band_prof = nullptr;
-            ws.band_slots = 0;
-            store.band_capacity = 0;
-            CK(cudaMalloc(&ws.band_prof, (size_t)(per_warp * slots)), "band scratch alloc");
-            store.band_capacity = per_warp * slots;
-            ws.band_slots = slots;
-            ws.band_rstride = rstride;
-            ws.band_prof_stride = per_warp;
-        }
+        CK(grow(&ws.fmax_off, &store.fmax_off_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     }
     CK(grow(&ws.bin_of, &store.bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     CK(grow(&ws.order, &store.order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
@@ -446,6 +437,15 @@ int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, const swgb_
             store.region_slots[c][s] = n;
             slots += n;
         }
+    // the band kernels run beside the reverse kernels of their shapes
+    for (int s = kFirstChunkable; s < kBandShapeEnd; ++s) {
+        const int b = s - kFirstChunkable;
+        const int64_t n = (int64_t)ctx->sm_count * std::max(ctx->band_blocks[0][b], ctx->band_blocks[1][b]) *
+                          (kDPThreads / 32);
+        store.band_region_off[b] = slots;
+        store.band_region_slots[b] = n;
+        slots += n;
+    }
     if (stride > ws.boundary_stride || slots > ws.boundary_slots || !ws.boundary) {
         cudaFree(ws.boundary);
         ws.boundary = nullptr;
@@ -481,8 +481,8 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     ClassArgs ca = make_class_args(params->matrix, params->gap_open + params->gap_extend, max_score,
                                    force32);
     ca.tile_overhead = ctx->tile_overhead;
-    // the banded reverse pass needs the packed path and the store's scratch
-    const bool band = ctx->band_min > 0 && !ca.force32 && ws.fmax && ws.band_prof;
+    // the banded reverse pass needs the packed path and the forward maxima
+    const bool band = ctx->band_min > 0 && !ca.force32 && ws.fmax && ws.fmax_off;
     ca.band_min = band ? ctx->band_min : 0;
     const int pv = q->max_code < kStdLetters ? 0 : 1;   // profile variant
     sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;
@@ -494,8 +494,9 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
 
     const SeqView qv = view(q), rv = view(r);
     // one round: keys -> scan -> scatter -> the DP kernels of every (class,
-    // shape) and, in the reverse round, the band kernels, spread over the
-    // caller's stream and the side streams, largest tiles first
+    // shape) and, in the reverse round, the band kernels of the chunkable
+    // shapes, spread over the caller's stream and the side streams, largest
+    // tiles first
     auto round = [&](int mode, int dir) -> int {
         CK(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kNumBins, st), "memset");
         CK(launch_keys(qv, rv, pairs, n_pairs, out, mode, ca, ws, st), "keys kernel");
@@ -512,54 +513,50 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
             const int k = rr++ % (swgb_ctx::kSide + 1);
             return k == 0 ? st : ctx->side[k - 1];
         };
+        auto dp_args = [&]() {
+            DPArgs a;
+            a.q = qv;
+            a.r = rv;
+            a.pairs = pairs;
+            a.order = ws.order;
+            a.scan = ws.scan;
+            a.out = out;
+            a.status = ws.status;
+            a.boundary_stride = ws.boundary_stride;
+            a.fmax = band ? ws.fmax : nullptr;
+            a.fmax_off = band ? ws.fmax_off : nullptr;
+            a.counters = ws.counters;
+            a.sc = sc;
+            return a;
+        };
         if (mode == kKeysReverse && band) {
-            for (int c = kBandConfigs - 1; c >= 0; --c) {
-                BandArgs b;
-                b.q = qv;
-                b.r = rv;
-                b.pairs = pairs;
-                b.order = ws.order;
-                b.scan = ws.scan;
-                b.task_ctr = ws.task_ctr + 3 * kNumKernels + c;
-                b.out = out;
-                b.status = ws.status;
-                b.fmax = ws.fmax;
-                b.prof = ws.band_prof + store.band_region_off[c] * ws.band_prof_stride;
-                b.prof_stride = ws.band_prof_stride;
-                b.rstride = ws.band_rstride;
-                b.slots = store.band_region_slots[c];
-                b.counters = ws.counters;
-                b.bucket = kBandFirstBucket + c;
-                b.sc = sc;
-                const int64_t per_block = (kBandThreads / 32) * (32 / band_G(c)) * 2;
-                int64_t grid = (int64_t)ctx->sm_count * ctx->band_blocks[c];
-                grid = std::min(grid, (n_pairs + per_block - 1) / per_block);
-                grid = std::min(grid, b.slots / (kBandThreads / 32));
-                CK(launch_band(c, b, (int)std::max<int64_t>(grid, 1), next_stream()), "band kernel");
+            for (int s = kBandShapeEnd - 1; s >= kFirstChunkable; --s) {
+                const int b = s - kFirstChunkable;
+                DPArgs a = dp_args();
+                a.task_ctr = ws.task_ctr + 3 * kNumKernels + b;
+                a.boundary = ws.boundary + store.band_region_off[b] * ws.boundary_stride;
+                a.boundary_slots = store.band_region_slots[b];
+                a.first_bucket = band_first_bucket(s);
+                a.end_bucket = band_end_bucket(s);
+                int64_t grid = (int64_t)ctx->sm_count * ctx->band_blocks[pv][b];
+                const int64_t need = (n_pairs + pairs_per_block(0, s) - 1) / pairs_per_block(0, s);
+                grid = std::max<int64_t>(1, std::min(grid, need));
+                CK(launch_dp(0, s, true, a, (int)grid, next_stream(), true), "band dp kernel");
                 ++launches;
             }
         }
         for (int c = 0; c < kClasses; ++c) {
             for (int s = kNumShapes - 1; s >= 0; --s) {
                 cudaStream_t ks = next_stream();
-                DPArgs a;
-                a.q = qv;
-                a.r = rv;
-                a.pairs = pairs;
-                a.order = ws.order;
-                a.scan = ws.scan;
+                DPArgs a = dp_args();
                 a.task_ctr = ws.task_ctr + dir * kNumKernels + c * kNumShapes + s;
-                a.out = out;
-                a.status = ws.status;
                 const bool chunkable = s >= kFirstChunkable;
                 a.boundary = chunkable ? ws.boundary + store.region_off[c][s] * ws.boundary_stride : nullptr;
-                a.boundary_stride = ws.boundary_stride;
                 a.boundary_slots = chunkable ? store.region_slots[c][s] : 0;
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
-                a.fmax = (mode == kKeysForward && band) ? ws.fmax : nullptr;
-                a.band_min = ca.band_min;
-                a.sc = sc;
+                // the forward maxima are written by the forward round only
+                if (mode != kKeysForward) a.fmax_off = nullptr;
                 const int rev = mode != kKeysForward ? 1 : 0;
                 int64_t grid = (int64_t)ctx->sm_count * ctx->blocks_per_sm[pv][rev][c][s];
                 const int64_t need = (n_pairs + pairs_per_block(c, s) - 1) / pairs_per_block(c, s);
@@ -920,7 +917,8 @@ SWGB_EXPORT int swgb_align_noalloc(const uint8_t* q_codes, const int64_t* q_offs
                 a.first_bucket = shape_first_bucket(c, s);
                 a.end_bucket = shape_end_bucket(c, s);
                 a.fmax = nullptr;
-                a.band_min = 0;
+                a.fmax_off = nullptr;
+                a.counters = ws.counters;
                 a.sc = sc;
                 int64_t grid = (int64_t)d->sm_count * d->blocks_per_sm[dir][c][s];
                 const int64_t per_block = (int64_t)(kDPThreads / 32) * (32 / shape_G(s)) * (c == 0 ? 2 : 1);

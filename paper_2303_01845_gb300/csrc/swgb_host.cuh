@@ -27,10 +27,9 @@ struct Store {
     int64_t order_capacity = 0;  // ws.order
     int64_t region_off[kClasses][kNumShapes] = {};
     int64_t region_slots[kClasses][kNumShapes] = {};
-    int64_t fmax_capacity = 0;          // ws.fmax, in int32
-    int64_t band_capacity = 0;          // ws.band_prof, in bytes
-    int64_t band_region_off[kBandConfigs] = {};   // warp slots of each band config
-    int64_t band_region_slots[kBandConfigs] = {};
+    int64_t fmax_off_capacity = 0;      // ws.fmax_off
+    int64_t band_region_off[kBandShapes] = {};   // chunk-boundary rows of the band kernels
+    int64_t band_region_slots[kBandShapes] = {};
 };
 
 struct swgb_ctx {
@@ -50,7 +49,7 @@ struct swgb_ctx {
     int blocks_per_sm[2][2][kClasses][kNumShapes] = {};
     int tile_overhead = kTileOverhead;
     int band_min = kBandMinDefault;  // banded reverse pass from this length (0 = off)
-    int band_blocks[kBandConfigs] = {};   // resident blocks per SM of each band kernel
+    int band_blocks[2][kBandShapes] = {};   // resident blocks per SM of each band kernel, [variant]
     swgb_tuning tuning{};            // the last swgb_autotune's figures
     cudaEvent_t ev[6] = {};
     // the DP kernels of one direction run on the caller's stream and these

@@ -70,47 +70,64 @@ constexpr int kQBinShift = 3;                 // 8 residues per bin
 constexpr int kNumKernels = kClasses * kNumShapes;
 
 // ---- banded reverse pass ---------------------------------------------------
-// A scored pair on the packed path may run its reverse pass over a diagonal
-// band of the reversed prefixes instead of the whole rectangle (band_kernel,
-// swgb_band.cu).  Config c uses groups of band_G(c) lanes of band_R(c) rows
-// arranged as a ring: a lane moves on to rows G*R further up when its window
-// of (G-1)(R+1) streamed positions ends, so every lane stays busy and the
-// computed region is a staircase band that always covers band_width(c) whole
-// diagonals.  A pair takes config c only when the drift of its end diagonal
-// plus twice band_margin(its length) fits that width.  The band's result is kept only
-// under the exactness certificate checked by the kernel; otherwise the pair
-// is re-run by the full reverse pass.
-constexpr int kBandConfigs = 2;
-__host__ __device__ constexpr int band_G(int c) { return c == 0 ? 16 : 32; }
-__host__ __device__ constexpr int band_R(int c) { return c == 0 ? 16 : 12; }
-// Diagonals a band must keep free on each side of the drift for a pair of
-// length L (the longer prefix) to certify: the forward maxima bound a block of
-// about L / 63 rows, and the path's wander grows with L.
-__host__ __device__ constexpr int64_t band_margin(int64_t L) { return 40 + L / 24; }
-__host__ __device__ constexpr int band_width(int c) { return band_G(c) * (band_R(c) + 1) - 2 * band_R(c); }
-// Per-pair maxima of the forward pass's H over blocks of reference rows, the
-// certificate's bound on the part of an alignment before a band exit: entry 0
-// holds the block height SB (or kFmaxNone: no maxima recorded), entry 1 + k the
-// largest H of reference rows [k SB, (k + 1) SB).  SB is a whole number of the
-// forward tile's rows per lane, so every forward lane lies in one block and
-// adds its maximum there alone; at most kFmaxSlots - 1 blocks.
-constexpr int kFmaxSlots = 64;
-constexpr int32_t kFmaxNone = 0x7fffffff;
-__host__ __device__ inline int fmax_slot_rows(int64_t lr, int lane_rows) {
-    const int64_t per = (lr + kFmaxSlots - 2) / (kFmaxSlots - 1);
-    return (int)((per + lane_rows - 1) / lane_rows * lane_rows);
+// A scored pair on the packed path whose sequences are both at least the
+// context's band_min long may run its reverse pass over a staircase band of
+// the reversed prefixes (la query x lb reference positions) instead of the
+// whole rectangle.  It runs on a 32-lane tile of ROWS = 32 R rows: chunk c
+// (reversed reference rows [c ROWS, (c + 1) ROWS)) streams only the window
+// [c ROWS - khi, (c + 1) ROWS + W - khi) of query positions, which holds the
+// diagonals (khi - W, khi] (row - position) of every row of the chunk.
+// band_geometry centres them on the segment from the origin's diagonal 0 to
+// the far corner's lb - la, with band_margin(L) diagonals free on each side.
+// The DP over the band is anchored (H = 0 only before the origin, kFloorH
+// outside the band and as the floor), and its start is kept only under the
+// exactness certificate the kernel checks; otherwise the pair is re-run over
+// the whole rectangle.
+constexpr int kFloorH = -8192;
+__host__ __device__ constexpr int64_t band_margin(int64_t L) { return 64 + L / 32; }
+__host__ __device__ inline void band_geometry(int64_t la, int64_t lb, int64_t* W, int64_t* khi) {
+    const int64_t d = lb - la;
+    const int64_t m = band_margin(la > lb ? la : lb);
+    *W = (d < 0 ? -d : d) + 2 * m;
+    *khi = (d > 0 ? d : 0) + m;
 }
+// Window [w0, w1) of chunk c (rows per chunk `rows`), clipped to [0, la).
+__host__ __device__ inline void band_window(int64_t c, int64_t rows, int64_t W, int64_t khi, int64_t la,
+                                            int64_t* w0, int64_t* w1) {
+    const int64_t lo = c * rows - khi, hi = (c + 1) * rows + W - khi;
+    *w0 = lo < 0 ? 0 : lo;
+    *w1 = hi > la ? la : hi;
+}
+// Per-pair maxima of the forward pass's H over the reference rows of each
+// forward lane, the certificate's bound on the part of an alignment beyond a
+// band exit.  The keys kernel hands each recording pair a slice of
+// 1 + ceil(lr / Rf) entries (fmax_off[p], -1 = none; Rf = its forward tile's
+// rows per lane): entry 0 holds Rf, entry 1 + k the largest H of reference
+// rows [k Rf, (k + 1) Rf), written once by the forward lane holding them.
 // Shortest query and reference (whole sequences) of a pair whose forward pass
-// records those maxima; the context's setting, tuned by swgb_autotune (0 = no
-// banded reverse pass, the default).
+// records them; the context's setting, tuned by swgb_autotune (0 = no banded
+// reverse pass, the default).
 constexpr int kBandMinDefault = 0;
-
-// bins: the two classes' buckets, then one bucket per band config
+// Entries of a store's forward-maxima pool at most (int32 each, 512 MB).
+constexpr int64_t kFmaxPoolMax = int64_t(1) << 27;
+// The band tiles are the chunkable shapes with 9 to 13 rows per lane (smaller
+// chunks give narrower windows, and these kernels keep all their state in
+// registers); their buckets follow the classes' buckets, kChunkBuckets per
+// shape (more chunks first).
+constexpr int kBandShapeEnd = kFirstChunkable + 5;
+constexpr int kBandShapes = kBandShapeEnd - kFirstChunkable;
 constexpr int kBandFirstBucket = kNumBuckets;
-constexpr int kNumBins = (kNumBuckets + kBandConfigs) * kQBins;
+constexpr int kNumBins = (kNumBuckets + kBandShapes * kChunkBuckets) * kQBins;
+__host__ __device__ inline int band_first_bucket(int s) {
+    return kBandFirstBucket + (s - kFirstChunkable) * kChunkBuckets;
+}
+__host__ __device__ inline int band_end_bucket(int s) { return band_first_bucket(s) + kChunkBuckets; }
+__host__ __device__ inline int band_bucket_of(int s, int nch) {
+    return band_first_bucket(s) + kChunkBuckets - (nch < kChunkBuckets ? nch : kChunkBuckets);
+}
 // work-queue counters: forward, reverse, reverse fallback (per class and
-// shape), then one per band config
-constexpr int kTaskCounters = 3 * kNumKernels + kBandConfigs;
+// shape), then one per band shape
+constexpr int kTaskCounters = 3 * kNumKernels + kBandShapes;
 
 // Tile of a pair: the shape (and chunk count) of least modelled cost, where a
 // pair costs (streamed steps incl. the G-1 wavefront fill) x chunks x G x
@@ -165,34 +182,43 @@ struct ClassArgs {
     int32_t band_min;             // forward maxima / banded reverse from this length (0 = off)
 };
 
-// Modelled cost of a reverse pass of query prefix lq, reference prefix lr and
-// score S over the whole rectangle (choose_shape's model) or a band; returns
-// the band config of least cost, or -1 when the rectangle is cheaper or no
-// band fits the end diagonal.  The reverse pass stops after the start: an
-// alignment that scores S spans about S / 2 streamed positions on these
-// workloads (homologous pairs gain 2 to 3 per column), so the model streams
+// Tile of a banded reverse pass of query prefix lq, reference prefix lr and
+// score S: the band shape of least modelled cost over its chunk windows
+// (choose_shape's per-step cost), if that is below the whole rectangle's cost
+// by a tenth (the share kept for pairs the certificate sends back); returns
+// false otherwise.  The reverse pass stops after the start: an alignment that
+// scores S spans about S / 2 streamed positions on these workloads
+// (homologous pairs gain 2 to 3 per column), so both models stream at most
 // a = min(lq, S / 2 + 1) positions.  The choice changes no result.
-__host__ __device__ inline int choose_band(int64_t lq, int64_t lr, int64_t S, int overhead) {
+__host__ __device__ inline bool choose_band(int64_t lq, int64_t lr, int64_t S, int overhead, int* shape,
+                                            int* nch) {
     int64_t a = S / 2 + 1;
     if (a > lq) a = lq;
-    int shape = 0, nch = 1;
-    choose_shape(a, lr, overhead, &shape, &nch);
-    int64_t best = (a + shape_G(shape) - 1) * nch * shape_G(shape) * (shape_R(shape) + overhead);
-    int pick = -1;
-    const int64_t delta = lr - lq;
-    const int64_t ad = delta < 0 ? -delta : delta;
-    const int64_t margin = band_margin(lq > lr ? lq : lr);
-    for (int c = 0; c < kBandConfigs; ++c) {
-        if (ad + 2 * margin > band_width(c)) continue;
-        const int64_t khi = (delta > 0 ? delta : 0) + (band_width(c) - ad) / 2;
-        const int64_t t = a + khi + (a + khi) / band_R(c) + band_G(c);
-        const int64_t cost = t * band_G(c) * (band_R(c) + overhead);
-        if (cost < best) {
+    int fs = 0, fn = 1;
+    choose_shape(a, lr, overhead, &fs, &fn);
+    const int64_t full = (a + shape_G(fs) - 1) * fn * shape_G(fs) * (shape_R(fs) + overhead);
+    int64_t W = 0, khi = 0;
+    band_geometry(lq, lr, &W, &khi);
+    int64_t best = -1;
+    for (int s = kFirstChunkable; s < kBandShapeEnd; ++s) {
+        const int64_t rows = (int64_t)shape_G(s) * shape_R(s);
+        const int64_t n = (lr + rows - 1) / rows;
+        int64_t steps = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            int64_t w0 = 0, w1 = 0;
+            band_window(c, rows, W, khi, lq, &w0, &w1);
+            if (w1 > a) w1 = a;
+            if (w1 <= w0) break;
+            steps += (w1 - w0 + shape_G(s) + 2) / 4 * 4;
+        }
+        const int64_t cost = steps * shape_G(s) * (shape_R(s) + overhead);
+        if (best < 0 || cost < best) {
             best = cost;
-            pick = c;
+            *shape = s;
+            *nch = (int)n;
         }
     }
-    return pick;
+    return best >= 0 && best * 10 < full * 9;
 }
 
 // Per-call device workspace (owned by the context).
@@ -208,11 +234,9 @@ struct Workspace {
     uint2* boundary;       // chunk-boundary rows, [slots][boundary_stride]
     int64_t boundary_stride;
     int64_t boundary_slots;
-    int32_t* fmax;         // [n_pairs][kFmaxSlots] forward maxima (null: no banded reverse)
-    uint8_t* band_prof;    // band kernels' profiles, [band_slots][band_prof_stride]
-    int64_t band_prof_stride;
-    int64_t band_rstride;  // bytes of one profile row
-    int64_t band_slots;
+    int32_t* fmax;         // forward maxima slices (null: no banded reverse pass)
+    int64_t fmax_capacity; // entries of fmax
+    int64_t* fmax_off;     // [n_pairs] slice of each pair, -1 = none
 };
 
 // Arguments of one DP launch.
@@ -228,27 +252,9 @@ struct DPArgs {
     int64_t boundary_stride;
     int64_t boundary_slots;
     int32_t first_bucket, end_bucket;
-    int32_t* fmax;              // forward: per-pair row-block maxima (null: none)
-    int32_t band_min;           // forward: pairs with both lengths >= band_min record them
-    ScoreArgs sc;
-};
-
-// Arguments of one band_kernel launch (config c).
-struct BandArgs {
-    SeqView q, r;
-    const int32_t* pairs;
-    const int32_t* order;
-    const uint32_t* scan;
-    uint32_t* task_ctr;
-    swgb_record* out;
-    int32_t* status;
-    const int32_t* fmax;
-    uint8_t* prof;             // profile scratch of the launch's warps
-    int64_t prof_stride;       // bytes per warp
-    int64_t rstride;           // bytes per profile row
-    int64_t slots;             // warps the scratch holds
+    int32_t* fmax;              // forward maxima slices (forward: written; banded reverse: read)
+    const int64_t* fmax_off;    // slice of each pair (-1 = none); null: no maxima
     unsigned long long* counters;
-    int32_t bucket;            // the config's bin bucket
     ScoreArgs sc;
 };
 
@@ -260,10 +266,12 @@ enum Counter {
     kCtrRevPairs = 4,
     kCtrBandPairs = 5,      // reverse passes run over a band
     kCtrBandCertified = 6,  // of which the certificate held
+    kCtrFmaxUsed = 7,       // forward-maxima entries handed out
 };
 
-// Marker left in q_start by the band kernel for a pair whose certificate did
-// not hold: the fallback keys pass sends it to the full reverse pass.
+// Marker left in q_start by the banded reverse pass for a pair whose
+// certificate did not hold: the fallback keys pass sends it to the full
+// reverse pass.
 constexpr int32_t kBandFallback = -2;
 
 // ---- launchers (swgb_kernels.cu) -------------------------------------------
@@ -275,32 +283,24 @@ cudaError_t launch_encode(const uint8_t* in, uint8_t* out, int64_t n, bool ascii
 cudaError_t launch_offsets(int64_t* off, int64_t n_seqs, int64_t base, int64_t max_len, int32_t* flags,
                            cudaStream_t st);
 // mode 0: forward keys; 1: reverse keys (band or full rectangle); 2: the
-// pairs the band kernels left for the full reverse pass
+// pairs the banded pass left for the full reverse pass
 enum KeysMode { kKeysForward = 0, kKeysReverse = 1, kKeysFallback = 2 };
 cudaError_t launch_keys(const SeqView& q, const SeqView& r, const int32_t* pairs, int64_t n_pairs,
                         swgb_record* out, int mode, const ClassArgs& ca,
                         const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scan(const Workspace& ws, cudaStream_t st);
 cudaError_t launch_scatter(int64_t n_pairs, const Workspace& ws, cudaStream_t st);
-// Launches the DP kernel of (class, shape); grid sized from occupancy.
+// Launches the DP kernel of (class, shape); grid sized from occupancy.  band:
+// the banded reverse pass of a chunkable shape on the packed path.
 cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
-                      cudaStream_t st);
+                      cudaStream_t st, bool band = false);
 // Blocks per SM the DP kernel of (class, shape, direction) can keep resident
 // with prof_rows profile rows.
-int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows);
+int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows, bool band = false);
 // Threads per block of every DP kernel.
 constexpr int kDPThreads = 64;
 size_t dp_smem_bytes(int cls, int shape, int prof_rows);
 cudaError_t dp_configure(int cls, int shape, bool reverse);
-// The banded reverse kernel of config c (swgb_band.cu).
-constexpr int kBandThreads = 64;
-cudaError_t launch_band(int cfg, const BandArgs& a, int grid_blocks, cudaStream_t st);
-int band_blocks_per_sm(int cfg);
-cudaError_t band_configure(int cfg);
-// Row length of the band scratch for sequences up to max_len residues, and
-// its bytes per warp with prof_rows profile rows (plus a query row) per pair.
-int64_t band_rstride(int64_t max_len);
-int64_t band_prof_bytes_per_warp(int64_t rstride, int prof_rows);
 cudaError_t launch_probe_addmax(unsigned long long* cycles, uint32_t* sink, int blocks,
                                 int iters, cudaStream_t st);
 constexpr int kProbeThreads = 256;

@@ -192,16 +192,37 @@ __device__ int64_t score_bound(const uint8_t* __restrict__ q, int64_t lq, const 
     return bq < br ? bq : br;
 }
 
+// Hands each lane of a warp `need` consecutive entries of a shared pool whose
+// cursor is *ctr: one atomic per warp.  Every lane of the warp calls it.
+__device__ int64_t warp_alloc(unsigned long long* ctr, int64_t need) {
+    const int lane = threadIdx.x & 31;
+    int64_t incl = need;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const int64_t total = __shfl_sync(kFull, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(ctr, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    return (int64_t)base + incl - need;
+}
+
 __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pairs,
                             int64_t n_pairs, swgb_record* out, int mode, ClassArgs ca,
                             Workspace ws) {
     unsigned long long cells = 0, n16 = 0, n32 = 0, nband = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs; p += stride) {
+    // every lane of a warp runs the same iterations (warp_alloc)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_pairs; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const bool valid = p < n_pairs;
         int bin = -1;
         int64_t lq = 0, lr = 0;
-        int cls = 0, band = -1;
-        if (mode == kKeysForward) {
+        int cls = 0, band_shape = -1, band_nch = 0;
+        int64_t fmax_need = 0, fmax_rows = 0;
+        if (valid && mode == kKeysForward) {
             const int32_t qi = pairs[2 * p], ri = pairs[2 * p + 1];
             if (qi < 0 || qi >= q.n || ri < 0 || ri >= r.n) {
                 set_status(ws.status, SWGB_ERANGE);
@@ -217,20 +238,16 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 } else if ((int64_t)ca.max_score * (lq < lr ? lq : lr) > 32767) {
                     cls = score_bound(q.res + q.off[qi], lq, r.res + r.off[ri], lr, ca) > 32767;
                 }
-                // a pair long enough for a banded reverse pass: the block height of
-                // its forward maxima (from its forward tile) and cleared blocks,
-                // which the packed forward kernels fill; absent on the 32-bit path
-                if (ws.fmax && ca.band_min > 0 && lq >= ca.band_min && lr >= ca.band_min) {
+                // a pair long enough for a banded reverse pass records the
+                // maxima of its forward lanes (packed path only)
+                if (ws.fmax_off && ca.band_min > 0 && cls == 0 && lq >= ca.band_min && lr >= ca.band_min) {
                     int shape = 0, nch = 1;
                     choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
-                    const int sb = cls == 0 ? fmax_slot_rows(lr, shape_R(shape)) : kFmaxNone;
-                    int4* f = reinterpret_cast<int4*>(ws.fmax + p * kFmaxSlots);
-#pragma unroll
-                    for (int k = 0; k < kFmaxSlots / 4; ++k)
-                        f[k] = k > 0 ? make_int4(0, 0, 0, 0) : make_int4(sb, 0, 0, 0);
+                    fmax_rows = shape_R(shape);
+                    fmax_need = 1 + (lr + fmax_rows - 1) / fmax_rows;
                 }
             }
-        } else {
+        } else if (valid) {
             const swgb_record rec = out[p];
             const bool take = mode == kKeysReverse ? rec.score > 0 : (rec.score > 0 && rec.q_start == kBandFallback);
             if (take) {
@@ -254,27 +271,43 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                     lr = (int64_t)rec.r_end + 1;
                     // every cell of the reversed prefixes scores at most S
                     cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
-                    if (mode == kKeysReverse && cls == 0 && ws.fmax && ca.band_min > 0 &&
-                        nq >= ca.band_min && nr >= ca.band_min && ws.fmax[p * kFmaxSlots] != kFmaxNone)
-                        band = choose_band(lq, lr, rec.score, ca.tile_overhead);
+                    // a banded pass needs the pair's forward maxima
+                    if (mode == kKeysReverse && cls == 0 && ws.fmax_off && ca.band_min > 0 &&
+                        nq >= ca.band_min && nr >= ca.band_min && ws.fmax_off[p] >= 0 &&
+                        !choose_band(lq, lr, rec.score, ca.tile_overhead, &band_shape, &band_nch))
+                        band_shape = -1;
                 } else {
                     set_status(ws.status, SWGB_EINTERNAL);
                     zero_record(&out[p]);
                 }
             }
         }
+        if (mode == kKeysForward && ws.fmax_off) {
+            // the slice of the forward maxima (all lanes: warp_alloc)
+            const int64_t off = warp_alloc(&ws.counters[kCtrFmaxUsed], fmax_need);
+            if (valid) {
+                const bool got = fmax_need > 0 && off + fmax_need <= ws.fmax_capacity;
+                ws.fmax_off[p] = got ? off : -1;
+                if (got) ws.fmax[off] = (int32_t)fmax_rows;
+            }
+        }
         if (lq > 0) {
-            int64_t qb = lq >> kQBinShift;
-            if (qb > kQBins - 1) qb = kQBins - 1;
             int bucket;
-            if (band >= 0) {
-                bucket = kBandFirstBucket + band;
+            int64_t qb;
+            if (band_shape >= 0) {
+                // band pairs sorted by the drift of the end diagonal, so that
+                // the two pairs of a warp share most of their windows
+                bucket = band_bucket_of(band_shape, band_nch);
+                qb = (lr - lq + 4 * (kQBins / 2)) / 4;
                 ++nband;
             } else {
                 int shape = 0, nch = 1;
                 choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
                 bucket = bucket_of(cls, shape, nch);
+                qb = lq >> kQBinShift;
             }
+            if (qb < 0) qb = 0;
+            if (qb > kQBins - 1) qb = kQBins - 1;
             bin = bucket * kQBins + (kQBins - 1 - (int)qb);
             atomicAdd(&ws.hist[bin], 1u);
             if (mode != kKeysFallback) {
@@ -282,7 +315,7 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 if (cls == 0) ++n16; else ++n32;
             }
         }
-        ws.bin_of[p] = bin;
+        if (valid) ws.bin_of[p] = bin;
     }
     // block reduction of the counters
     for (int off = 16; off > 0; off >>= 1) {
@@ -417,6 +450,32 @@ __host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16,
 // REV = true : local DP over the reversed prefixes q[q_end..0] x r[r_end..0]
 //              of each scored pair -> start cell.  The score S is known, so the
 //              pass stops once the wavefront is past the first step holding S.
+// FMAX (forward): also records the maxima of each lane's rows for the banded
+//              reverse pass.
+// BAND (reverse, packed, 32-lane tiles): the banded reverse pass.  Chunk c of
+//              the reversed reference streams only its window [w0, wend) (the
+//              union of the two halves' band windows); lane gl computes the
+//              positions [w0 - gl, w0 - gl + steps) of its rows, so the
+//              computed region D is a staircase of those ranges.  The DP is
+//              anchored: H = 0 only before the origin, the floor kFloorH
+//              outside D and below every cell.  Certificate: every cell x of
+//              D with a successor y outside D (right, down or diagonal, inside
+//              the matrix) is an exit.  An alignment from the origin that
+//              leaves D leaves it first through an exit x: its part up to x
+//              scores at most H_D(x), and the rest, read in the forward
+//              direction, is a local alignment ending at y's cell, which scores
+//              at most the forward H there plus o (had it opened with a gap
+//              extension) -- at most the forward maximum of y's rows plus o.
+//              A cell of value S reached that way lies at a position no
+//              earlier than x's, so if every exit at a position <= a* (the
+//              first position holding S in D) has H_D(x) + fmax(y's rows) + o
+//              < S, the first cell of value S in D is the first in the whole
+//              rectangle and the start is exact; otherwise the pair is marked
+//              for the full reverse pass.  Exits are tracked per lane with
+//              bounds over a few rows (conservative): the last two positions
+//              of each lane's range (its right edge) and, for the bottom row
+//              of a chunk, the positions the next chunk's first row does not
+//              cover.
 //
 // Position of the maximum.  Every lane keeps lb1 = max(its running maximum,
 // T - 1), T a lower bound of the pair's final score (the largest lb1 of the
@@ -431,9 +490,10 @@ __host__ __device__ constexpr int dp_prof_bytes_per_warp(int G, int R, bool P16,
 // the register budget: 65536 / (64 threads x blocks) registers per thread.
 __host__ __device__ constexpr int dp_min_blocks(int R) { return R <= 8 ? 8 : R <= 12 ? 6 : 5; }
 
-template <int G, int R, bool P16, bool REV, bool FMAX>
+template <int G, int R, bool P16, bool REV, bool FMAX, bool BAND>
 __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const DPArgs a) {
     static_assert(!FMAX || (P16 && !REV), "forward maxima are recorded by packed forward kernels");
+    static_assert(!BAND || (P16 && REV && G == 32), "the banded reverse pass runs on packed 32-lane tiles");
     using L = Lane<P16>;
     constexpr int PACK = L::kPack;
     constexpr int GROUPS = 32 / G;
@@ -479,6 +539,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
     const int zero_h = P16 ? kBias - oe : -oe;
     const uint32_t HZ = L::splat(zero_h);
     const uint32_t BV = L::splat(kBias);                  // H = 0 on the packed path
+    // the banded pass's "minus infinity" / floor: HF the row state (and E, F)
+    // at H = kFloorH, BF the floor of U's maximum; the local DP uses H = 0
+    const uint32_t HF = BAND ? L::splat(zero_h + kFloorH) : HZ;
+    const uint32_t BF = BAND ? L::splat(kBias + kFloorH) : BV;
     const uint32_t one = (uint32_t)a.sc.one;              // 1 at run time: adds issue as multiply-adds
     const uint32_t neg_one = 0u - one;
     const uint32_t ONE = L::splat(1);
@@ -567,9 +631,80 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
         for (int h = 0; h < PACK; ++h) fi[h] = INT_MAX;
         int ls_c = ls;   // streamed positions the chunk still needs
 
+        // banded pass, per half: the band (width bW, offset bK), the slice of
+        // the pair's forward maxima (foff, rows per entry frf) and vmin, the
+        // smallest position of an exit whose bound reaches S (INT_MIN: no
+        // maxima, never certified)
+        int bW[PACK], bK[PACK], frf[PACK], vmin[PACK];
+        int64_t foff[PACK];
+        if constexpr (BAND) {
+#pragma unroll
+            for (int h = 0; h < PACK; ++h) {
+                int64_t w = 0, k = 0;
+                if (pid[h] >= 0) band_geometry(lq[h], lr[h], &w, &k);
+                bW[h] = (int)w;
+                bK[h] = (int)k;
+                foff[h] = pid[h] >= 0 ? a.fmax_off[pid[h]] : -1;
+                frf[h] = foff[h] >= 0 ? a.fmax[foff[h]] : 0;
+                vmin[h] = (foff[h] >= 0 && frf[h] > 0) ? INT_MAX : INT_MIN;
+            }
+        }
+        // largest forward H over the reversed rows [j0, j1] of half h, i.e.
+        // reference rows lr - 1 - j1 .. lr - 1 - j0 (kFloorH if none)
+        auto fmax_rows = [&](int h, int j0, int j1) -> int {
+            int lo = lr[h] - 1 - j1, hi = lr[h] - 1 - j0, m = kFloorH;
+            if (lo < 0) lo = 0;
+            for (int k = lo / frf[h]; hi >= lo && k <= hi / frf[h]; ++k) m = max(m, a.fmax[foff[h] + 1 + k]);
+            return m;
+        };
+        // exits through the bottom row of the chunk before row jrow at the
+        // positions [p0, p1), read from the chunk-boundary row (every lane)
+        auto stair_exits = [&](int jrow, int p0, int p1) {
+            int fn[PACK];
+#pragma unroll
+            for (int h = 0; h < PACK; ++h)
+                fn[h] = (vmin[h] != INT_MIN && jrow < lr[h]) ? fmax_rows(h, jrow, jrow) + a.sc.go : INT_MIN;
+            for (int p = p0 + lane; p < p1; p += 32) {
+                const uint32_t y = bnd[p].y;
+#pragma unroll
+                for (int h = 0; h < PACK; ++h)
+                    if (fn[h] != INT_MIN && p < lq[h] && L::get(y, h) - zero_h + fn[h] >= target[h])
+                        vmin[h] = min(vmin[h], p);
+            }
+        };
+        const int ls_all = ls_w;      // positions a chunk-boundary row may hold
+        int prev_lo = 0, prev_hi = 0; // positions the last chunk's bottom row holds
+
         for (int c = 0; c < nch; ++c) {
             const int jc = c * ROWS;          // first held row of the chunk
             const int jl = jc + gl * R;       // first held row of this lane
+            // streamed window [w0, wend) of the chunk: the positions the
+            // chunks before left to scan, or in the banded pass the union of
+            // the halves' band windows within them (empty: wend <= w0)
+            int w0 = 0, wend = ls_w;
+            if constexpr (BAND) {
+                int64_t lo = INT_MAX, hi = 0;
+#pragma unroll
+                for (int h = 0; h < PACK; ++h) {
+                    if (pid[h] >= 0 && jc < lr[h]) {
+                        int64_t x0 = 0, x1 = 0;
+                        band_window(c, ROWS, bW[h], bK[h], lq[h], &x0, &x1);
+                        lo = min(lo, x0);
+                        hi = max(hi, x1);
+                    }
+                }
+                if (hi > ls_w) hi = ls_w;
+                w0 = (int)(lo < INT_MAX / 2 ? lo : INT_MAX / 2);
+                wend = (int)hi;
+                // the last chunk's bottom row at the positions left of this
+                // chunk's first row (all of them if this chunk scans nothing);
+                // this chunk's last lane overwrites them
+                if (c > 0) stair_exits(jc, prev_lo, wend > w0 ? min(prev_hi, w0) : prev_hi);
+                if (wend <= w0) {
+                    prev_lo = prev_hi = 0;
+                    continue;
+                }
+            }
             // ---- profile of the chunk: prof[h][x][row] = s(x, held row) + o + e
             __syncwarp();
 #pragma unroll
@@ -616,10 +751,17 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             uint32_t HopA[R], HopB[R], F[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                HopA[r] = HZ;   // H = 0 before the first query position
-                F[r] = HZ;
+                HopA[r] = HF;   // H = 0 before the first query position (banded: the floor)
+                F[r] = HF;
             }
+            // the diagonal input of the lane's first row at its first position:
+            // the banded pass is anchored (H = 0 only at the origin's corner; in
+            // later chunks lane 0 takes the row above from the last chunk)
             uint32_t hin_prev = HZ;
+            if constexpr (BAND) {
+                hin_prev = (c == 0 && gl == 0) ? HZ : HF;
+                if (c > 0 && gl == 0 && w0 - 1 >= prev_lo && w0 - 1 < prev_hi) hin_prev = bnd[w0 - 1].y;
+            }
             // per half max(this lane's maximum in this chunk, T - 1)
             uint32_t lb1 = L::addmax(T, MONE, HZ);
             // forward maxima variant: this lane's own running maximum over its
@@ -640,7 +782,13 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 
             const bool read_bnd = (c > 0) && (gl == 0);
             const bool write_bnd = (c + 1 < nch) && (gl == G - 1);
-            const int steps = ls_w + G - 1;
+            const int steps = (wend - w0) + G - 1;
+            // lane 0 reads the row above at the positions [w0, rd_hi) the last
+            // chunk's bottom row holds; the last lane writes its bottom row
+            // at the positions [0, wr_hi)
+            const int rd_hi = BAND ? prev_hi : ls_c;
+            const int wr_hi = BAND ? ls_all : ls_c;
+            int t_end = 0;   // steps the wavefront ran
             int stop_w = INT_MAX;   // reverse pass: warp-uniform last useful step
 
             // software pipeline: profile words of the next step and the query
@@ -656,10 +804,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             int xn[PACK], xb[PACK], xc[PACK];
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                pwA[h] = load_prof<LS>(plane + h * PROF + code_at(h, -gl) * RS);
-                xn[h] = code_at(h, 1 - gl);
-                xb[h] = code_at(h, 2 + gl);            // positions for steps 0 .. kBatch - 1
-                xc[h] = code_at(h, 2 + kBatch + gl);   // steps kBatch .. 2 kBatch - 1
+                pwA[h] = load_prof<LS>(plane + h * PROF + code_at(h, w0 - gl) * RS);
+                xn[h] = code_at(h, w0 + 1 - gl);
+                xb[h] = code_at(h, w0 + 2 + gl);            // positions for steps 0 .. kBatch - 1
+                xc[h] = code_at(h, w0 + 2 + kBatch + gl);   // steps kBatch .. 2 kBatch - 1
             }
             // per half 1 where the previous step had an event whose registers
             // are not kept yet, else 0; endp: per half 1 where a run of events
@@ -668,20 +816,20 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // mp: the last step's maximum (with lb1, before a bound refresh
             // raised it), i.e. the value of that step's event if it had one
             uint32_t pend = 0, endp = 0, lbp = lb1, mp = lb1;
-            uint32_t ein = HZ, hin = HZ;   // from lane gl-1, previous step
+            uint32_t ein = HF, hin = HF;   // from lane gl-1, previous step
             // multiplier and addend that give lane 0 of a group HZ for its
             // inputs from above (one-tile wavefronts; run-time values, so the
             // product is issued as a multiply-add, not a select)
             const uint32_t not0 = gl == 0 ? 0u : one;
-            const uint32_t hz0 = gl == 0 ? HZ : 0u;
+            const uint32_t hz0 = gl == 0 ? HF : 0u;
 
             // The step loop, compiled twice for the 32-lane tiles: with the
             // chunk-boundary exchange (BND, references longer than one tile) and
             // without it (one tile, and every smaller shape).
             auto wavefront = [&](auto bnd_tag) {
             constexpr bool BND = decltype(bnd_tag)::value;
-            uint2 bcur = make_uint2(HZ, HZ);
-            if (BND && read_bnd && ls_c > 0) bcur = bnd[0];
+            uint2 bcur = make_uint2(HF, HF);
+            if (BND && read_bnd && rd_hi > w0) bcur = bnd[w0];
 
             // keeps the registers of an event of value v at streamed position
             // ii (Hs holds that step's values) as half h's candidate
@@ -715,7 +863,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // bound periods (multiples of four) end.
             auto step = [&](int t, const uint32_t (&Hp)[R], uint32_t (&Hn)[R],
                             const ProfWords<LS> (&pw)[PACK], ProfWords<LS> (&pwn)[PACK], bool last) {
-                const int i = t - gl;
+                const int i = w0 + t - gl;
 #pragma unroll
                 for (int h = 0; h < PACK; ++h) {
                     pwn[h] = load_prof<LS>(plane + h * PROF + xn[h] * RS);
@@ -728,11 +876,11 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                         // past the rows the previous chunk handed over, lane 0 sees
                         // "minus infinity": cells there score alignments confined
                         // to this chunk, never above the pair's score
-                        const bool take = read_bnd && i < ls_c;
-                        ein = take ? bcur.x : HZ;
-                        hin = take ? bcur.y : HZ;
+                        const bool take = read_bnd && i < rd_hi;
+                        ein = take ? bcur.x : HF;
+                        hin = take ? bcur.y : HF;
                     }
-                    if (read_bnd && i + 1 < ls_c) bcur = bnd[i + 1];
+                    if (read_bnd && i + 1 < rd_hi) bcur = bnd[i + 1];
                 }
                 // A run of events that ended at the previous step had its last
                 // event two steps back, whose row state is still in Hn until
@@ -750,7 +898,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     const uint32_t hd = r == 0 ? hin_prev : Hp[r - 1];
                     if constexpr (P16) {
                         const uint32_t d = s * one + hd;                 // H_diag + s (biased)
-                        Hn[r] = L::max3(d, F[r], BV) * one + C_UOP;      // max(., F, 0) - (o + e)
+                        Hn[r] = L::max3(d, F[r], BF) * one + C_UOP;      // max(., F, 0) - (o + e)
                     } else {
                         Hn[r] = L::addmax(L::addmax(hd, s, F[r]), NOE, NOE);
                     }
@@ -768,7 +916,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 for (int r = 0; r < R; ++r) F[r] = L::addmax(F[r], NE, Hn[r]);
                 hin_prev = hin;
                 if constexpr (BND) {
-                    if (write_bnd && i >= 0 && i < ls_c) bnd[i] = make_uint2(e, Hn[R - 1]);
+                    if (write_bnd && i >= 0 && i < wr_hi) bnd[i] = make_uint2(e, Hn[R - 1]);
                 }
                 const uint32_t e_next = __shfl_up_sync(kFull, e, 1, G);
                 const uint32_t h_next = __shfl_up_sync(kFull, Hn[R - 1], 1, G);
@@ -802,7 +950,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
                             xb[h] = xc[h];
-                            xc[h] = code_at(h, t + 3 + kBatch + gl);
+                            xc[h] = code_at(h, w0 + t + 3 + kBatch + gl);
                         }
                     }
                 }
@@ -811,7 +959,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 #pragma unroll
                         for (int h = 0; h < PACK; ++h) {
                             xb[h] = xc[h];
-                            xc[h] = code_at(h, t + 3 + kBatch + gl);
+                            xc[h] = code_at(h, w0 + t + 3 + kBatch + gl);
                         }
                     }
                     if constexpr (!REV) {   // the reverse pass's bound is S from the start
@@ -829,7 +977,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                             const int f = pid[h] >= 0 ? gm : 0;
                             stop = (stop == INT_MAX || f == INT_MAX) ? INT_MAX : max(stop, f);
                         }
-                        if (stop != INT_MAX) stop += G - 1;
+                        if (stop != INT_MAX) stop += G - 1 - w0;   // in steps
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1)
                             stop = max(stop, __shfl_xor_sync(kFull, stop, off));
@@ -866,9 +1014,10 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             // the B set), then a run still open at the last step (A set)
 #pragma unroll
             for (int h = 0; h < PACK; ++h) {
-                if (L::get(endp, h) != 0) keep(h, t - 2 - gl, HopB, L::get(lbp, h));
-                if (L::get(pend, h) != 0) keep(h, t - 1 - gl, HopA, L::get(mp, h));
+                if (L::get(endp, h) != 0) keep(h, w0 + t - 2 - gl, HopB, L::get(lbp, h));
+                if (L::get(pend, h) != 0) keep(h, w0 + t - 1 - gl, HopA, L::get(mp, h));
             }
+            t_end = t;
             };
             if constexpr (G == 32) {
                 if (nch > 1) wavefront(std::true_type{});
@@ -878,20 +1027,39 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             }
 
             // ---- forward maxima of the lane's rows for the banded reverse
-            // pass: block k of a pair holds the largest H of reference rows
-            // [k SB, (k + 1) SB); SB is a multiple of R, so the lane's rows lie
-            // in one block
+            // pass: entry jl / R of the pair's slice (its forward tile is this
+            // one, so every lane writes its own entry once).  Pad cells the
+            // lane computed score below real cells feeding them, so the value
+            // bounds the rows' H from above.
             if constexpr (FMAX) {
-                if (a.fmax) {
+                if (a.fmax_off) {
 #pragma unroll
                     for (int h = 0; h < PACK; ++h) {
-                        if (pid[h] >= 0 && lq[h] >= a.band_min && lr[h] >= a.band_min && jl < lr[h]) {
-                            const int sb = fmax_slot_rows(lr[h], R);
-                            const int v = L::get(pmax, h) - zero_h;   // H
-                            atomicMax(a.fmax + (int64_t)pid[h] * kFmaxSlots + 1 + jl / sb, v);
+                        if (pid[h] >= 0 && jl < lr[h]) {
+                            const int64_t off = a.fmax_off[pid[h]];
+                            if (off >= 0) a.fmax[off + 1 + jl / R] = L::get(pmax, h) - zero_h;
                         }
                     }
                 }
+            }
+
+            // ---- exits of the banded pass at the end of the chunk
+            if constexpr (BAND) {
+                // right edge: the lane's rows at its last position e, and its
+                // bottom row at e - 1 (the lane below stops at e - 1)
+                const int e = w0 + t_end - 1 - gl;
+                const uint32_t m = tree_max<P16, R>(HopA, HopB[R - 1]);
+#pragma unroll
+                for (int h = 0; h < PACK; ++h)
+                    if (vmin[h] != INT_MIN && jl < lr[h] && e < lq[h] &&
+                        L::get(m, h) - zero_h + fmax_rows(h, jl, jl + R) + a.sc.go >= target[h])
+                        vmin[h] = min(vmin[h], e - 1);
+                // the last chunk's bottom row from the position where this
+                // chunk's first row stops on: this chunk's last lane wrote only
+                // positions before it
+                if (c > 0) stair_exits(jc, max(prev_lo, w0 + t_end - 1), prev_hi);
+                prev_lo = max(0, w0 - (G - 1));
+                prev_hi = min(ls_all, w0 + t_end - (G - 1));
             }
 
             // ---- the lane's candidate of this chunk: the recorded step and the
@@ -930,9 +1098,11 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
         }
 
         // ---- reduce over the lanes of the group and write the records
+        int ncert = 0;
 #pragma unroll
         for (int h = 0; h < PACK; ++h) {
             int v = bv[h], ii = bi[h], jj = bj[h];
+            const int vm = BAND ? group_min<G>(vmin[h]) : 0;
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) {
                 const int ov = __shfl_xor_sync(kFull, v, off, G);
@@ -953,6 +1123,16 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                     } else {
                         *rec = swgb_record{0, -1, -1, -1, -1};
                     }
+                } else if (BAND) {
+                    // certified: S found in the band before every exit whose
+                    // bound reaches S; otherwise left for the full pass
+                    if (S == target[h] && ii != INT_MAX && vm > ii) {
+                        rec->q_start = lq[h] - 1 - ii;
+                        rec->r_start = lr[h] - 1 - jj;
+                        ++ncert;
+                    } else {
+                        rec->q_start = kBandFallback;
+                    }
                 } else {
                     if (S != target[h] || ii == INT_MAX) {
                         set_status(a.status, SWGB_EINTERNAL);
@@ -963,6 +1143,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
                 }
             }
         }
+        if (BAND && ncert > 0) atomicAdd(&a.counters[kCtrBandCertified], (unsigned long long)ncert);
     }
 }
 
@@ -971,9 +1152,9 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
 // ---------------------------------------------------------------------------
 using DPFn = void (*)(const DPArgs);
 
-template <int S, bool P16, bool REV, bool FMAX>
+template <int S, bool P16, bool REV, bool FMAX, bool BAND = false>
 constexpr DPFn dp_fn() {
-    return &dp_kernel<shape_G(S), shape_R(S), P16, REV, FMAX>;
+    return &dp_kernel<shape_G(S), shape_R(S), P16, REV, FMAX, BAND>;
 }
 
 template <bool P16, bool REV, bool FMAX>
@@ -1003,11 +1184,24 @@ DPFn dp_pick(int shape) {
     }
 }
 
+// the banded reverse pass: packed 32-lane tiles of the band shapes only
+static DPFn dp_pick_band(int shape) {
+    switch (shape) {
+        case 13: return dp_fn<13, true, true, false, true>();
+        case 14: return dp_fn<14, true, true, false, true>();
+        case 15: return dp_fn<15, true, true, false, true>();
+        case 16: return dp_fn<16, true, true, false, true>();
+        default: return dp_fn<17, true, true, false, true>();
+    }
+}
+
 // fmax: the packed forward variant that records forward maxima for the
-// banded reverse pass (ignored otherwise)
-static DPFn dp_lookup(int cls, int shape, bool reverse, bool fmax = false) {
+// banded reverse pass; band: the banded reverse pass (both packed only)
+static DPFn dp_lookup(int cls, int shape, bool reverse, bool fmax = false, bool band = false) {
     if (cls == 0) {
-        if (reverse) return dp_pick<true, true, false>(shape);
+        if (reverse)
+            return band && shape >= kFirstChunkable && shape < kBandShapeEnd ? dp_pick_band(shape)
+                                                                             : dp_pick<true, true, false>(shape);
         return fmax ? dp_pick<true, false, true>(shape) : dp_pick<true, false, false>(shape);
     }
     return reverse ? dp_pick<false, true, false>(shape) : dp_pick<false, false, false>(shape);
@@ -1025,20 +1219,25 @@ cudaError_t dp_configure(int cls, int shape, bool reverse) {
     if (e == cudaSuccess && cls == 0 && !reverse)
         e = cudaFuncSetAttribute(dp_lookup(cls, shape, false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)dp_smem_bytes(cls, shape, kProfileRows));
+    if (e == cudaSuccess && cls == 0 && reverse && shape >= kFirstChunkable && shape < kBandShapeEnd)
+        e = cudaFuncSetAttribute(dp_lookup(cls, shape, true, false, true),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dp_smem_bytes(cls, shape, kProfileRows));
     return e;
 }
 
-int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows) {
+int dp_blocks_per_sm(int cls, int shape, bool reverse, int prof_rows, bool band) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dp_lookup(cls, shape, reverse), kDPThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dp_lookup(cls, shape, reverse, false, band),
+                                                      kDPThreads,
                                                       dp_smem_bytes(cls, shape, prof_rows)) != cudaSuccess)
         return 0;
     return n;
 }
 
 cudaError_t launch_dp(int cls, int shape, bool reverse, const DPArgs& a, int grid_blocks,
-                      cudaStream_t st) {
-    DPFn fn = dp_lookup(cls, shape, reverse, a.fmax != nullptr);
+                      cudaStream_t st, bool band) {
+    DPFn fn = dp_lookup(cls, shape, reverse, !reverse && a.fmax != nullptr, band);
     fn<<<grid_blocks, kDPThreads, dp_smem_bytes(cls, shape, a.sc.prof_rows), st>>>(a);
     return cudaGetLastError();
 }

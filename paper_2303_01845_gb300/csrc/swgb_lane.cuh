@@ -1,7 +1,7 @@
-// swgb_lane.cuh -- device helpers shared by the DP kernels (swgb_kernels.cu)
-// and the banded reverse kernel (swgb_band.cu): packed 16x2 / 32-bit lane
-// arithmetic, profile word loads, group reductions and the transposed score
-// table the profiles are built from.  Not part of the public ABI.
+// swgb_lane.cuh -- device helpers of the DP kernels (swgb_kernels.cu): packed
+// 16x2 / 32-bit lane arithmetic, profile word loads, group reductions and the
+// transposed score table the profiles are built from.  Not part of the public
+// ABI.
 #pragma once
 
 #include <climits>

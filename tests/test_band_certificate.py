@@ -1,13 +1,18 @@
 """The exactness certificate of the banded reverse pass, checked on the CPU.
 
 A plain numpy model of the band's geometry and bound, written from their
-definition (it shares nothing with the CUDA kernel): the anchored reverse DP
-restricted to the staircase band of a ring of G lanes x R rows, the band's
-exits at or before the first position a0 holding S in the band, and the
-bound band value + forward maximum of the successor's rows + gap open < S at
-each of them.  The claim pinned here: whenever the bound holds, the band's
-row-major-first cell of value S gives exactly the oracle's start; a band that a planted optimal alignment must leave never certifies;
-and a band covering the whole matrix always certifies.
+definition (it shares nothing with the CUDA kernel): the anchored DP over the
+reversed prefixes restricted to the computed region D -- on a tile of G lanes
+x R rows, chunk c of the reversed reference streams the window
+[c G R - khi, (c + 1) G R + W - khi), and lane g of the chunk computes its rows
+at the positions [w0 - g, w0 - g + steps), steps = the window plus the G - 1
+steps of wavefront fill, rounded up to four -- the exits of D (cells of D with
+a successor inside the matrix but outside D) at positions up to a0, the first
+position holding S in D, and the bound region value + forward maximum of the
+successor's rows + gap open < S at each of them.  The claims pinned here:
+whenever the bound holds, the region's first cell of value S gives exactly
+the oracle's start; a region that a planted optimal alignment must leave
+never certifies; and a region covering the whole matrix always certifies.
 """
 import numpy as np
 import pytest
@@ -35,17 +40,32 @@ def forward_local(q, r, m, go, ge):
     return H
 
 
-def band_mask(la, lb, G, R, khi):
-    """Cells (a, b) of the band: virtual lane V = b // R holds positions
-    [V R - khi, V R - khi + (G - 1)(R + 1))."""
-    a = np.arange(la)[:, None]
-    V = np.arange(lb)[None, :] // R
-    return (a >= V * R - khi) & (a < V * R - khi + (G - 1) * (R + 1))
+def band_geometry(la, lb, margin):
+    d = lb - la
+    return abs(d) + 2 * margin, max(d, 0) + margin
 
 
-def anchored_in_band(qr, rr, m, go, ge, inD):
+def region(la, lb, G, R, W, khi):
+    """Mask [a, b] of the computed region D (a = position, b = row)."""
+    rows = G * R
+    D = np.zeros((la, lb), bool)
+    for c in range(-(-lb // rows)):
+        w0 = max(0, c * rows - khi)
+        w1 = min(la, (c + 1) * rows + W - khi)
+        if w1 <= w0:
+            continue
+        steps = 4 * (-(-(w1 - w0 + G - 1) // 4))
+        for g in range(G):
+            b0 = c * rows + g * R
+            if b0 >= lb:
+                break
+            D[max(0, w0 - g):max(0, min(la, w0 - g + steps)), b0:min(b0 + R, lb)] = True
+    return D
+
+
+def anchored_in_region(qr, rr, m, go, ge, inD):
     """Anchored DP over the reversed prefixes, H = 0 only before the origin,
-    cells outside the band at the floor."""
+    cells outside D at the floor."""
     la, lb = len(qr), len(rr)
     A = np.full((la, lb), FLOOR, np.int64)
     Hp = np.full(lb + 1, FLOOR, np.int64)
@@ -64,41 +84,34 @@ def anchored_in_band(qr, rr, m, go, ge, inD):
     return A
 
 
-def banded_start(q, r, rec, m, go, ge, G, R, slot_rows):
-    """(certified, start or None) of the band model for the record rec."""
+def banded_start(q, r, rec, m, go, ge, G, R, margin, lane_rows):
+    """(certified, start or None) of the band model for the record rec;
+    lane_rows = rows per entry of the forward maxima."""
     S, qs, qe, rs, re_ = rec
     qr, rr = q[:qe + 1][::-1], r[:re_ + 1][::-1]
     la, lb = len(qr), len(rr)
-    W = G * (R + 1) - 2 * R
-    d = lb - la
-    khi = max(0, d) + max(W - abs(d), 0) // 2
-    inD = band_mask(la, lb, G, R, khi)
-    A = anchored_in_band(qr, rr, m, go, ge, inD)
+    W, khi = band_geometry(la, lb, margin)
+    D = region(la, lb, G, R, W, khi)
+    A = anchored_in_region(qr, rr, m, go, ge, D)
     hits = np.argwhere(A == S)
     if len(hits) == 0:
         return False, None
     a0, b0 = hits[0]
     Hf = forward_local(q, r, m, go, ge)
-    slot = np.array([Hf[:, j:j + slot_rows].max() for j in range(0, len(r), slot_rows)])
-
-    def fmax(j_lo, j_hi):
-        j_lo, j_hi = max(j_lo, 0), min(j_hi, re_)
-        return slot[j_lo // slot_rows: j_hi // slot_rows + 1].max() if j_hi >= j_lo else NEG
-
-    # exits at or before the first S position a0 whose bound reaches S: an
-    # alignment through an exit starts at or after the exit's position
-    WV = (G - 1) * (R + 1)
-    for V in range(-(-lb // R)):
-        b_lo, b_hi = V * R, min(V * R + R, lb)
-        a_last = V * R - khi + WV - 1
-        if 0 <= a_last < la - 1 and a_last <= a0:     # right edge, successor inside the matrix
-            if A[a_last, b_lo:b_hi].max() + fmax(re_ - b_hi, re_ - b_lo) + go >= S:
-                return False, None
-        if b_hi < lb:                                 # staircase: bottom row before lane V + 1 starts
-            a_s, a_e = max(V * R - khi, 0), min(V * R - khi + R, la)
-            a_e = min(a_e, a0 + 1)
-            if a_e > a_s and A[a_s:a_e, b_hi - 1].max() + fmax(re_ - b_hi, re_ - b_hi + 1) + go >= S:
-                return False, None
+    blk = np.array([Hf[:, j:j + lane_rows].max() for j in range(0, len(r), lane_rows)])
+    fm = blk[(re_ - np.arange(lb)) // lane_rows]          # reversed row -> its block
+    fm_next = np.concatenate([fm[1:], [NEG]])
+    Dp = np.zeros((la + 1, lb + 1), bool)
+    Dp[:la, :lb] = D
+    inm = np.zeros((la + 1, lb + 1), bool)
+    inm[:la, :lb] = True
+    right = D & inm[1:, :lb] & ~Dp[1:, :lb]
+    down_or_diag = D & ((inm[:la, 1:] & ~Dp[:la, 1:]) | (inm[1:, 1:] & ~Dp[1:, 1:]))
+    early = (np.arange(la) <= a0)[:, None]
+    if (right & early & (A + fm[None, :] + go >= S)).any():
+        return False, None
+    if (down_or_diag & early & (A + fm_next[None, :] + go >= S)).any():
+        return False, None
     return True, (qe - a0, re_ - b0)
 
 
@@ -115,8 +128,8 @@ def homologous(rng, L, mut=0.3, indel=0.04):
     return q.astype(np.uint8), np.asarray(r, np.uint8)
 
 
-@pytest.mark.parametrize("G,R,slot_rows", [(16, 4, 4), (16, 6, 8), (32, 3, 2)])
-def test_a_certified_band_gives_the_oracle_start(oracle_mod, G, R, slot_rows):
+@pytest.mark.parametrize("G,R,margin,lane_rows", [(8, 4, 12, 4), (8, 3, 16, 8), (4, 5, 10, 2)])
+def test_a_certified_band_gives_the_oracle_start(oracle_mod, G, R, margin, lane_rows):
     mat = oracle_mod.blosum62()
     m = mat.astype(np.int64)
     rng = np.random.default_rng(G * 100 + R)
@@ -130,7 +143,7 @@ def test_a_certified_band_gives_the_oracle_start(oracle_mod, G, R, slot_rows):
         rec = oracle_mod.align_pair(q, r, mat, 11, 1)
         if rec[0] == 0:
             continue
-        ok, start = banded_start(q, r, rec, m, 11, 1, G, R, slot_rows)
+        ok, start = banded_start(q, r, rec, m, 11, 1, G, R, margin, lane_rows)
         if ok:
             certified += 1
             assert start == (rec[1], rec[3]), (trial, rec, start)
@@ -139,7 +152,8 @@ def test_a_certified_band_gives_the_oracle_start(oracle_mod, G, R, slot_rows):
 
 def test_an_alignment_leaving_the_band_is_refused(oracle_mod):
     """q = A X B C, r = A B Y C with |X| = |Y| = 40 and B identical: the optimal
-    alignment runs 40 diagonals off the end diagonal, wider than the band."""
+    alignment runs 40 diagonals off the end diagonal, more than the band's
+    margin of 8."""
     mat = oracle_mod.blosum62()
     m = mat.astype(np.int64)
     rng = np.random.default_rng(7)
@@ -150,7 +164,7 @@ def test_an_alignment_leaving_the_band_is_refused(oracle_mod):
         r = np.concatenate([A, B, Y, C]).astype(np.uint8)
         rec = oracle_mod.align_pair(q, r, mat, 11, 1)
         assert rec[1] < 20 and rec[2] > 119            # the planted alignment is the optimum
-        ok, _ = banded_start(q, r, rec, m, 11, 1, 4, 4, 4)   # a band of 12 diagonals
+        ok, _ = banded_start(q, r, rec, m, 11, 1, 4, 4, 8, 4)
         assert not ok
 
 
@@ -163,5 +177,27 @@ def test_a_band_over_the_whole_matrix_always_certifies(oracle_mod):
         rec = oracle_mod.align_pair(q, r, mat, 11, 1)
         if rec[0] == 0:
             continue
-        ok, start = banded_start(q, r, rec, m, 11, 1, 32, 8, 4)   # 272 diagonals
+        ok, start = banded_start(q, r, rec, m, 11, 1, 8, 4, 80, 4)   # margin wider than the pair
         assert ok and start == (rec[1], rec[3])
+
+
+def test_the_region_is_the_stated_staircase():
+    """Row b of chunk c, lane g: exactly the positions [w0 - g, w0 - g + steps)
+    inside the matrix; the origin's cell is in D, and D holds every diagonal
+    of the band for every row."""
+    la, lb, G, R = 90, 70, 4, 3
+    W, khi = band_geometry(la, lb, 6)
+    D = region(la, lb, G, R, W, khi)
+    assert D[0, 0]
+    rows = G * R
+    for b in range(lb):
+        c, g = divmod(b, rows)
+        g //= R
+        w0 = max(0, c * rows - khi)
+        w1 = min(la, (c + 1) * rows + W - khi)
+        steps = 4 * (-(-(w1 - w0 + G - 1) // 4))
+        want = np.zeros(la, bool)
+        want[max(0, w0 - g):max(0, min(la, w0 - g + steps))] = True
+        assert (D[:, b] == want).all(), b
+        for a in range(max(0, b - khi), min(la, b - khi + W)):
+            assert D[a, b], (a, b)
