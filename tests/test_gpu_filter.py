@@ -242,16 +242,16 @@ def block(aligner, torch_mod, mat, seed, n_fam=1000):
 
 def test_trained_filter_beats_the_kmer_threshold(aligner, torch_mod, mat):
     """Trained on one seeded family block, tested on another: at a threshold
-    set for 99.5 % recall of the training positives, the network keeps at
-    least 97 % of the held-out passing pairs while aligning at most a third of
-    the candidates; the next common-k-mer threshold (3 instead of 2) loses
-    far more of the passing pairs."""
+    set for 99.8 % recall of the training positives, the network keeps at
+    least 99 % of the held-out passing pairs (the target recall) while
+    aligning at most a third of the candidates; the next common-k-mer
+    threshold (3 instead of 2) loses far more of the passing pairs."""
     from paper_2303_01845_gb300 import filter as F
     _, s_tr, _, _, X_tr, y_tr = block(aligner, torch_mod, mat, 4)
     _, s_te, cand_te, cnt_te, X_te, y_te = block(aligner, torch_mod, mat, 3)
     net, losses = F.train(aligner, X_tr, y_tr, epochs=20, batch=1024, lr=3e-3, seed=1)
     assert losses[-1] < losses[0]
-    thr = F.calibrate(net, X_tr, y_tr, 0.995)
+    thr = F.calibrate(net, X_tr, y_tr, 0.998)
     z = net.forward(X_te).cpu().numpy()
     y = y_te.cpu().numpy() > 0.5
     keep = z >= thr
@@ -260,7 +260,7 @@ def test_trained_filter_beats_the_kmer_threshold(aligner, torch_mod, mat):
     c = cnt_te.cpu().numpy()
     recall_k3 = (c[y] >= 3).mean()
     assert y.sum() > 500
-    assert recall >= 0.97, recall
+    assert recall >= 0.99, recall
     assert kept_frac <= 1 / 3, kept_frac
     assert recall_k3 < 0.8, recall_k3
     # the filtered search returns exactly the kept candidates' exact results
