@@ -419,6 +419,7 @@ int prepare_store(swgb_ctx* ctx, Store& store, const swgb_seqset* q, const swgb_
             ws.fmax_capacity = want;
         }
         CK(grow(&ws.fmax_off, &store.fmax_off_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
+        ws.fmax_off_n = store.fmax_off_capacity;
     }
     CK(grow(&ws.bin_of, &store.bin_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
     CK(grow(&ws.order, &store.order_capacity, std::max<int64_t>(n_pairs, 1)), "workspace alloc");
@@ -482,7 +483,9 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
                                    force32);
     ca.tile_overhead = ctx->tile_overhead;
     // the banded reverse pass needs the packed path and the forward maxima
-    const bool band = ctx->band_min > 0 && !ca.force32 && ws.fmax && ws.fmax_off;
+    // (a store grown for a banded call keeps its maxima arrays when the
+    // setting goes back to 0; they are sized for that call's pairs only)
+    const bool band = ctx->band_min > 0 && !ca.force32 && ws.fmax && ws.fmax_off && ws.fmax_off_n >= n_pairs;
     ca.band_min = band ? ctx->band_min : 0;
     const int pv = q->max_code < kStdLetters ? 0 : 1;   // profile variant
     sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;

@@ -236,7 +236,8 @@ struct Workspace {
     int64_t boundary_slots;
     int32_t* fmax;         // forward maxima slices (null: no banded reverse pass)
     int64_t fmax_capacity; // entries of fmax
-    int64_t* fmax_off;     // [n_pairs] slice of each pair, -1 = none
+    int64_t* fmax_off;     // [fmax_off_n] slice of each pair, -1 = none
+    int64_t fmax_off_n;    // entries of fmax_off (pairs a call may record)
 };
 
 // Arguments of one DP launch.

@@ -240,7 +240,8 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 }
                 // a pair long enough for a banded reverse pass records the
                 // maxima of its forward lanes (packed path only)
-                if (ws.fmax_off && ca.band_min > 0 && cls == 0 && lq >= ca.band_min && lr >= ca.band_min) {
+                if (ws.fmax_off && ca.band_min > 0 && p < ws.fmax_off_n && cls == 0 && lq >= ca.band_min &&
+                    lr >= ca.band_min) {
                     int shape = 0, nch = 1;
                     choose_shape(lq, lr, ca.tile_overhead, &shape, &nch);
                     fmax_rows = shape_R(shape);
@@ -273,7 +274,7 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                     cls = (ca.force32 || rec.score > 32767) ? 1 : 0;
                     // a banded pass needs the pair's forward maxima
                     if (mode == kKeysReverse && cls == 0 && ws.fmax_off && ca.band_min > 0 &&
-                        nq >= ca.band_min && nr >= ca.band_min && ws.fmax_off[p] >= 0 &&
+                        p < ws.fmax_off_n && nq >= ca.band_min && nr >= ca.band_min && ws.fmax_off[p] >= 0 &&
                         !choose_band(lq, lr, rec.score, ca.tile_overhead, &band_shape, &band_nch))
                         band_shape = -1;
                 } else {
@@ -282,10 +283,11 @@ __global__ void keys_kernel(SeqView q, SeqView r, const int32_t* __restrict__ pa
                 }
             }
         }
-        if (mode == kKeysForward && ws.fmax_off) {
-            // the slice of the forward maxima (all lanes: warp_alloc)
+        if (mode == kKeysForward && ws.fmax_off && ca.band_min > 0) {
+            // the slice of the forward maxima (all lanes: warp_alloc); only a
+            // banded call, whose workspace holds an entry per pair, records
             const int64_t off = warp_alloc(&ws.counters[kCtrFmaxUsed], fmax_need);
-            if (valid) {
+            if (valid && p < ws.fmax_off_n) {
                 const bool got = fmax_need > 0 && off + fmax_need <= ws.fmax_capacity;
                 ws.fmax_off[p] = got ? off : -1;
                 if (got) ws.fmax[off] = (int32_t)fmax_rows;

@@ -149,3 +149,27 @@ def test_mixed_batch_with_gap_settings(aligner, oracle_mod, blosum):
         got, st = run(aligner, wl, params(blosum, go, ge), 128)
         assert_same(got, oracle_records(oracle_mod, wl, blosum, go, ge), wl)
         assert st["n_band_pairs"] > 0
+
+
+def test_band_setting_changes_between_calls_of_one_context(torch_cuda, oracle_mod, blosum):
+    """A context whose workspace was grown for a small banded call, then set
+    back to no band, aligns a larger batch (its maxima arrays hold the small
+    call's pairs only and must not be touched), then a larger banded one."""
+    from paper_2303_01845_gb300 import swgb
+    al = swgb.Aligner(0)
+    try:
+        prm = params(blosum)
+        small = long_homologous(blosum, 300, 900, 1400, seed=47)
+        got, st = run(al, small, prm, 256)
+        assert st["n_band_pairs"] > 0
+        assert_same(got, oracle_records(oracle_mod, small, blosum, 11, 1), small)
+        big = long_homologous(blosum, 4000, 50, 1200, seed=48)
+        want = oracle_records(oracle_mod, big, blosum, 11, 1)
+        got, st = run(al, big, prm, 0)
+        assert st["n_band_pairs"] == 0
+        assert_same(got, want, big)
+        got, st = run(al, big, prm, 256)
+        assert st["n_band_pairs"] > 0
+        assert_same(got, want, big)
+    finally:
+        al.close()
