@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct swgb_align calls instead of replaying a captured CUDA graph")
-    ap.add_argument("--tune-pairs", type=int, default=400000,
-                    help="pairs of the batch the tile selection is tuned on")
+    ap.add_argument("--tune-pairs", type=int, default=0,
+                    help="pairs of the batch the tile and band selection is tuned on "
+                         "(0 = the whole batch; a smaller number = an evenly strided sample)")
     ap.add_argument("--tile-overhead", type=int, default=-1,
                     help="fixed tile-cost overhead instead of tuning (profiling runs)")
     ap.add_argument("--band-min", type=int, default=-1,
@@ -303,7 +304,8 @@ def run_ours(args):
     params = swgb.make_params(mat, 11, 1, timing=True)
     P = len(wl.pairs)
 
-    # tile selection tuned on an evenly strided sample of the batch (untimed)
+    # tile and band selection tuned on the batch, or an evenly strided sample
+    # of it (untimed): the band's extra rounds weigh more on a small sample
     tuning = None
     if args.band_min >= 0:
         swgb.swgb_set_band_min(al.ctx, args.band_min)
@@ -311,13 +313,14 @@ def run_ours(args):
         swgb.swgb_set_tile_overhead(al.ctx, args.tile_overhead)
         tile_overhead = args.tile_overhead
     else:
-        tune_n = min(P, args.tune_pairs)
+        tune_n = P if args.tune_pairs <= 0 else min(P, args.tune_pairs)
         tune_idx = torch.from_numpy(np.linspace(0, P - 1, tune_n).astype(np.int64)).to(dev)
         tune_pairs = pairs[tune_idx].contiguous()
         tune_out = torch.empty((tune_n, 5), dtype=torch.int32, device=dev)
         tile_overhead, _ = swgb.swgb_autotune(al.ctx, q.handle, r.handle, tune_pairs, params,
                                               tune_out, stream)
         tuning = swgb.swgb_last_tuning(al.ctx)
+        tuning["pairs"] = int(tune_n)
         del tune_pairs, tune_out
 
     # the timed step replays the whole pipeline captured once into a CUDA graph

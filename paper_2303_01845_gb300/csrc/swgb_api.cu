@@ -548,7 +548,10 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
                 ++launches;
             }
         }
-        for (int c = 0; c < kClasses; ++c) {
+        // band pairs are on the packed path: the fallback round needs no
+        // 32-bit launches
+        const int classes = mode == kKeysFallback ? 1 : kClasses;
+        for (int c = 0; c < classes; ++c) {
             for (int s = kNumShapes - 1; s >= 0; --s) {
                 cudaStream_t ks = next_stream();
                 DPArgs a = dp_args();

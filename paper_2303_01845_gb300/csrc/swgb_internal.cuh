@@ -190,6 +190,8 @@ struct ClassArgs {
 // scores S spans about S / 2 streamed positions on these workloads
 // (homologous pairs gain 2 to 3 per column), so both models stream at most
 // a = min(lq, S / 2 + 1) positions.  The choice changes no result.
+// A score large enough that choose_band streams the whole query prefix.
+constexpr int64_t kBandAnyScore = int64_t(1) << 40;
 __host__ __device__ inline bool choose_band(int64_t lq, int64_t lr, int64_t S, int overhead, int* shape,
                                             int* nch) {
     int64_t a = S / 2 + 1;
