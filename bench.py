@@ -370,6 +370,15 @@ def run_ours(args):
     aln_per_s = job_rate(P, world, args.steps, total_ms)
     fwd_mean = statistics.mean(fwd_ms)
     achieved = cells / (fwd_mean / 1e3) / 1e9
+    # the cells the reverse pass needs: the prefixes up to the end, from the
+    # start's query row on (a pass cannot stop before the start)
+    recs = out.cpu().numpy().astype(np.int64)
+    scored = recs[:, 0] > 0
+    rev_needed = int(((recs[scored, 2] - recs[scored, 1] + 1) * (recs[scored, 4] + 1)).sum())
+    slot_split = {"forward_slots": stats["forward_slots"], "reverse_slots": stats["reverse_slots"],
+                  "reverse_needed_cells": rev_needed,
+                  "forward_cells_per_slot": cells / max(stats["forward_slots"], 1),
+                  "reverse_needed_per_slot": rev_needed / max(stats["reverse_slots"], 1)}
 
     # roofline of the forward DP: add-max issue rate x SMs x max clock
     ops_per_clk, sms = swgb.swgb_probe_addmax_rate(al.ctx)
@@ -407,6 +416,7 @@ def run_ours(args):
                    "band_min": swgb.swgb_get_band_min(al.ctx),
                    "autotune": tuning,
                    "band_pairs": stats["n_band_pairs"], "band_certified": stats["n_band_certified"],
+                   "dp_slots": slot_split,
                    "launch": launch_kind,
                    "l2": "inputs (%.2f GB of residues) exceed L2; no flush" %
                          ((len(wl.q_res) + len(wl.r_res)) / 1e9),

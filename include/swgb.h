@@ -117,6 +117,9 @@ typedef struct {
     int64_t n_band_pairs;    /* reverse passes run over a band (swgb_set_band_min) */
     int64_t n_band_certified;/* of which the exactness certificate held (the others re-ran
                                 over the whole rectangle) */
+    int64_t forward_slots;   /* cell updates the forward DP kernels computed: wavefront steps x
+                                tile rows x 2 pairs per register (fill and padding included) */
+    int64_t reverse_slots;   /* likewise for the reverse pass, all its rounds */
 } swgb_stats;
 
 /* Creates a context on CUDA device `device` (made current on the calling

@@ -136,9 +136,9 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
     if ((e = cudaMalloc(&ws.task_ctr, sizeof(uint32_t) * kTaskCounters)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ws.status, sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMalloc(&ctx->d_encode_flag, 4 * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc");
-    if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "alloc");
+    if ((e = cudaMalloc(&ws.counters, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess) return bail(e, "alloc");
     if ((e = cudaMemset(ws.status, 0, sizeof(int32_t))) != cudaSuccess) return bail(e, "memset");
-    if ((e = cudaMemset(ws.counters, 0, sizeof(unsigned long long) * 8)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemset(ws.counters, 0, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess) return bail(e, "memset");
     for (int d = 0; d < 2; ++d)
         for (int c = 0; c < kClasses; ++c)
             for (int s = 0; s < kNumShapes; ++s) {
@@ -491,7 +491,7 @@ int enqueue(swgb_ctx* ctx, const Store& store, const swgb_seqset* q, const swgb_
     sc.prof_rows = pv ? kProfileRows : kStdLetters + 1;
 
     int launches = 0;
-    CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * 8, st), "memset");
+    CK(cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * kNumCounters, st), "memset");
     CK(cudaMemsetAsync(ws.task_ctr, 0, sizeof(uint32_t) * kTaskCounters, st), "memset");
     if (timed) CK(record_timing(ctx->ev[0], st), "event");
 
@@ -619,7 +619,7 @@ SWGB_EXPORT int swgb_align(swgb_ctx* ctx, const swgb_seqset* queries, const swgb
         ctx->last_launches = 0;
         ctx->timed = false;
         ctx->last_stream = (cudaStream_t)stream;
-        CK(cudaMemsetAsync(ctx->ws.counters, 0, sizeof(unsigned long long) * 8, (cudaStream_t)stream), "memset");
+        CK(cudaMemsetAsync(ctx->ws.counters, 0, sizeof(unsigned long long) * kNumCounters, (cudaStream_t)stream), "memset");
         return SWGB_OK;
     }
     rc = prepare_store(ctx, ctx->store, queries, refs, n_pairs);
@@ -666,7 +666,7 @@ SWGB_EXPORT int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out) {
     if (!ctx || !out) return SWGB_EINVAL;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(ctx->last_stream), "stream sync");
-    unsigned long long c[8];
+    unsigned long long c[kNumCounters];
     CK(cudaMemcpy(c, ctx->ws.counters, sizeof(c), cudaMemcpyDeviceToHost), "counters D2H");
     std::memset(out, 0, sizeof(*out));
     out->n_pairs = ctx->last_pairs;
@@ -684,6 +684,8 @@ SWGB_EXPORT int swgb_last_stats(swgb_ctx* ctx, swgb_stats* out) {
     out->kernel_launches = ctx->last_launches;
     out->n_band_pairs = (int64_t)c[kCtrBandPairs];
     out->n_band_certified = (int64_t)c[kCtrBandCertified];
+    out->forward_slots = (int64_t)c[kCtrFwdSlots];
+    out->reverse_slots = (int64_t)c[kCtrRevSlots];
     return SWGB_OK;
 }
 
@@ -742,6 +744,7 @@ constexpr int64_t kNaStatus = kNaTask + align256(4 * 2 * (int64_t)kNumKernels);
 constexpr int64_t kNaFlags = kNaStatus + 256;
 constexpr int64_t kNaCounters = kNaFlags + 256;
 constexpr int64_t kNaBinOf = kNaCounters + 256;
+static_assert(8 * kNumCounters <= 256, "no-alloc counters exceed their slot");
 constexpr int64_t kNaOrder = kNaBinOf + align256(4 * (int64_t)SWGB_NOALLOC_MAX_PAIRS);
 constexpr int64_t kNaBoundary = kNaOrder + align256(4 * (int64_t)SWGB_NOALLOC_MAX_PAIRS);
 constexpr int64_t kNaEnd = kNaBoundary + 8 * kNoallocSlots * (int64_t)SWGB_NOALLOC_MAX_QUERY_LENGTH;

@@ -270,7 +270,10 @@ enum Counter {
     kCtrBandPairs = 5,      // reverse passes run over a band
     kCtrBandCertified = 6,  // of which the certificate held
     kCtrFmaxUsed = 7,       // forward-maxima entries handed out
+    kCtrFwdSlots = 8,       // cell updates the forward DP kernels computed (fill, padding included)
+    kCtrRevSlots = 9,       // likewise, the reverse pass (all its rounds)
 };
+constexpr int kNumCounters = 16;
 
 // Marker left in q_start by the banded reverse pass for a pair whose
 // certificate did not hold: the fallback keys pass sends it to the full

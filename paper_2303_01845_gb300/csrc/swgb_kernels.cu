@@ -554,6 +554,9 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
     const uint32_t ONE = L::splat(1);
     const uint32_t C_UOP = (uint32_t)(-(oe * 65537));    // U -> U - (o + e) in both halves
 
+    // wavefront steps this warp ran; steps x its 32 lanes' rows x PACK cell
+    // updates go to the pass's counter once, when the warp runs out of work
+    uint32_t steps_run = 0;
     for (;;) {
         uint32_t task = 0;
         if (lane == 0) task = atomicAdd(a.task_ctr, 1u);
@@ -1053,6 +1056,7 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
             } else {
                 run(std::false_type{});
             }
+            steps_run += (uint32_t)t_end;
 
             // ---- forward maxima of the lane's rows for the banded reverse
             // pass: entry jl / R of the pair's slice (its forward tile is this
@@ -1173,6 +1177,8 @@ __global__ void __launch_bounds__(kDPThreads, dp_min_blocks(R)) dp_kernel(const 
         }
         if (BAND && ncert > 0) atomicAdd(&a.counters[kCtrBandCertified], (unsigned long long)ncert);
     }
+    if (lane == 0 && steps_run > 0 && a.counters)
+        atomicAdd(&a.counters[REV ? kCtrRevSlots : kCtrFwdSlots], (unsigned long long)steps_run * (32 * R * PACK));
 }
 
 // ---------------------------------------------------------------------------

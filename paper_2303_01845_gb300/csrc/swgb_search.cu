@@ -1067,7 +1067,8 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 if (lane < kFeatBins) s_hist[w][lane] = 0;
                 __syncwarp();
                 int c = 0;
-                int64_t dmin = INT64_MAX, dmax = INT64_MIN;
+                int32_t dmin = INT32_MAX, dmax = INT32_MIN;
+                const int32_t lj32 = (int32_t)lj, D32 = (int32_t)D;
                 // four probes in flight per lane
                 for (uint32_t e0 = lane; e0 < nj; e0 += 128) {
                     uint32_t xs[4];
@@ -1081,8 +1082,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                         for (uint32_t probe = 0; probe < cap; ++probe) {
                             const uint32_t key = keys[h];
                             if (key == x) {
-                                const int64_t d = (int64_t)pos[h] - (int64_t)a.posB[oj + e0 + 32 * u];
-                                atomicAdd(&s_hist[w][(kFeatBins * (d + lj - a.k)) / D], 1u);
+                                // 0 <= d + lj - k <= li + lj - 2k = D - 1 (both positions
+                                // start a k-mer): the bin is an unsigned 32-bit quotient
+                                const int32_t d = (int32_t)pos[h] - (int32_t)a.posB[oj + e0 + 32 * u];
+                                atomicAdd(&s_hist[w][(uint32_t)(kFeatBins * (d + lj32 - a.k)) / (uint32_t)D32], 1u);
                                 ++c;
                                 dmin = min(dmin, d);
                                 dmax = max(dmax, d);
@@ -1095,8 +1098,8 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 }
                 for (int s = 16; s; s >>= 1) {
                     c += __shfl_xor_sync(0xffffffffu, c, s);
-                    dmin = min(dmin, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)dmin, s));
-                    dmax = max(dmax, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)dmax, s));
+                    dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, s));
+                    dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, s));
                 }
                 __syncwarp();
                 const uint32_t hmax =
@@ -1120,7 +1123,7 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 else if (lane == 28) { num = lj; den = lj + 256; }
                 else if (lane == 29) { num = hmax; den = c; }
                 else if (lane == 30) { num = c; den = min(ni, nj); }
-                else { num = dmax - dmin; den = c >= 2 ? D : 0; }
+                else { num = (int64_t)dmax - dmin; den = c >= 2 ? D : 0; }
                 o[lane] = feat_ratio(num, den);
                 __syncwarp();
             }

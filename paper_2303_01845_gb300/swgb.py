@@ -67,7 +67,8 @@ class swgb_stats(ctypes.Structure):
                 ("forward_cells", ctypes.c_int64), ("reverse_cells", ctypes.c_int64),
                 ("forward_ms", ctypes.c_float), ("reverse_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int32),
-                ("n_band_pairs", ctypes.c_int64), ("n_band_certified", ctypes.c_int64)]
+                ("n_band_pairs", ctypes.c_int64), ("n_band_certified", ctypes.c_int64),
+                ("forward_slots", ctypes.c_int64), ("reverse_slots", ctypes.c_int64)]
 
 
 class swgb_tuning(ctypes.Structure):
