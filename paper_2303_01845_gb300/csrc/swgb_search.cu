@@ -961,7 +961,12 @@ constexpr int kFeat = 32;
 constexpr int kFeatBins = 24;
 constexpr int kFeatWarps = 8;
 constexpr int kFeatWarpSlots = 1024;  // warp-private shared table of K(i): up to 512 k-mers
-constexpr int kFeatSmemBytes = kFeatWarps * kFeatWarpSlots * 8;
+// Per warp, an 8192-bit filter of K(i) (one bit per k-mer, another
+// multiplicative hash than the table's): a partner k-mer whose bit is clear is
+// not in K(i), so most misses cost one shared load instead of a probe run.
+constexpr int kFeatBitWords = 256;
+constexpr int kFeatSmemBytes = kFeatWarps * (kFeatWarpSlots * 8 + kFeatBitWords * 4);
+__device__ __forceinline__ uint32_t feat_bit_of(uint32_t key) { return (key * 0x85ebca6bu) >> 19; }
 constexpr int kFeatChunk = 32;        // consecutive pairs per warp task
 
 struct FeatArgs {
@@ -1008,6 +1013,7 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
     __shared__ uint32_t s_hist[kFeatWarps][kFeatBins];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t* const s_keys = s_tab + w * 2 * kFeatWarpSlots;
+    uint32_t* const s_bits = s_tab + kFeatWarps * 2 * kFeatWarpSlots + w * kFeatBitWords;
     uint32_t* const g_keys = a.gtab ? a.gtab + ((size_t)blockIdx.x * kFeatWarps + w) * 2 * a.gslots
                                     : nullptr;
     for (;;) {
@@ -1037,10 +1043,13 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
             __syncwarp();
             if (table_ok) {
                 for (uint32_t s = lane; s < cap; s += 32) keys[s] = kEmpty;
+                for (int s = lane; s < kFeatBitWords; s += 32) s_bits[s] = 0u;
                 __syncwarp();
                 const int64_t oi = a.A.off[i];
                 for (uint32_t e = lane; e < ni; e += 32) {
                     const uint32_t x = a.kmA[oi + e];
+                    const uint32_t hb = feat_bit_of(x);
+                    atomicOr(&s_bits[hb >> 5], 1u << (hb & 31));
                     uint32_t h = slot_of(x, mask);
                     for (uint32_t probe = 0; probe < cap; ++probe) {
                         if (atomicCAS(&keys[h], kEmpty, x) == kEmpty) {
@@ -1078,6 +1087,8 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                     for (int u = 0; u < 4; ++u) {
                         const uint32_t x = xs[u];
                         if (x == kEmpty) continue;
+                        const uint32_t hb = feat_bit_of(x);
+                        if (((s_bits[hb >> 5] >> (hb & 31)) & 1u) == 0u) continue;   // not in K(i)
                         uint32_t h = slot_of(x, mask);
                         for (uint32_t probe = 0; probe < cap; ++probe) {
                             const uint32_t key = keys[h];
