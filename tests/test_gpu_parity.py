@@ -55,6 +55,11 @@ def test_plain_10k_bit_exact(aligner, oracle_mod, blosum, plain10k):
     assert st["forward_cells"] == plain10k.cells()
     assert st["n_int16_pairs"] == len(plain10k.pairs)
     assert st["n_reverse_pairs"] == int((want[:, 0] > 0).sum())
+    # cell updates computed: every forward cell at least once, fill and
+    # padding on top; the reverse pass computes some
+    assert st["forward_slots"] >= st["forward_cells"]
+    assert st["forward_slots"] < 2 * st["forward_cells"]
+    assert 0 < st["reverse_slots"] <= st["forward_slots"]
 
 
 def test_plain_10k_forced_int32_path(aligner, oracle_mod, blosum, plain10k):
