@@ -300,6 +300,13 @@ struct JoinArgs {
     int32_t* status;
     int32_t* large_rows;       // [n] the rows above the shared-memory table
     int64_t n_tasks;           // LARGE launches: tasks are large_rows[0, n_tasks); else rows
+    // counting pass with a stash: each row's sorted list (j << 32 | count) also
+    // goes to stash[stash_off[i] ..) (slices handed out by stash_ctr; -1 where
+    // the stash is full), so that a copy replaces the writing pass
+    uint64_t* stash;           // [stash_cap] or null
+    int64_t stash_cap;
+    int64_t* stash_off;        // [n]
+    unsigned long long* stash_ctr;
 };
 
 __global__ void row_need_kernel(JoinArgs a) {
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
     uint32_t* s_cnts = s_keys + kJoinSmemSlots;
     __shared__ int64_t s_task;
     __shared__ uint32_t s_n;
+    __shared__ int64_t s_off;
     const int64_t n = a.s.n;
     for (;;) {
         int64_t i = next_task(a.ctr, &s_task);
@@ -413,14 +421,14 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
             const uint32_t j = keys[t];
             if (j != kEmpty && cnts[t] >= (uint32_t)a.min_shared) {
                 const uint32_t e = atomicAdd(&s_n, 1u);
-                if (WRITE) list[e] = ((uint64_t)j << 32) | cnts[t];
+                if (WRITE || a.stash) list[e] = ((uint64_t)j << 32) | cnts[t];
             }
         }
         __syncthreads();
         const uint32_t m = s_n;
         if (!WRITE) {
             if (threadIdx.x == 0) a.ccount[i] = m;
-            continue;
+            if (!a.stash) continue;
         }
         if (m == 0) continue;
         // bitonic sort of list[0, P) by j (padding sorts last); P <= cap / 2
@@ -443,11 +451,47 @@ __global__ void __launch_bounds__(kSearchThreads) join_kernel(JoinArgs a) {
                 __syncthreads();
             }
         }
+        if (!WRITE) {
+            // the counting pass stashes the sorted row
+            if (threadIdx.x == 0) {
+                int64_t off = (int64_t)atomicAdd(a.stash_ctr, (unsigned long long)m);
+                if (off + m > a.stash_cap) off = -1;
+                a.stash_off[i] = off;
+                s_off = off;
+            }
+            __syncthreads();
+            const int64_t off = s_off;
+            if (off >= 0)
+                for (uint32_t t = threadIdx.x; t < m; t += blockDim.x) a.stash[off + t] = list[t];
+            __syncthreads();
+            continue;
+        }
         const int64_t base = (int64_t)a.coff[i];
         for (uint32_t t = threadIdx.x; t < m; t += blockDim.x) {
             const int64_t d = base + t;
             if (d < a.capacity) {
                 const uint64_t v = list[t];
+                a.out_pairs[2 * d] = (int32_t)i;
+                a.out_pairs[2 * d + 1] = (int32_t)(v >> 32);
+                if (a.out_counts) a.out_counts[d] = (int32_t)(v & 0xffffffffu);
+            }
+        }
+    }
+}
+
+// Copies every row's stashed list to its place in (i, j) order (one warp per
+// row): what the writing pass would write, without its second join.
+__global__ void join_copy_kernel(JoinArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.s.n; i += warps) {
+        const uint32_t m = a.ccount[i];
+        if (m == 0) continue;
+        const int64_t src = a.stash_off[i], base = (int64_t)a.coff[i];
+        for (uint32_t t = lane; t < m; t += 32) {
+            const int64_t d = base + t;
+            if (d < a.capacity) {
+                const uint64_t v = a.stash[src + t];
                 a.out_pairs[2 * d] = (int32_t)i;
                 a.out_pairs[2 * d + 1] = (int32_t)(v >> 32);
                 if (a.out_counts) a.out_counts[d] = (int32_t)(v & 0xffffffffu);
@@ -513,14 +557,14 @@ __global__ void __launch_bounds__(kWarpJoinWarps * 32) join_warp_kernel(JoinArgs
             const uint32_t j = keys[t];
             if (j != kEmpty && cnts[t] >= (uint32_t)a.min_shared) {
                 const uint32_t e = atomicAdd(&s_n[w], 1u);
-                if (WRITE) list[e] = ((uint64_t)j << 32) | cnts[t];
+                if (WRITE || a.stash) list[e] = ((uint64_t)j << 32) | cnts[t];
             }
         }
         __syncwarp();
         const uint32_t m = s_n[w];
         if (!WRITE) {
             if (lane == 0) a.ccount[i] = m;
-            continue;
+            if (!a.stash) continue;
         }
         if (m == 0) continue;
         // bitonic sort of list[0, P) by j (padding sorts last); P <= cap / 2
@@ -541,6 +585,20 @@ __global__ void __launch_bounds__(kWarpJoinWarps * 32) join_warp_kernel(JoinArgs
                 }
                 __syncwarp();
             }
+        }
+        if (!WRITE) {
+            // the counting pass stashes the sorted row
+            int64_t off = 0;
+            if (lane == 0) {
+                off = (int64_t)atomicAdd(a.stash_ctr, (unsigned long long)m);
+                if (off + m > a.stash_cap) off = -1;
+                a.stash_off[i] = off;
+            }
+            off = __shfl_sync(0xffffffffu, off, 0);
+            if (off >= 0)
+                for (uint32_t t = lane; t < m; t += 32) a.stash[off + t] = list[t];
+            __syncwarp();
+            continue;
         }
         const int64_t base = (int64_t)a.coff[i];
         for (uint32_t t = lane; t < m; t += 32) {
@@ -967,6 +1025,7 @@ constexpr int kFeatWarpSlots = 1024;  // warp-private shared table of K(i): up t
 constexpr int kFeatBitWords = 256;
 constexpr int kFeatSmemBytes = kFeatWarps * (kFeatWarpSlots * 8 + kFeatBitWords * 4);
 __device__ __forceinline__ uint32_t feat_bit_of(uint32_t key) { return (key * 0x85ebca6bu) >> 19; }
+constexpr int64_t kJoinStashMax = int64_t(1) << 27;   // entries (8 B) of the joins' stash
 constexpr int kFeatChunk = 32;        // consecutive pairs per warp task
 
 struct FeatArgs {
@@ -1188,6 +1247,8 @@ struct SearchStore {
     int64_t* lists = nullptr;     int64_t lists_cap = 0;
     uint2* range = nullptr;       int64_t range_cap = 0;
     int32_t* large_rows = nullptr; int64_t large_rows_cap = 0;
+    uint64_t* stash = nullptr;    int64_t stash_cap = 0;     // joins: the counting pass's rows
+    int64_t* stash_off = nullptr; int64_t stash_off_cap = 0;
     // pair features: k-mer sets of a second set, letter counts of both
     uint32_t* ent2_kmer = nullptr; int64_t ent2_cap = 0;
     uint32_t* ent2_pos = nullptr;  int64_t ent2p_cap = 0;
@@ -1205,7 +1266,7 @@ void search_store_free(SearchStore* s) {
     void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq,
                     s->need, s->ccount, s->coff, s->part, s->gtab, s->bnd, s->ctr,
                     s->status, s->large_rows, s->lists, s->range, s->ent2_kmer, s->ent2_pos, s->kcount2,
-                    s->comp, s->comp2, s->flags};
+                    s->comp, s->comp2, s->flags, s->stash, s->stash_off};
     for (void* p : ptrs) cudaFree(p);
     delete s;
 }
@@ -1336,7 +1397,13 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     CK(grow(&S->coff, &S->coff_cap, n + 1), "join scratch");
     CK(grow(&S->large_rows, &S->large_rows_cap, n), "join scratch");
     CK(grow(&S->range, &S->range_cap, std::max<int64_t>(rows->total, 1)), "join scratch");
-    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 9, st), "memset");
+    // the counting pass stashes each row's sorted list (room for the caller's
+    // capacity, at most kJoinStashMax entries); if they all fit, a copy
+    // replaces the writing pass
+    const int64_t stash_cap = std::min<int64_t>(std::max<int64_t>(capacity, 1), kJoinStashMax);
+    CK(grow(&S->stash, &S->stash_cap, stash_cap), "join scratch");
+    CK(grow(&S->stash_off, &S->stash_off_cap, n), "join scratch");
+    CK(cudaMemsetAsync(S->ctr + 1, 0, sizeof(unsigned long long) * 10, st), "memset");
     JoinArgs ja{};
     ja.s = view(rows);
     ja.ent_kmer = kmer;
@@ -1357,6 +1424,10 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
     ja.large_rows = S->large_rows;
     ja.n_tasks = n;
     ja.range = S->range;
+    ja.stash = S->stash;
+    ja.stash_cap = stash_cap;
+    ja.stash_off = S->stash_off;
+    ja.stash_ctr = S->ctr + 10;
     const int64_t wg = warp_grid(ctx, n, 256);
     row_need_kernel<<<(unsigned)wg, 256, 0, st>>>(ja);
     CK(cudaGetLastError(), "row_need kernel");
@@ -1394,6 +1465,15 @@ int join_rows(swgb_ctx* ctx, SearchStore* S, const swgb_seqset* rows, const uint
             *launches += (large_blocks ? 3 : 2) + 3;
             int rc = device_scan<uint64_t>(ctx, S, S->ccount, n, S->coff, st);
             if (rc) return rc;
+            unsigned long long stashed = 0;
+            CK(cudaMemcpyAsync(&stashed, S->ctr + 10, sizeof(stashed), cudaMemcpyDeviceToHost, st), "stash D2H");
+            CK(cudaStreamSynchronize(st), "stream sync");
+            if ((int64_t)stashed <= stash_cap) {
+                join_copy_kernel<<<(unsigned)wg, 256, 0, st>>>(ja);
+                CK(cudaGetLastError(), "join copy kernel");
+                *launches += 1;
+                break;   // every row's list is in place: no writing pass
+            }
         } else {
             join_warp_kernel<true><<<warp_blocks, kWarpJoinWarps * 32, kWarpJoinSmemBytes, st>>>(jw);
             join_kernel<false, true><<<join_blocks, kSearchThreads, kJoinSmemBytes, st>>>(ja);
