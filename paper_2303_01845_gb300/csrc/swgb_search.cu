@@ -1027,6 +1027,7 @@ constexpr int kFeatSmemBytes = kFeatWarps * (kFeatWarpSlots * 8 + kFeatBitWords 
 __device__ __forceinline__ uint32_t feat_bit_of(uint32_t key) { return (key * 0x85ebca6bu) >> 19; }
 constexpr int64_t kJoinStashMax = int64_t(1) << 27;   // entries (8 B) of the joins' stash
 constexpr int kFeatChunk = 32;        // consecutive pairs per warp task
+constexpr int kFeatInFlight = 8;      // partner k-mers loaded at once per lane
 
 struct FeatArgs {
     SeqView A, B;
@@ -1105,17 +1106,30 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 for (int s = lane; s < kFeatBitWords; s += 32) s_bits[s] = 0u;
                 __syncwarp();
                 const int64_t oi = a.A.off[i];
-                for (uint32_t e = lane; e < ni; e += 32) {
-                    const uint32_t x = a.kmA[oi + e];
-                    const uint32_t hb = feat_bit_of(x);
-                    atomicOr(&s_bits[hb >> 5], 1u << (hb & 31));
-                    uint32_t h = slot_of(x, mask);
-                    for (uint32_t probe = 0; probe < cap; ++probe) {
-                        if (atomicCAS(&keys[h], kEmpty, x) == kEmpty) {
-                            pos[h] = a.posA[oi + e];
-                            break;
+                // K(i)'s entries (k-mer, position) loaded four per lane ahead
+                // of their inserts, so the loads overlap
+                for (uint32_t e0 = lane; e0 < ni; e0 += 128) {
+                    uint32_t xs[4], ps[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool in = e0 + 32 * u < ni;
+                        xs[u] = in ? a.kmA[oi + e0 + 32 * u] : kEmpty;
+                        ps[u] = in ? a.posA[oi + e0 + 32 * u] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t x = xs[u];
+                        if (x == kEmpty) continue;
+                        const uint32_t hb = feat_bit_of(x);
+                        atomicOr(&s_bits[hb >> 5], 1u << (hb & 31));
+                        uint32_t h = slot_of(x, mask);
+                        for (uint32_t probe = 0; probe < cap; ++probe) {
+                            if (atomicCAS(&keys[h], kEmpty, x) == kEmpty) {
+                                pos[h] = ps[u];
+                                break;
+                            }
+                            h = (h + 1) & mask;
                         }
-                        h = (h + 1) & mask;
                     }
                 }
                 __syncwarp();
@@ -1137,13 +1151,14 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(FeatArgs a) {
                 int c = 0;
                 int32_t dmin = INT32_MAX, dmax = INT32_MIN;
                 const int32_t lj32 = (int32_t)lj, D32 = (int32_t)D;
-                // four probes in flight per lane
-                for (uint32_t e0 = lane; e0 < nj; e0 += 128) {
-                    uint32_t xs[4];
+                // kFeatInFlight partner k-mers loaded per lane at once
+                for (uint32_t e0 = lane; e0 < nj; e0 += 32 * kFeatInFlight) {
+                    uint32_t xs[kFeatInFlight];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) xs[u] = e0 + 32 * u < nj ? a.kmB[oj + e0 + 32 * u] : kEmpty;
+                    for (int u = 0; u < kFeatInFlight; ++u)
+                        xs[u] = e0 + 32 * u < nj ? a.kmB[oj + e0 + 32 * u] : kEmpty;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kFeatInFlight; ++u) {
                         const uint32_t x = xs[u];
                         if (x == kEmpty) continue;
                         const uint32_t hb = feat_bit_of(x);
