@@ -173,3 +173,21 @@ def test_band_setting_changes_between_calls_of_one_context(torch_cuda, oracle_mo
         assert_same(got, want, big)
     finally:
         al.close()
+
+
+def test_band_with_an_asymmetric_matrix_and_the_32_bit_path(aligner, oracle_mod, blosum):
+    """The certificate does not depend on the matrix: BLOSUM62 with an
+    asymmetric perturbation of -1..1 (homologous pairs still score high, so
+    long ones take the band) gives the oracle's records; with the 32-bit path
+    forced no pair takes the band (it needs the packed path)."""
+    from paper_2303_01845_gb300 import swgb
+    wl = long_homologous(blosum, 600, 700, 1600, seed=49)
+    rng = np.random.default_rng(50)
+    asym = (blosum.astype(np.int16) + rng.integers(-1, 2, size=blosum.shape)).astype(np.int8)
+    assert not np.array_equal(asym, asym.T)
+    got, st = run(aligner, wl, params(asym, 10, 1), 256)
+    assert_same(got, oracle_records(oracle_mod, wl, asym, 10, 1), wl)
+    assert st["n_band_pairs"] > 0
+    got, st = run(aligner, wl, swgb.make_params(blosum, 11, 1, force_int32=True), 256)
+    assert_same(got, oracle_records(oracle_mod, wl, blosum, 11, 1), wl)
+    assert st["n_band_pairs"] == 0 and st["n_int32_pairs"] == len(wl.pairs)
