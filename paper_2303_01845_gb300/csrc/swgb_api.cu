@@ -161,6 +161,11 @@ SWGB_EXPORT int swgb_create(int device, swgb_ctx** out) {
         if ((e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "cudaEventCreate");
     }
+    int least_prio = 0, greatest_prio = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&least_prio, &greatest_prio)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetStreamPriorityRange");
+    if ((e = cudaStreamCreateWithPriority(&ctx->first, cudaStreamNonBlocking, greatest_prio)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
     *out = ctx;
     return SWGB_OK;
 }
@@ -193,6 +198,7 @@ SWGB_EXPORT void swgb_destroy(swgb_ctx* ctx) {
         if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
         if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
     }
+    if (ctx->first) cudaStreamDestroy(ctx->first);
     delete ctx;
 }
 

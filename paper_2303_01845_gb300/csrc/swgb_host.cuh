@@ -58,6 +58,10 @@ struct swgb_ctx {
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kSide] = {};
+    // a stream of the greatest priority: the block scheduler places the
+    // blocks of its launches before pending blocks of the other streams (the
+    // identity's cooperative spans, the critical path of its launches)
+    cudaStream_t first = nullptr;
     bool timed = false;
     cudaStream_t last_stream = nullptr;
     int32_t last_launches = 0;

@@ -641,6 +641,12 @@ constexpr int kIdCoopCols = 2048;              // spans of >= 8 chunks: one bloc
 constexpr int kIdCoopColsSmall = 1024;         // >= 4 chunks, when the batch leaves warps idle
 constexpr int kIdSmallBatchPerSM = 64;         // pairs per SM up to which a batch counts as small
 constexpr int kIdSpinLimit = 1 << 25;          // bounded wait on the previous chunk's progress
+// Work lists: the regular classes 0..3, then the cooperative spans of classes
+// 2 and 3.  Each list is ordered by decreasing work (longest first, so that
+// no long span starts near the end of its launch), through a counting sort
+// over kIdBuckets buckets of a span's warp steps, four per doubling.
+constexpr int kIdLists = kIdClasses + 2;
+constexpr int kIdBuckets = 128;
 constexpr int32_t kNegInf = -(1 << 28);
 
 // A chunk's last column at one row: H, E and the (matches, columns) of H and E.
@@ -661,12 +667,11 @@ struct IdentArgs {
     int32_t* out;              // [n_pairs][3]: matches, columns, pass
     IdBnd* bnd;                // per-warp boundary columns, one entry per row
     int64_t bnd_stride;
-    const int64_t* list;       // the pairs of this launch's class
+    const int64_t* list;       // the pairs of this launch's list, longest first
     int64_t n_list;
-    int64_t n_front;           // tasks < n_front read list[task], later ones
-    int64_t back_base;         // list[back_base - (task - n_front)]
-    int64_t* lists;            // classification: kIdClasses lists of n_pairs entries
-    unsigned long long* ctr;   // [0] task counter, [1..kIdClasses] list sizes
+    int64_t* lists;            // the kIdLists lists one after another (n_pairs entries)
+    uint32_t* hist;            // [kIdLists][kIdBuckets] pair counts, then as many list cursors
+    unsigned long long* ctr;   // [0] task counter, [1..kIdLists] list sizes
     int32_t* status;
 };
 
@@ -709,37 +714,109 @@ __device__ __forceinline__ void ident_write(const IdentArgs& a, int64_t p, int32
 }
 
 // Classes (rows + columns < 65536): 0 = at most kIdSmallCols columns, 1 = at
-// most kIdMidCols, 2 = more; 3 = rows + columns >= 65536.  Zero scores and
-// records outside their sequences are answered here.
-__global__ void ident_classify_kernel(IdentArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_pairs; p += stride) {
-        const swgb_record rc = a.rec[p];
-        if (rc.score <= 0) {
-            ident_write(a, p, 0, 0, 0);
-            continue;
-        }
-        const int32_t qi = a.pairs[2 * p], ri = a.pairs[2 * p + 1];
-        const bool ok_idx = qi >= 0 && qi < a.q.n && ri >= 0 && ri < a.r.n;
-        const int64_t lq = ok_idx ? a.q.off[qi + 1] - a.q.off[qi] : 0;
-        const int64_t lr = ok_idx ? a.r.off[ri + 1] - a.r.off[ri] : 0;
-        const int64_t n = (int64_t)rc.q_end - rc.q_start + 1, m = (int64_t)rc.r_end - rc.r_start + 1;
-        if (!ok_idx || rc.q_start < 0 || rc.q_end >= lq || rc.r_start < 0 || rc.r_end >= lr ||
-            n <= 0 || m <= 0 || n >= a.bnd_stride) {
+// most kIdMidCols, 2 = more; 3 = rows + columns >= 65536.  ident_route gives
+// pair p's list (its class, or 4 / 5 for the spans of classes 2 / 3 of at
+// least coop_cols columns) and work bucket, or -1 for a pair answered at
+// classification: a zero score (0, 0, fail) or a record outside its
+// sequences (-1, -1, fail and status 3), written when ANSWER is set.
+template <bool ANSWER>
+__device__ int ident_route(const IdentArgs& a, int64_t p, int* bucket) {
+    const swgb_record rc = a.rec[p];
+    if (rc.score <= 0) {
+        if (ANSWER) ident_write(a, p, 0, 0, 0);
+        return -1;
+    }
+    const int32_t qi = a.pairs[2 * p], ri = a.pairs[2 * p + 1];
+    const bool ok_idx = qi >= 0 && qi < a.q.n && ri >= 0 && ri < a.r.n;
+    const int64_t lq = ok_idx ? a.q.off[qi + 1] - a.q.off[qi] : 0;
+    const int64_t lr = ok_idx ? a.r.off[ri + 1] - a.r.off[ri] : 0;
+    const int64_t n = (int64_t)rc.q_end - rc.q_start + 1, m = (int64_t)rc.r_end - rc.r_start + 1;
+    if (!ok_idx || rc.q_start < 0 || rc.q_end >= lq || rc.r_start < 0 || rc.r_end >= lr ||
+        n <= 0 || m <= 0 || n >= a.bnd_stride) {
+        if (ANSWER) {
             atomicMax(a.status, 3);
             ident_write(a, p, -1, -1, 0);
-            continue;
         }
-        const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
-        int64_t* list = a.lists + cls * a.n_pairs;
-        if (cls >= 2 && m >= a.coop_cols) {
-            // spans of many chunks at the front of the list (the cooperative
-            // launch takes them), the rest from its back
-            list[(int64_t)atomicAdd(&a.ctr[5 + (cls - 2)], 1ull)] = p;
-        } else if (cls >= 2) {
-            list[a.n_pairs - 1 - (int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
-        } else {
-            list[(int64_t)atomicAdd(&a.ctr[1 + cls], 1ull)] = p;
+        return -1;
+    }
+    const int cls = n + m >= 65536 ? 3 : (m <= kIdSmallCols ? 0 : (m <= kIdMidCols ? 1 : 2));
+    const bool coop = cls >= 2 && m >= a.coop_cols;
+    // warp steps of the span: chunks (per warp when cooperative) x rows
+    const int64_t chunk = cls == 0 ? 8 * kIdR : (cls == 1 ? 16 * kIdR : 32 * kIdR);
+    int64_t nch = (m + chunk - 1) / chunk;
+    if (coop) nch = (nch + kIdWarps - 1) / kIdWarps;
+    const uint64_t work = (uint64_t)(nch * (n + 32));
+    const int e = 63 - __clzll((long long)work);                 // work >= 33: e >= 5
+    *bucket = min(4 * e + (int)((work >> (e - 2)) & 3u), kIdBuckets - 1);
+    return coop ? kIdClasses + (cls - 2) : cls;
+}
+
+// Counting pass: answers what needs no alignment and counts the pairs of
+// each (list, bucket).
+__global__ void ident_classify_kernel(IdentArgs a) {
+    __shared__ uint32_t s_hist[kIdLists * kIdBuckets];
+    for (int i = threadIdx.x; i < kIdLists * kIdBuckets; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    for (int64_t p0 = base; p0 < a.n_pairs; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        int bucket = 0;
+        const int list = p < a.n_pairs ? ident_route<true>(a, p, &bucket) : -1;
+        const int key = list < 0 ? -1 : list * kIdBuckets + bucket;
+        // one shared atomic per distinct key of the warp
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&s_hist[key], (uint32_t)__popc(same));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kIdLists * kIdBuckets; i += blockDim.x)
+        if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+}
+
+// One block: the lists one after another, each by decreasing bucket; the
+// cursor of every (list, bucket) and the list sizes (ctr[1 + list]).
+__global__ void ident_scan_kernel(IdentArgs a) {
+    __shared__ uint32_t s_cnt[kIdLists * kIdBuckets];
+    for (int i = threadIdx.x; i < kIdLists * kIdBuckets; i += blockDim.x) s_cnt[i] = a.hist[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t off = 0;
+        for (int l = 0; l < kIdLists; ++l) {
+            const uint32_t first = off;
+            for (int b = kIdBuckets - 1; b >= 0; --b) {
+                const uint32_t c = s_cnt[l * kIdBuckets + b];
+                s_cnt[l * kIdBuckets + b] = off;
+                off += c;
+            }
+            a.ctr[1 + l] = off - first;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kIdLists * kIdBuckets; i += blockDim.x)
+        a.hist[kIdLists * kIdBuckets + i] = s_cnt[i];
+}
+
+// Placing pass: each routed pair at its (list, bucket) cursor.
+__global__ void ident_place_kernel(IdentArgs a) {
+    uint32_t* cursor = a.hist + kIdLists * kIdBuckets;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t p0 = base; p0 < a.n_pairs; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        int bucket = 0;
+        const int list = p < a.n_pairs ? ident_route<false>(a, p, &bucket) : -1;
+        const int key = list < 0 ? -1 : list * kIdBuckets + bucket;
+        // one global atomic per distinct key of the warp; ranks below it
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(same) - 1;
+        uint32_t pos = 0;
+        if (key >= 0 && lane == leader) pos = atomicAdd(&cursor[key], (uint32_t)__popc(same));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        const uint64_t at = (uint64_t)pos + __popc(same & ((1u << lane) - 1u));
+        if (key >= 0) {
+            if (at < (uint64_t)a.n_pairs) a.lists[at] = p;
+            else atomicMax(a.status, 5);   // the two passes routed differently
         }
     }
 }
@@ -767,6 +844,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
     __shared__ int8_t s_mat[kAlpha * kAlpha];
     __shared__ __align__(8) uint2 s_prof[PROF ? kIdWarps * 32 * kAlpha : 1];
     __shared__ long long s_prog[COOP ? kIdWarps : 1];
+    __shared__ IdBnd s_stage[COOP ? kIdWarps * 2 * 32 : 1];
     __shared__ int s_abort;    // COOP: a wait ran out; later waits return at once
     __shared__ int64_t s_task;
     for (int t = threadIdx.x; t < kAlpha * kAlpha; t += blockDim.x) s_mat[t] = a.mat[t];
@@ -799,7 +877,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
         // this group's pair (groups past the list compute nothing)
         const int64_t li = first + grp;
         const bool live = li < a.n_list;
-        const int64_t p = !live ? 0 : li < a.n_front ? a.list[li] : a.list[a.back_base - (li - a.n_front)];
+        const int64_t p = !live ? 0 : a.list[li];
         swgb_record rc{0, 0, 0, 0, 0};
         int n = 0, m = 0, lq = 0, lr = 0;
         const uint8_t *qs = nullptr, *rs = nullptr;
@@ -858,22 +936,38 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
             // the letter of span row `row` (any code outside the span: its
             // cells are not computed)
             auto letter = [&](int row) -> int { return row >= 1 && row <= n ? qs[row - 1] : 0; };
+            // COOP: the whole warp waits (bounded) until the previous chunk's
+            // warp has finished span row `row`
+            auto wait_rows = [&](int row) {
+                const long long want = (long long)(c - 1) * (n + 1) + row;
+                volatile long long* prog = s_prog + (c - 1) % kIdWarps;
+                volatile int* abort_flag = &s_abort;
+                int spins = 0;
+                while (*prog < want && !*abort_flag && ++spins < kIdSpinLimit) {
+                }
+                if (spins >= kIdSpinLimit) {
+                    *abort_flag = 1;
+                    atomicMax(a.status, 4);
+                }
+                __threadfence_block();
+            };
+            // COOP: the previous chunk's boundary passes through a two-batch
+            // stage in shared memory, batch k = rows 32 k + 1 .. 32 k + 32:
+            // the warp loads batch k + 1 from global memory (one row a lane)
+            // at step 32 k + 8 and stages it at the end of step 32 k + 30, so
+            // that lane 0's read of row r at step r - 2 never waits on a
+            // global load
+            IdBnd* const stage = s_stage + (COOP ? w * 64 : 0);
+            const bool staged = COOP && c > 0;
+            IdBnd next_row{kNegInf, kNegInf, 0, 0};
+            if (staged) {
+                wait_rows(min(32, n));
+                if (lane + 1 <= n) stage[lane] = rbuf[lane + 1];
+                __syncwarp();
+            }
             // lane 0 of a later chunk: the previous chunk's boundary at `row`
             auto boundary = [&](int row) -> IdBnd {
-                if (COOP) {
-                    // the previous chunk's warp must have finished this row
-                    const long long want = (long long)(c - 1) * (n + 1) + row;
-                    volatile long long* prog = s_prog + (c - 1) % kIdWarps;
-                    volatile int* abort_flag = &s_abort;
-                    int spins = 0;
-                    while (*prog < want && !*abort_flag && ++spins < kIdSpinLimit) {
-                    }
-                    if (spins >= kIdSpinLimit) {
-                        *abort_flag = 1;
-                        atomicMax(a.status, 4);
-                    }
-                    __threadfence_block();
-                }
+                if (COOP) return stage[(((row - 1) >> 5) & 1) * 32 + ((row - 1) & 31)];
                 return rbuf[row];
             };
             // PF: the letter two rows on, its profile word and the boundary
@@ -983,6 +1077,16 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                 }
                 hd_next = gl == 0 ? hl : up_h;
                 sd_next = gl == 0 ? shl : up_sh;
+                if (staged) {
+                    const int row0 = 32 * ((t >> 5) + 1) + 1;   // the next batch's first row
+                    if ((t & 31) == 8 && row0 <= n) {
+                        wait_rows(min(row0 + 31, n));
+                        if (row0 + lane <= n) next_row = rbuf[row0 + lane];
+                    } else if ((t & 31) == 30 && row0 <= n) {
+                        stage[(((row0 - 1) >> 5) & 1) * 32 + lane] = next_row;
+                        __syncwarp();
+                    }
+                }
             }
             __syncwarp();
         }
@@ -1271,7 +1375,8 @@ struct SearchStore {
     uint32_t* comp = nullptr;      int64_t comp_cap = 0;
     uint32_t* comp2 = nullptr;     int64_t comp2_cap = 0;
     uint32_t* flags = nullptr;     int64_t flags_cap = 0;
-    unsigned long long* ctr = nullptr;   // [8] work counters and statistics
+    unsigned long long* ctr = nullptr;   // [16] work counters and statistics
+    uint32_t* id_hist = nullptr;         // identity lists: bucket counts and cursors
     int32_t* status = nullptr;
 };
 
@@ -1281,7 +1386,7 @@ void search_store_free(SearchStore* s) {
     void* ptrs[] = {s->ent_kmer, s->ent_pos, s->kcount, s->hist, s->start, s->bseq,
                     s->need, s->ccount, s->coff, s->part, s->gtab, s->bnd, s->ctr,
                     s->status, s->large_rows, s->lists, s->range, s->ent2_kmer, s->ent2_pos, s->kcount2,
-                    s->comp, s->comp2, s->flags, s->stash, s->stash_off};
+                    s->comp, s->comp2, s->flags, s->stash, s->stash_off, s->id_hist};
     for (void* p : ptrs) cudaFree(p);
     delete s;
 }
@@ -1295,6 +1400,7 @@ int search_store(swgb_ctx* ctx, SearchStore** out) {
         s->device = ctx->device;
         cudaError_t e = cudaMalloc(&s->ctr, sizeof(unsigned long long) * 16);
         if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&s->id_hist, sizeof(uint32_t) * 2 * kIdLists * kIdBuckets);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(join_kernel<false, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kJoinSmemBytes);
@@ -1310,6 +1416,26 @@ int search_store(swgb_ctx* ctx, SearchStore** out) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(join_warp_kernel<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpJoinSmemBytes);
+        // The identity launches run side by side; an SM holds blocks of
+        // several kernels only under one split of its L1 / shared memory, so
+        // all of them ask for the same (largest shared) split.
+        {
+            const void* ident_fns[] = {
+                (const void*)ident_kernel<8, uint32_t, false, false, false>,
+                (const void*)ident_kernel<16, uint32_t, true, false, false>,
+                (const void*)ident_kernel<32, uint32_t, true, false, false>,
+                (const void*)ident_kernel<32, uint64_t, true, false, false>,
+                (const void*)ident_kernel<8, uint32_t, false, false, true>,
+                (const void*)ident_kernel<16, uint32_t, true, false, true>,
+                (const void*)ident_kernel<32, uint32_t, true, false, true>,
+                (const void*)ident_kernel<32, uint64_t, true, false, true>,
+                (const void*)ident_kernel<32, uint32_t, true, true, true>,
+                (const void*)ident_kernel<32, uint64_t, true, true, true>};
+            for (const void* fn : ident_fns)
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        }
         if (e != cudaSuccess) {
             search_store_free(s);
             return cuda_fail(ctx, e, "search scratch");
@@ -1750,21 +1876,35 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     // longest query + 1)
     const int64_t max_rows = queries->max_len + 1;
     a.bnd_stride = max_rows;
-    CK(grow(&S->lists, &S->lists_cap, (int64_t)kIdClasses * n_pairs), "identity scratch");
+    CK(grow(&S->lists, &S->lists_cap, n_pairs), "identity scratch");
     a.lists = S->lists;
+    a.hist = S->id_hist;
     a.ctr = S->ctr;
     CK(cudaMemsetAsync(S->ctr, 0, sizeof(unsigned long long) * 8, st), "memset");
+    CK(cudaMemsetAsync(S->id_hist, 0, sizeof(uint32_t) * kIdLists * kIdBuckets, st), "memset");
     CK(cudaMemsetAsync(S->status, 0, sizeof(int32_t), st), "memset");
+    // the lists, each longest span first: count, scan, place
     const int64_t g = std::min<int64_t>((n_pairs + 255) / 256, (int64_t)ctx->sm_count * 16);
     ident_classify_kernel<<<(unsigned)g, 256, 0, st>>>(a);
     CK(cudaGetLastError(), "ident_classify kernel");
-    unsigned long long cnt[6] = {0, 0, 0, 0, 0, 0};   // class sizes (long spans of 2, 3 apart)
+    ident_scan_kernel<<<1, 256, 0, st>>>(a);
+    CK(cudaGetLastError(), "ident_scan kernel");
+    ident_place_kernel<<<(unsigned)g, 256, 0, st>>>(a);
+    CK(cudaGetLastError(), "ident_place kernel");
+    unsigned long long cnt[kIdLists] = {0, 0, 0, 0, 0, 0};   // list sizes (long spans of 2, 3 apart)
+    static_assert(kIdLists == 6, "four classes and two cooperative lists");
     CK(cudaMemcpyAsync(cnt, S->ctr + 1, sizeof(cnt), cudaMemcpyDeviceToHost, st), "sizes D2H");
     CK(cudaStreamSynchronize(st), "stream sync");
-    int32_t launches = 1;
+    int64_t list_base[kIdLists];
+    int64_t listed = 0;
+    for (int l = 0; l < kIdLists; ++l) {
+        list_base[l] = listed;
+        listed += (int64_t)cnt[l];
+    }
+    int32_t launches = 3;
     const int64_t resident_blocks = (int64_t)ctx->sm_count * 8;
-    // classes 2 and 3 split: spans of >= coop_cols columns at the front of
-    // their lists go to the cooperative launches, the rest to the regular ones
+    // classes 2 and 3 split: spans of >= coop_cols columns go to the
+    // cooperative launches, the rest to the regular ones
     const int64_t coop_n[2] = {(int64_t)cnt[4], (int64_t)cnt[5]};
     const int64_t reg_n[kIdClasses] = {(int64_t)cnt[0], (int64_t)cnt[1], (int64_t)cnt[2], (int64_t)cnt[3]};
     const int pairs_per_warp[kIdClasses] = {4, 2, 1, 1};
@@ -1785,22 +1925,23 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     a.bnd = S->bnd;
     // The regular chunked classes (2, then 3: they share their boundary
     // columns) run on the caller's stream; the cooperative launches (the
-    // longest spans, their own boundary region) on one side stream and the
-    // short-span classes (0, 1) on another, all at once, so that the short
-    // spans fill the SMs the long spans' tail leaves idle.  Each launch has
-    // its own work counter.
+    // longest spans, their own boundary region) on the stream of the
+    // greatest priority, so that their blocks are resident from the start
+    // (the regular launches are persistent and would otherwise hold every
+    // SM's registers until their lists run out), and the short-span classes
+    // (0, 1) on a side stream, all at once, so that the short spans fill the
+    // SMs the long spans' tail leaves idle.  Each launch has its own work
+    // counter.
     CK(cudaMemsetAsync(S->ctr + 8, 0, sizeof(unsigned long long) * 8, st), "memset");
     CK(cudaEventRecord(ctx->fork_ev, st), "event record");
-    cudaStream_t side = ctx->side[0], side_coop = ctx->side[1];
+    cudaStream_t side = ctx->side[0], side_coop = ctx->first;
     CK(cudaStreamWaitEvent(side, ctx->fork_ev, 0), "stream wait");
     CK(cudaStreamWaitEvent(side_coop, ctx->fork_ev, 0), "stream wait");
     for (int k = 0; k < 2; ++k) {
         if (coop_n[k] == 0) continue;
         IdentArgs b = a;
-        b.list = S->lists + (2 + k) * n_pairs;
+        b.list = S->lists + list_base[kIdClasses + k];
         b.n_list = coop_n[k];
-        b.n_front = coop_n[k];
-        b.back_base = n_pairs - 1;
         b.bnd = S->bnd + bnd_warps * max_rows;
         b.ctr = S->ctr + 12 + k;
         if (k == 0) ident_kernel<32, uint32_t, true, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
@@ -1813,11 +1954,8 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         const int cls = order[k];
         if (reg_n[cls] == 0) continue;
         IdentArgs b = a;
-        // classes 2 and 3: the back of the list (the front went cooperative)
-        b.list = S->lists + cls * n_pairs;
+        b.list = S->lists + list_base[cls];
         b.n_list = reg_n[cls];
-        b.n_front = cls >= 2 ? 0 : reg_n[cls];
-        b.back_base = n_pairs - 1;
         b.ctr = S->ctr + 8 + cls;
         const int blocks = blocks_of[cls];
         cudaStream_t s = cls >= 2 ? st : side;
@@ -1845,6 +1983,7 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
     ctx->last_search_launches = launches;
     if (status == 3) return fail(ctx, SWGB_ERANGE, "identity: a pair index or record outside its sequences");
     if (status == 4) return fail(ctx, SWGB_EINTERNAL, "identity: a chunk waited too long for the previous one");
+    if (status == 5) return fail(ctx, SWGB_EINTERNAL, "identity: a work list overflowed");
     if (status) return fail(ctx, SWGB_EINTERNAL, "identity: a span's global optimum differs from its record's score");
     return SWGB_OK;
 }
