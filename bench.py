@@ -64,6 +64,9 @@ def parse():
                     help="family blocks: training epochs of the learned filter")
     ap.add_argument("--filter-recall", type=float, default=0.995,
                     help="family blocks: recall of the training positives the threshold keeps")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="family blocks: keep the aligner's default knobs instead of tuning them "
+                         "(untimed) on the training block")
     ap.add_argument("--serve-refs", type=int, default=1_000_000, help="serving: resident references")
     ap.add_argument("--serve-requests", type=int, default=400, help="serving: timed requests")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
@@ -650,10 +653,13 @@ def run_search(args):
         dist.destroy_process_group()
 
 
-def train_filter(al, dev, mat, spec, seed, epochs, recall):
+def train_filter(al, dev, mat, spec, seed, epochs, recall, tune=False):
     """The learned filter, trained (untimed) on a family block drawn with
-    `seed`: exact labels, features, network, threshold.  Returns (MLP,
-    threshold, summary)."""
+    `seed`: exact labels, features, network, threshold.  With `tune`, the
+    aligner's knobs (tile overhead, band threshold) for the filtered pipeline
+    are also tuned, on the pairs of this block the trained filter keeps (the
+    plain pipeline keeps the defaults: tuning on all candidates gained
+    nothing there).  Returns (MLP, threshold, summary)."""
     import dataclasses
 
     import torch
@@ -673,6 +679,22 @@ def train_filter(al, dev, mat, spec, seed, epochs, recall):
     torch.cuda.synchronize()
     summary = {"candidates": int(cand.shape[0]), "passing": int(y.sum().item()), "epochs": epochs,
                "seconds": time.perf_counter() - t, "final_loss": losses[-1], "seed": seed}
+    if tune:
+        t = time.perf_counter()
+        knobs = {"plain": (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))}
+        logits = torch.empty((cand.shape[0],), dtype=torch.float32, device=dev)
+        net.forward(X, logits, torch.cuda.current_stream(dev))
+        kept, _ = swgb.swgb_select_pairs(al.ctx, cand, logits, threshold)
+        kept = kept.contiguous()
+        out = torch.empty((kept.shape[0], 5), dtype=torch.int32, device=dev)
+        swgb.swgb_autotune(al.ctx, s.handle, s.handle, kept, params, out)
+        knobs["filtered"] = (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))
+        swgb.swgb_set_tile_overhead(al.ctx, knobs["plain"][0])
+        swgb.swgb_set_band_min(al.ctx, knobs["plain"][1])
+        torch.cuda.synchronize()
+        summary["aligner_knobs"] = {k: {"tile_overhead": v[0], "band_min": v[1]} for k, v in knobs.items()}
+        summary["tuning_seconds"] = time.perf_counter() - t
+        del out, logits, kept
     del cand, ident, X, y
     s.close()
     return net, threshold, summary
@@ -700,7 +722,14 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
 
     # ---- training block (untimed): exact labels, features, network, threshold
     net, threshold, trained = train_filter(al, dev, mat, spec, spec.seed + 1, args.filter_epochs,
-                                           args.filter_recall)
+                                           args.filter_recall, tune=not args.no_tune)
+    knobs = trained.get("aligner_knobs")
+    saved_knobs = (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))
+
+    def use_knobs(pipeline):
+        if knobs:
+            swgb.swgb_set_tile_overhead(al.ctx, knobs[pipeline]["tile_overhead"])
+            swgb.swgb_set_band_min(al.ctx, knobs[pipeline]["band_min"])
 
     # ---- the measured block
     fs = workload.generate_families(dataclasses.replace(spec, seed=spec.seed), mat)
@@ -730,6 +759,7 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
         return lib.swgb_search_launches(al.ctx)
 
     def plain_step(timed):
+        use_knobs("plain")
         ev[0].record(stream)
         nl = discover()
         ev[1].record(stream)
@@ -751,6 +781,7 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
         return None
 
     def filtered_step(timed):
+        use_knobs("filtered")
         ev[0].record(stream)
         nl = discover()
         ev[1].record(stream)
@@ -830,6 +861,9 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
                                  (name, trained["seed"], trained["candidates"], trained["passing"],
                                   trained["epochs"], trained["seconds"]),
                    "final_loss": trained["final_loss"],
+                   "aligner_knobs": knobs and dict(knobs, tuned_on="filtered: the pairs the filter "
+                                                   "keeps on the training block (untimed, %.1f s); "
+                                                   "plain: the defaults" % trained["tuning_seconds"]),
                    "kmer_threshold_3": {"recall": float((cnt[y] >= 3).mean()) if y.any() else None,
                                         "kept_fraction": float((cnt >= 3).mean())},
                    "speedup_vs_plain": filt_rate / plain_rate,
@@ -848,6 +882,8 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
         "clocks": {"sm_mhz": clock["sm_mhz"], "sm_max_mhz": clock["sm_max_mhz"],
                    "reasons": clock["reasons"]},
     }
+    swgb.swgb_set_tile_overhead(al.ctx, saved_knobs[0])
+    swgb.swgb_set_band_min(al.ctx, saved_knobs[1])
     return line, mlp_params, threshold
 
 

@@ -654,6 +654,12 @@ struct IdBnd {
     int32_t h, e;
     uint64_t sh, se;
 };
+// The same in the kernel's own statistics width (the shared-memory stage).
+template <class St>
+struct IdRow {
+    int32_t h, e;
+    St sh, se;
+};
 
 struct IdentArgs {
     SeqView q, r;
@@ -844,7 +850,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
     __shared__ int8_t s_mat[kAlpha * kAlpha];
     __shared__ __align__(8) uint2 s_prof[PROF ? kIdWarps * 32 * kAlpha : 1];
     __shared__ long long s_prog[COOP ? kIdWarps : 1];
-    __shared__ IdBnd s_stage[COOP ? kIdWarps * 2 * 32 : 1];
+    __shared__ IdRow<St> s_stage[G == 32 ? kIdWarps * 2 * 32 : 1];
     __shared__ int s_abort;    // COOP: a wait ran out; later waits return at once
     __shared__ int64_t s_task;
     for (int t = threadIdx.x; t < kAlpha * kAlpha; t += blockDim.x) s_mat[t] = a.mat[t];
@@ -951,30 +957,35 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                 }
                 __threadfence_block();
             };
-            // COOP: the previous chunk's boundary passes through a two-batch
-            // stage in shared memory, batch k = rows 32 k + 1 .. 32 k + 32:
-            // the warp loads batch k + 1 from global memory (one row a lane)
-            // at step 32 k + 8 and stages it at the end of step 32 k + 30, so
-            // that lane 0's read of row r at step r - 2 never waits on a
-            // global load
-            IdBnd* const stage = s_stage + (COOP ? w * 64 : 0);
-            const bool staged = COOP && c > 0;
-            IdBnd next_row{kNegInf, kNegInf, 0, 0};
+            // G = 32: the previous chunk's boundary passes through a
+            // two-batch stage in shared memory, batch k = rows 32 k + 1 ..
+            // 32 k + 32: the warp loads batch k + 1 from global memory (one
+            // row a lane) at step 32 k + 8 and stages it at the end of step
+            // 32 k + 30, so that lane 0's read of a row never waits on a
+            // global load.  (Without COOP the previous chunk is this warp's
+            // own, finished before this one began; the rows a batch load
+            // reads are past the ones lane 31 has overwritten by then.)
+            IdRow<St>* const stage = s_stage + (G == 32 ? w * 64 : 0);
+            const bool staged = G == 32 && c > 0;
+            auto fetch = [&](int row) -> IdRow<St> {
+                const IdBnd b = rbuf[row];
+                return IdRow<St>{b.h, b.e, S::narrow(b.sh), S::narrow(b.se)};
+            };
+            IdRow<St> next_row{kNegInf, kNegInf, 0, 0};
             if (staged) {
-                wait_rows(min(32, n));
-                if (lane + 1 <= n) stage[lane] = rbuf[lane + 1];
+                if (COOP) wait_rows(min(32, n));
+                if (lane + 1 <= n) stage[lane] = fetch(lane + 1);
                 __syncwarp();
             }
             // lane 0 of a later chunk: the previous chunk's boundary at `row`
-            auto boundary = [&](int row) -> IdBnd {
-                if (COOP) return stage[(((row - 1) >> 5) & 1) * 32 + ((row - 1) & 31)];
-                return rbuf[row];
+            auto boundary = [&](int row) -> IdRow<St> {
+                return stage[(((row - 1) >> 5) & 1) * 32 + ((row - 1) & 31)];
             };
             // PF: the letter two rows on, its profile word and the boundary
             // entry one row on
             int qc_next = 0, qc_after = 0;
             uint2 pw_next = make_uint2(0u, 0u);
-            IdBnd b_next{kNegInf, kNegInf, 0, 0};
+            IdRow<St> b_next{kNegInf, kNegInf, 0, 0};
             if constexpr (PF) {
                 qc_next = letter(1 - gl);
                 qc_after = letter(2 - gl);
@@ -1007,7 +1018,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                         shl = 0;
                         sel = 0;
                     } else if (arow >= 1 && arow <= n) {
-                        IdBnd v;
+                        IdRow<St> v;
                         if constexpr (PF) {
                             v = b_next;
                             if (arow + 1 <= n) b_next = boundary(arow + 1);
@@ -1016,8 +1027,8 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                         }
                         hl = v.h;
                         el = v.e;
-                        shl = S::narrow(v.sh);
-                        sel = S::narrow(v.se);
+                        shl = v.sh;
+                        sel = v.se;
                     }
                 }
                 if (arow >= 1 && arow <= n && c0 < m) {
@@ -1080,8 +1091,8 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                 if (staged) {
                     const int row0 = 32 * ((t >> 5) + 1) + 1;   // the next batch's first row
                     if ((t & 31) == 8 && row0 <= n) {
-                        wait_rows(min(row0 + 31, n));
-                        if (row0 + lane <= n) next_row = rbuf[row0 + lane];
+                        if (COOP) wait_rows(min(row0 + 31, n));
+                        if (row0 + lane <= n) next_row = fetch(row0 + lane);
                     } else if ((t & 31) == 30 && row0 <= n) {
                         stage[(((row0 - 1) >> 5) & 1) * 32 + lane] = next_row;
                         __syncwarp();
