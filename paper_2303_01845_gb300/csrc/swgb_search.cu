@@ -649,17 +649,22 @@ constexpr int kIdLists = kIdClasses + 2;
 constexpr int kIdBuckets = 128;
 constexpr int32_t kNegInf = -(1 << 28);
 
-// A chunk's last column at one row: H, E and the (matches, columns) of H and E.
+// A chunk's last column at one row: H, E and the (matches, columns) of H and
+// E.  The scratch is sized in IdBnd entries (the widest form); a kernel keeps
+// its boundary rows in its own statistics width (16 bytes when the pairs are
+// packed 16 / 16 bits: one store and one load a row), in global memory and
+// in the shared-memory stage.
 struct IdBnd {
     int32_t h, e;
     uint64_t sh, se;
 };
-// The same in the kernel's own statistics width (the shared-memory stage).
 template <class St>
-struct IdRow {
+struct __align__(sizeof(St) == 4 ? 16 : 8) IdRow {
     int32_t h, e;
     St sh, se;
 };
+static_assert(sizeof(IdRow<uint32_t>) <= sizeof(IdBnd) && sizeof(IdRow<uint64_t>) <= sizeof(IdBnd),
+              "a boundary row fits its scratch entry");
 
 struct IdentArgs {
     SeqView q, r;
@@ -699,8 +704,6 @@ struct Stat<uint32_t> {
     __device__ static uint32_t inc(bool match) { return match ? 0x10001u : 1u; }
     __device__ static uint32_t matches(uint32_t s) { return s >> 16; }
     __device__ static uint32_t columns(uint32_t s) { return s & 0xffffu; }
-    __device__ static uint64_t wide(uint32_t s) { return ((uint64_t)(s >> 16) << 32) | (s & 0xffffu); }
-    __device__ static uint32_t narrow(uint64_t w) { return ((uint32_t)(w >> 32) << 16) | (uint32_t)(w & 0xffffu); }
 };
 template <>
 struct Stat<uint64_t> {
@@ -708,8 +711,6 @@ struct Stat<uint64_t> {
     __device__ static uint64_t inc(bool match) { return match ? 0x100000001ull : 1ull; }
     __device__ static uint32_t matches(uint64_t s) { return (uint32_t)(s >> 32); }
     __device__ static uint32_t columns(uint64_t s) { return (uint32_t)s; }
-    __device__ static uint64_t wide(uint64_t s) { return s; }
-    __device__ static uint64_t narrow(uint64_t w) { return w; }
 };
 
 __device__ __forceinline__ void ident_write(const IdentArgs& a, int64_t p, int32_t mt, int32_t cols,
@@ -860,7 +861,8 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
     const int grp = lane / G, gl = lane % G;
     const int64_t gw = (int64_t)blockIdx.x * kIdWarps + w;
     // boundary columns: one per warp (COOP: the block's kIdWarps, one per chunk residue)
-    IdBnd* const bnd_base = a.bnd + (COOP ? (int64_t)blockIdx.x * kIdWarps : gw) * a.bnd_stride;
+    IdRow<St>* const bnd_base =
+        reinterpret_cast<IdRow<St>*>(a.bnd) + (COOP ? (int64_t)blockIdx.x * kIdWarps : gw) * a.bnd_stride;
     uint2* prof = s_prof + (PROF ? (w * 32 + lane) * kAlpha : 0);
     const int32_t ge = a.ge, oe = a.go + a.ge;
     for (;;) {
@@ -907,8 +909,8 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
         St snm = 0;
         for (int c = COOP ? w : 0; c < nch_w; c += COOP ? kIdWarps : 1) {
             const int c0 = c * CHUNK + gl * kIdR;
-            IdBnd* const wbuf = bnd_base + (COOP ? (c % kIdWarps) * a.bnd_stride : 0);
-            IdBnd* const rbuf = bnd_base + (COOP ? ((c + kIdWarps - 1) % kIdWarps) * a.bnd_stride : 0);
+            IdRow<St>* const wbuf = bnd_base + (COOP ? (c % kIdWarps) * a.bnd_stride : 0);
+            IdRow<St>* const rbuf = bnd_base + (COOP ? ((c + kIdWarps - 1) % kIdWarps) * a.bnd_stride : 0);
             int rcode[kIdR];
             int32_t H[kIdR], F[kIdR];
             St SH[kIdR], SF[kIdR];
@@ -967,10 +969,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
             // reads are past the ones lane 31 has overwritten by then.)
             IdRow<St>* const stage = s_stage + (G == 32 ? w * 64 : 0);
             const bool staged = G == 32 && c > 0;
-            auto fetch = [&](int row) -> IdRow<St> {
-                const IdBnd b = rbuf[row];
-                return IdRow<St>{b.h, b.e, S::narrow(b.sh), S::narrow(b.se)};
-            };
+            auto fetch = [&](int row) -> IdRow<St> { return rbuf[row]; };
             IdRow<St> next_row{kNegInf, kNegInf, 0, 0};
             if (staged) {
                 if (COOP) wait_rows(min(32, n));
@@ -1071,7 +1070,7 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                     sh_out = shleft;
                     se_out = seleft;
                     if (G == 32 && gl == 31 && c + 1 < nch_w) {
-                        wbuf[arow] = IdBnd{hleft, eleft, S::wide(shleft), S::wide(seleft)};
+                        wbuf[arow] = IdRow<St>{hleft, eleft, shleft, seleft};
                         if (COOP) {
                             __threadfence_block();
                             *(volatile long long*)(s_prog + c % kIdWarps) = (long long)c * (n + 1) + arow;
