@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--filter-recall", type=float, default=0.995,
                     help="family blocks: recall of the training positives the threshold keeps")
     ap.add_argument("--no-tune", action="store_true",
-                    help="family blocks: keep the aligner's default knobs instead of tuning them "
-                         "(untimed) on the training block")
+                    help="family blocks: keep the context's aligner knobs for the filtered pipeline "
+                         "instead of tuning them (untimed) on the block's kept pairs")
     ap.add_argument("--serve-refs", type=int, default=1_000_000, help="serving: resident references")
     ap.add_argument("--serve-requests", type=int, default=400, help="serving: timed requests")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="serving: requests per second")
@@ -530,7 +530,8 @@ def measure_next_rows(args, al, dev):
             "stage_ms": {"plain": {k: line["plain"][k] for k in ("discover_ms", "align_ms", "identity_ms")},
                          "filtered": f["ms"]},
             "gcups_forward_kernel": line["plain"]["gcups_forward_kernel"],
-            "trained_on": f["trained_on"], "steps": steps, "cpu_baseline": line["cpu_baseline"],
+            "trained_on": f["trained_on"], "aligner_knobs": f["aligner_knobs"], "steps": steps,
+            "cpu_baseline": line["cpu_baseline"],
             "clocks": line["clocks"]}
     except Exception as e:   # noqa: BLE001
         out["families_200k"] = {"error": "%s: %s" % (type(e).__name__, e), "trace": traceback.format_exc()[-800:]}
@@ -653,13 +654,10 @@ def run_search(args):
         dist.destroy_process_group()
 
 
-def train_filter(al, dev, mat, spec, seed, epochs, recall, tune=False):
+def train_filter(al, dev, mat, spec, seed, epochs, recall):
     """The learned filter, trained (untimed) on a family block drawn with
-    `seed`: exact labels, features, network, threshold.  With `tune`, the
-    aligner's knobs (tile overhead, band threshold) for the filtered pipeline
-    are also tuned, on the pairs of this block the trained filter keeps (the
-    plain pipeline keeps the defaults: tuning on all candidates gained
-    nothing there).  Returns (MLP, threshold, summary)."""
+    `seed`: exact labels, features, network, threshold.  Returns (MLP,
+    threshold, summary)."""
     import dataclasses
 
     import torch
@@ -679,22 +677,6 @@ def train_filter(al, dev, mat, spec, seed, epochs, recall, tune=False):
     torch.cuda.synchronize()
     summary = {"candidates": int(cand.shape[0]), "passing": int(y.sum().item()), "epochs": epochs,
                "seconds": time.perf_counter() - t, "final_loss": losses[-1], "seed": seed}
-    if tune:
-        t = time.perf_counter()
-        knobs = {"plain": (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))}
-        logits = torch.empty((cand.shape[0],), dtype=torch.float32, device=dev)
-        net.forward(X, logits, torch.cuda.current_stream(dev))
-        kept, _ = swgb.swgb_select_pairs(al.ctx, cand, logits, threshold)
-        kept = kept.contiguous()
-        out = torch.empty((kept.shape[0], 5), dtype=torch.int32, device=dev)
-        swgb.swgb_autotune(al.ctx, s.handle, s.handle, kept, params, out)
-        knobs["filtered"] = (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))
-        swgb.swgb_set_tile_overhead(al.ctx, knobs["plain"][0])
-        swgb.swgb_set_band_min(al.ctx, knobs["plain"][1])
-        torch.cuda.synchronize()
-        summary["aligner_knobs"] = {k: {"tile_overhead": v[0], "band_min": v[1]} for k, v in knobs.items()}
-        summary["tuning_seconds"] = time.perf_counter() - t
-        del out, logits, kept
     del cand, ident, X, y
     s.close()
     return net, threshold, summary
@@ -722,12 +704,16 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
 
     # ---- training block (untimed): exact labels, features, network, threshold
     net, threshold, trained = train_filter(al, dev, mat, spec, spec.seed + 1, args.filter_epochs,
-                                           args.filter_recall, tune=not args.no_tune)
-    knobs = trained.get("aligner_knobs")
+                                           args.filter_recall)
+    # the aligner's knobs (tile overhead, band threshold) of each pipeline:
+    # plain keeps the context's; filtered is tuned (untimed) on this block's
+    # kept pairs after the first warm-up step, as the batched line is tuned
+    # on its own batch
     saved_knobs = (swgb.swgb_get_tile_overhead(al.ctx), swgb.swgb_get_band_min(al.ctx))
+    knobs = {"plain": {"tile_overhead": saved_knobs[0], "band_min": saved_knobs[1]}}
 
     def use_knobs(pipeline):
-        if knobs:
+        if pipeline in knobs:
             swgb.swgb_set_tile_overhead(al.ctx, knobs[pipeline]["tile_overhead"])
             swgb.swgb_set_band_min(al.ctx, knobs[pipeline]["band_min"])
 
@@ -751,6 +737,7 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
     plain = {"discover": [], "align": [], "identity": [], "step": [], "fwd": []}
     filt = {"features": [], "network": [], "select": [], "align": [], "identity": [], "step": []}
     launches = {"plain": 0, "filtered": 0}
+    band_stats = {}
 
     def discover():
         swgb._check(al.ctx, lib.swgb_discover(al.ctx, s.handle, 6, 2, cand.data_ptr(),
@@ -809,11 +796,27 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
                               ("align", 4, 5), ("identity", 5, 6), ("step", 0, 6)):
                 filt[key].append(ev[a].elapsed_time(ev[b]))
             filt.setdefault("discover", []).append(ev[0].elapsed_time(ev[1]))
-            launches["filtered"] += nl + swgb.swgb_last_stats(al.ctx)["kernel_launches"]
+            st = swgb.swgb_last_stats(al.ctx)
+            launches["filtered"] += nl + st["kernel_launches"]
+            filt.setdefault("align_forward", []).append(st["forward_ms"])
+            filt.setdefault("align_reverse", []).append(st["reverse_ms"])
+            band_stats.update(pairs=st["n_band_pairs"], certified=st["n_band_certified"])
 
-    for _ in range(warmup):
+    tune_s = 0.0
+    for w_ in range(warmup):
         plain_step(False)
         filtered_step(False)
+        if w_ == 0 and not args.no_tune:
+            t_ = time.perf_counter()
+            k = n_kept.value
+            tmp = torch.empty((max(k, 1), 5), dtype=torch.int32, device=dev)
+            swgb.swgb_autotune(al.ctx, s.handle, s.handle, kept[:k], params, tmp[:k])
+            tu = swgb.swgb_last_tuning(al.ctx)
+            knobs["filtered"] = {"tile_overhead": tu["tile_overhead"], "band_min": tu["band_min"],
+                                 "tuned_ms": round(tu["best_ms"], 3), "band_off_ms": round(tu["band_off_ms"], 3),
+                                 "tuned_pairs": int(k)}
+            del tmp
+            tune_s = time.perf_counter() - t_
     stats = None
     with ClockSampler(dev.index) as clocks:
         torch.cuda.synchronize()
@@ -861,9 +864,11 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
                                  (name, trained["seed"], trained["candidates"], trained["passing"],
                                   trained["epochs"], trained["seconds"]),
                    "final_loss": trained["final_loss"],
-                   "aligner_knobs": knobs and dict(knobs, tuned_on="filtered: the pairs the filter "
-                                                   "keeps on the training block (untimed, %.1f s); "
-                                                   "plain: the defaults" % trained["tuning_seconds"]),
+                   "align_band": band_stats,
+                   "aligner_knobs": dict(knobs, tuned_on="filtered: this block's kept pairs, after the "
+                                                 "first warm-up step (untimed, %.1f s), as the batched "
+                                                 "line is tuned on its batch; plain: the context's "
+                                                 "knobs" % tune_s),
                    "kmer_threshold_3": {"recall": float((cnt[y] >= 3).mean()) if y.any() else None,
                                         "kept_fraction": float((cnt >= 3).mean())},
                    "speedup_vs_plain": filt_rate / plain_rate,
