@@ -70,6 +70,7 @@ extern "C" {
 /* swgb_seqset_create / swgb_seqset_load */
 #define SWGB_SEQ_ASCII 0x1u   /* residues are ASCII letters; otherwise codes 0..23 */
 #define SWGB_SEQ_DEVICE 0x2u  /* residues and offsets are device pointers; otherwise host */
+#define SWGB_SEQ_COPY 0x4u    /* host residues go through the copy engines even when pinned */
 /* swgb_params.flags */
 #define SWGB_FORCE_INT32 0x1u /* every pair on the 32-bit path (no 16x2 packing) */
 #define SWGB_TIMING 0x2u      /* record CUDA events around the forward and reverse kernels */
@@ -146,8 +147,10 @@ void swgb_blosum62(int8_t* out);
  * The host reads only offsets[0] and offsets[n_seqs]: the offsets are checked
  * (non-decreasing, lengths up to SWGB_MAX_LENGTH), measured and rebased on
  * the device.  Host residues in pinned (page-locked) memory are read in place
- * by the encode kernel over the host link; other host residues are uploaded
- * first (in four concurrent parts from 64 MB on).
+ * by the encode kernel over the host link (the fastest load on an idle GPU);
+ * other host residues, and pinned ones with SWGB_SEQ_COPY, are uploaded first
+ * by the copy engines (in four concurrent parts from 64 MB on), so the upload
+ * itself needs no SMs.
  * Errors: EINVAL, ERANGE (a sequence longer than SWGB_MAX_LENGTH, or offsets
  * decreasing), EBADRES (a letter/code outside the alphabet; such codes are
  * stored as 0), ENOMEM, ECUDA.  After ERANGE from the offsets the set is

@@ -235,7 +235,7 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
                                  int64_t n_seqs, uint32_t flags, void* stream) {
     if (!set || !set->ctx) return SWGB_EINVAL;
     swgb_ctx* ctx = set->ctx;
-    if (n_seqs < 0 || (flags & ~(SWGB_SEQ_ASCII | SWGB_SEQ_DEVICE)))
+    if (n_seqs < 0 || (flags & ~(SWGB_SEQ_ASCII | SWGB_SEQ_DEVICE | SWGB_SEQ_COPY)))
         return fail(ctx, SWGB_EINVAL, "seqset: negative count or unknown flags");
     if (n_seqs > 0 && !offsets) return fail(ctx, SWGB_EINVAL, "seqset: offsets is NULL");
     if (n_seqs > INT32_MAX) return fail(ctx, SWGB_ERANGE, "seqset: more than 2^31-1 sequences");
@@ -278,7 +278,7 @@ SWGB_EXPORT int swgb_seqset_load(swgb_seqset* set, const void* residues, const i
     if (total > 0) {
         if (on_dev) {
             src += base;
-        } else if (const uint8_t* mapped = mapped_host(src + base, total)) {
+        } else if (const uint8_t* mapped = (flags & SWGB_SEQ_COPY) ? nullptr : mapped_host(src + base, total)) {
             // pinned host memory: the encode pass reads it in place over the
             // host link (no staging copy)
             src = mapped;

@@ -29,6 +29,7 @@ SWGB_ALPHABET_SIZE = 24
 SWGB_MAX_LENGTH = 65536
 SWGB_SEQ_ASCII = 0x1
 SWGB_SEQ_DEVICE = 0x2
+SWGB_SEQ_COPY = 0x4
 SWGB_FORCE_INT32 = 0x1
 SWGB_TIMING = 0x2
 SWGB_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -268,10 +269,11 @@ def _seq_args(residues, offsets, flags):
     return flags, max(n, 0)
 
 
-def swgb_seqset_create(ctx, residues, offsets, ascii=False, stream=None):
+def swgb_seqset_create(ctx, residues, offsets, ascii=False, stream=None, copy=False):
     """residues: uint8 codes (or ASCII with ascii=True); offsets: int64 [n+1].
-    Host (numpy / CPU tensor) or device (CUDA tensor) buffers."""
-    flags, n = _seq_args(residues, offsets, SWGB_SEQ_ASCII if ascii else 0)
+    Host (numpy / CPU tensor) or device (CUDA tensor) buffers.  copy: pinned
+    host residues go through the copy engines (SWGB_SEQ_COPY)."""
+    flags, n = _seq_args(residues, offsets, (SWGB_SEQ_ASCII if ascii else 0) | (SWGB_SEQ_COPY if copy else 0))
     h = _VP()
     rc = load().swgb_seqset_create(ctx, _ptr(residues), _ptr(offsets), n, flags,
                                    _stream_handle(stream), ctypes.byref(h))
@@ -279,8 +281,8 @@ def swgb_seqset_create(ctx, residues, offsets, ascii=False, stream=None):
     return h
 
 
-def swgb_seqset_load(ctx, seqset, residues, offsets, ascii=False, stream=None):
-    flags, n = _seq_args(residues, offsets, SWGB_SEQ_ASCII if ascii else 0)
+def swgb_seqset_load(ctx, seqset, residues, offsets, ascii=False, stream=None, copy=False):
+    flags, n = _seq_args(residues, offsets, (SWGB_SEQ_ASCII if ascii else 0) | (SWGB_SEQ_COPY if copy else 0))
     rc = load().swgb_seqset_load(seqset, _ptr(residues), _ptr(offsets), n, flags,
                                  _stream_handle(stream))
     _check(ctx, rc)
@@ -793,8 +795,8 @@ class Aligner:
         except Exception:
             pass
 
-    def seqset(self, residues, offsets, ascii=False, stream=None):
-        return SeqSet(self, swgb_seqset_create(self.ctx, residues, offsets, ascii, stream))
+    def seqset(self, residues, offsets, ascii=False, stream=None, copy=False):
+        return SeqSet(self, swgb_seqset_create(self.ctx, residues, offsets, ascii, stream, copy))
 
     def align(self, queries, refs, pairs, params=None, out=None, stream=None, sync=True):
         params = params or make_params()
@@ -831,8 +833,8 @@ class SeqSet:
     def info(self):
         return swgb_seqset_info(self.handle)
 
-    def load(self, residues, offsets, ascii=False, stream=None):
-        swgb_seqset_load(self.aligner.ctx, self.handle, residues, offsets, ascii, stream)
+    def load(self, residues, offsets, ascii=False, stream=None, copy=False):
+        swgb_seqset_load(self.aligner.ctx, self.handle, residues, offsets, ascii, stream, copy)
 
     def close(self):
         if self.handle:

@@ -327,6 +327,51 @@ def test_seqset_offsets_checked_and_rebased_on_device(aligner, oracle_mod, blosu
     ok.close()
 
 
+def test_sets_uploaded_by_copy_engines_on_another_context(aligner, oracle_mod, blosum, plain10k, torch_cuda):
+    """SWGB_SEQ_COPY sends pinned host residues through the copy engines
+    instead of the encode kernel's in-place read: the same records, also from
+    offsets that start past 0.  Sets of a second context, loaded on a helper
+    thread while the first context aligns the other buffer (the pipelined
+    end-to-end pattern), align identically."""
+    torch = torch_cuda
+    import concurrent.futures
+    from paper_2303_01845_gb300 import swgb
+    sub = plain10k.subset(np.arange(0, 10000, 53))
+    want = oracle_records(oracle_mod, sub, blosum, 11, 1)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    pad = np.full(7, 3, np.uint8)
+    q = aligner.seqset(pin(np.concatenate([pad, sub.q_res])), pin(sub.q_off + 7), copy=True)
+    r = aligner.seqset(pin(np.concatenate([pad, sub.r_res])), pin(sub.r_off + 7), copy=True)
+    assert swgb.swgb_seqset_info(q.handle) == (len(sub.q_off) - 1, int(np.diff(sub.q_off).max()))
+    assert_same(gpu_records(aligner, sub, params(blosum), sets=(q, r)), want, sub)
+    q.close()
+    r.close()
+    q_res, q_off, r_res, r_off = pin(sub.q_res), pin(sub.q_off), pin(sub.r_res), pin(sub.r_off)
+    loader = swgb.Aligner(0)
+    stream = torch.cuda.Stream()
+    bufs = []
+    try:
+        bufs = [(loader.seqset(q_res, q_off, stream=stream, copy=True),
+                 loader.seqset(r_res, r_off, stream=stream, copy=True)) for _ in range(2)]
+
+        def load(k):
+            bufs[k][0].load(q_res, q_off, stream=stream, copy=True)
+            bufs[k][1].load(r_res, r_off, stream=stream, copy=True)
+
+        with concurrent.futures.ThreadPoolExecutor(1) as ex:
+            pending = ex.submit(load, 0)
+            for i in range(4):
+                pending.result()
+                if i + 1 < 4:
+                    pending = ex.submit(load, (i + 1) % 2)
+                assert_same(gpu_records(aligner, sub, params(blosum), sets=bufs[i % 2]), want, sub)
+    finally:
+        for bq, br in bufs:
+            bq.close()
+            br.close()
+        loader.close()
+
+
 def test_errors_are_reported(aligner, blosum, plain10k, torch_cuda):
     torch = torch_cuda
     from paper_2303_01845_gb300 import swgb
