@@ -1952,6 +1952,10 @@ SWGB_EXPORT int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const s
         IdentArgs b = a;
         b.list = S->lists + list_base[kIdClasses + k];
         b.n_list = coop_n[k];
+        // the cooperative region starts after bnd_warps x max_rows 24-byte
+        // entries: 16-byte aligned (its rows are 16-byte vectors) because
+        // bnd_warps is a multiple of the (even) warps per block
+        static_assert(kIdWarps % 2 == 0 && sizeof(IdBnd) == 24, "cooperative boundary region alignment");
         b.bnd = S->bnd + bnd_warps * max_rows;
         b.ctr = S->ctr + 12 + k;
         if (k == 0) ident_kernel<32, uint32_t, true, true, true><<<coop_blocks[k], kIdWarps * 32, 0, side_coop>>>(b);
