@@ -1076,14 +1076,6 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                             *(volatile long long*)(s_prog + c % kIdWarps) = (long long)c * (n + 1) + arow;
                         }
                     }
-                    if (arow == n && m > c0 && m <= c0 + kIdR) {
-#pragma unroll
-                        for (int x = 0; x < kIdR; ++x)
-                            if (c0 + x + 1 == m) {
-                                hnm = H[x];
-                                snm = SH[x];
-                            }
-                    }
                 }
                 hd_next = gl == 0 ? hl : up_h;
                 sd_next = gl == 0 ? shl : up_sh;
@@ -1097,6 +1089,16 @@ __global__ void __launch_bounds__(kIdWarps * 32) ident_kernel(IdentArgs a) {
                         __syncwarp();
                     }
                 }
+            }
+            // the lane owning column m: no row past n is computed, so its
+            // columns hold row n once the steps are done
+            if (n >= 1 && m > c0 && m <= c0 + kIdR) {
+#pragma unroll
+                for (int x = 0; x < kIdR; ++x)
+                    if (c0 + x + 1 == m) {
+                        hnm = H[x];
+                        snm = SH[x];
+                    }
             }
             __syncwarp();
         }
