@@ -351,11 +351,16 @@ typedef struct {
 /* Identity and pass/fail of n_pairs records of swgb_align (same sets, same
  * pairs, same params).  pairs, records and out are DEVICE buffers, out is
  * swgb_identity_record [n_pairs] in pair order.  Synchronous on `stream`.
- * Device scratch (4 bits per cell of the spans being traced, per resident
- * warp) is owned by the context and grown on demand.
+ * The span's DP runs forward carrying, per state, the (identical columns,
+ * columns) of the path the preference above traces; no traceback matrix.
+ * Device scratch (one work-list entry per pair, and one boundary column of
+ * the longest query's rows per resident warp of the classes that split a
+ * span into 256-column chunks) is owned by the context and grown on demand.
  * Errors: EINVAL, ENOMEM, ECUDA, ERANGE (a pair index or record coordinate
  * outside its sequences), EINTERNAL (a record whose span does not reach its
- * score); such a pair's entry is -1, -1, 0. */
+ * score, a span's chunk that waited too long for the previous chunk, or the
+ * work lists disagreeing with their counts); a pair outside its sequences or
+ * whose span does not reach its score gets -1, -1, 0. */
 int swgb_identity(swgb_ctx* ctx, const swgb_seqset* queries, const swgb_seqset* refs,
                   const int32_t* pairs, const swgb_record* records, int64_t n_pairs,
                   const swgb_params* params, const swgb_thresholds* thresholds,
