@@ -24,11 +24,14 @@
 //
 // Identity (the production filter keeps pairs of identity >= 30 % and
 // coverage >= 70 %, program-parameters table; the paper defines neither):
-// the global affine alignment of a record's span is filled by a warp
-// wavefront that stores four decision bits per cell, then traced back from
-// the span's end under a fixed preference -- diagonal, then a gap in the
-// reference (query residue against a gap), then a gap in the query; inside a
-// gap its opening before its extension -- counting identical columns.
+// the identical columns and columns of the alignment that a traceback of the
+// record span's global affine DP takes under a fixed preference -- diagonal,
+// then a gap in the reference (query residue against a gap), then a gap in
+// the query; inside a gap its opening before its extension -- computed by a
+// forward wavefront that carries those statistics with the DP (no decision
+// matrix, no traceback).  A counting sort lays the pairs out in work lists
+// by span class, each longest first; spans of many chunks are shared by the
+// warps of a block.
 #include <climits>
 #include <cstdint>
 #include <cstdio>
