@@ -865,10 +865,10 @@ def measure_families(args, al, dev, name, steps, warmup, cpu_seconds, dist=None,
                                   trained["epochs"], trained["seconds"]),
                    "final_loss": trained["final_loss"],
                    "align_band": band_stats,
-                   "aligner_knobs": dict(knobs, tuned_on="filtered: this block's kept pairs, after the "
-                                                 "first warm-up step (untimed, %.1f s), as the batched "
-                                                 "line is tuned on its batch; plain: the context's "
-                                                 "knobs" % tune_s),
+                   "aligner_knobs": dict(knobs, tuned_on=(
+                       "filtered: this block's kept pairs, after the first warm-up step (untimed, "
+                       "%.1f s), as the batched line is tuned on its batch; plain: the context's knobs"
+                       % tune_s) if "filtered" in knobs else "not tuned: both pipelines on the context's knobs"),
                    "kmer_threshold_3": {"recall": float((cnt[y] >= 3).mean()) if y.any() else None,
                                         "kept_fraction": float((cnt >= 3).mean())},
                    "speedup_vs_plain": filt_rate / plain_rate,
