@@ -83,3 +83,25 @@ def test_null_arguments_are_rejected(lib):
     assert lib.swgb_seqset_info(None, None, None) == swgb.SWGB_EINVAL
     lib.swgb_destroy(None)
     lib.swgb_seqset_destroy(None)
+
+
+def header_constants():
+    """The header's integer #defines (error codes, flags, sizes), evaluated."""
+    out = {}
+    for name, value in re.findall(r"^#define (SWGB_[A-Z_0-9]+)[ \t]+([^/\n]+)", open(HEADER).read(), flags=re.M):
+        expr = re.sub(r"\b(0x[0-9a-fA-F]+|[0-9]+)[uU]\b", r"\1", value.strip())
+        if re.fullmatch(r"[0-9a-fA-FxX()<> +\-]+", expr):
+            out[name] = eval(expr, {"__builtins__": {}})   # integer literals, shifts and signs only
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant the binding mirrors has the header's value, and
+    the binding mirrors every error code and flag."""
+    from paper_2303_01845_gb300 import swgb
+    consts = header_constants()
+    assert consts["SWGB_SEQ_COPY"] == 0x4 and consts["SWGB_EINVAL"] == -1
+    mirrored = {n: v for n, v in consts.items() if hasattr(swgb, n)}
+    assert mirrored == {n: getattr(swgb, n) for n in mirrored}
+    must = [n for n in consts if n.startswith(("SWGB_E", "SWGB_SEQ_")) or n in ("SWGB_OK", "SWGB_FORCE_INT32", "SWGB_TIMING")]
+    assert all(hasattr(swgb, n) for n in must), [n for n in must if not hasattr(swgb, n)]
